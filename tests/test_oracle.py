@@ -1,0 +1,326 @@
+"""Pins of the FP64 CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: closed-form
+moments, the exact discrete steady states of wall-driven and body-force-driven
+channel flow, conservation laws, finite differences of the bead-spring energy
+(Eq. 9, bending term without the square, which is the energy whose gradient
+is Eq. 12), and invariants of Eqs. 4-5.  No test here needs a GPU.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2212_14153_gb300 import workloads as wl
+
+CX = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1])
+CY = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1])
+CS2 = 1.0 / 3.0
+
+
+# ------------------------------------------------------------ moment basis
+def test_moment_matrix_rows_orthogonal_with_known_norms():
+    M = oracle.moment_matrix()
+    G = M @ M.T
+    # Lallemand-Luo (2000) basis: squared norms of rho,e,eps,jx,qx,jy,qy,pxx,pxy
+    assert np.array_equal(np.diag(G), [9, 36, 36, 6, 12, 6, 12, 4, 4])
+    assert np.count_nonzero(G - np.diag(np.diag(G))) == 0
+    # the conserved rows are the lattice's mass and momentum
+    assert np.array_equal(M[0], np.ones(9))
+    assert np.array_equal(M[3], CX) and np.array_equal(M[5], CY)
+    assert np.allclose(oracle.inverse_moment_matrix() @ M, np.eye(9), atol=1e-15)
+
+
+@pytest.mark.parametrize("rho,ux,uy", [(1.0, 0.0, 0.0), (1.03, 0.02, -0.015), (0.97, -0.05, 0.04)])
+def test_equilibrium_velocity_moments(rho, ux, uy):
+    f = oracle.feq(rho, ux, uy)
+    # zeroth, first and second velocity moments of the discrete equilibrium
+    assert math.isclose(f.sum(), rho, rel_tol=1e-15)
+    assert np.allclose([f @ CX, f @ CY], [rho * ux, rho * uy], atol=1e-16)
+    Pxx, Pyy, Pxy = f @ (CX * CX), f @ (CY * CY), f @ (CX * CY)
+    assert np.allclose([Pxx, Pyy, Pxy], [rho * (CS2 + ux * ux), rho * (CS2 + uy * uy), rho * ux * uy],
+                       atol=1e-16)
+    # velocity-space equilibrium and the moment-space equilibrium agree
+    assert np.allclose(oracle.moment_matrix() @ f, oracle.meq(rho, ux, uy), atol=4e-16)
+
+
+def test_guo_source_moments_and_two_forms_agree():
+    rng = np.random.default_rng(7)
+    for _ in range(20):
+        ux, uy = rng.uniform(-0.05, 0.05, 2)
+        Fx, Fy = rng.uniform(-1e-3, 1e-3, 2)
+        S = oracle.guo_velocity(ux, uy, Fx, Fy)
+        # Guo et al. (2002): zero mass source, momentum source F,
+        # second moment u F + F u
+        assert abs(S.sum()) < 1e-18
+        assert np.allclose([S @ CX, S @ CY], [Fx, Fy], atol=1e-18)
+        assert np.allclose([S @ (CX * CX), S @ (CY * CY), S @ (CX * CY)],
+                           [2 * ux * Fx, 2 * uy * Fy, ux * Fy + uy * Fx], atol=1e-18)
+        Sm = oracle.guo_moment(ux, uy, Fx, Fy)
+        assert np.allclose(oracle.moment_matrix() @ S, Sm, rtol=0, atol=1e-14 * max(abs(Fx), abs(Fy)))
+
+
+# ------------------------------------------------------------ collision
+def _random_state(rng):
+    rho = rng.uniform(0.95, 1.05)
+    u = rng.uniform(-0.05, 0.05, 2)
+    return oracle.feq(rho, *u) + rng.normal(0, 2e-3, 9)
+
+
+def test_mrt_with_equal_rates_is_velocity_space_bgk():
+    rng = np.random.default_rng(11)
+    for tau in (0.51, 0.8, 1.0, 3.0, 40.0):
+        for _ in range(10):
+            f = _random_state(rng)
+            Fx, Fy = rng.uniform(-1e-3, 1e-3, 2)
+            a = oracle.collide_mrt(f, Fx, Fy, np.full(9, 1.0 / tau))
+            b = oracle.collide_bgk(f, Fx, Fy, tau)
+            assert np.abs(a - b).max() <= 1e-14
+
+
+def test_collision_conserves_mass_and_adds_force_to_momentum():
+    rng = np.random.default_rng(12)
+    for coll in (0, 1):
+        for nu in (0.01, 0.1, 0.5, 25.0):
+            s = oracle.rates(coll, nu)
+            f = _random_state(rng)
+            Fx, Fy = rng.uniform(-1e-3, 1e-3, 2)
+            out = oracle.collide_mrt(f, Fx, Fy, s)
+            assert abs(out.sum() - f.sum()) < 1e-15
+            assert np.allclose([out @ CX - f @ CX, out @ CY - f @ CY], [Fx, Fy], atol=1e-16)
+
+
+def test_rates_of_conserved_moments_do_not_matter():
+    rng = np.random.default_rng(13)
+    f = _random_state(rng)
+    s = oracle.rates(0, 0.2)
+    base = oracle.collide_mrt(f, 3e-4, -2e-4, s)
+    for srho, sj in [(0.3, 0.7), (1.9, 1.2), (1.0, 0.01)]:
+        s2 = s.copy()
+        s2[0] = srho
+        s2[3] = s2[5] = sj
+        assert np.abs(oracle.collide_mrt(f, 3e-4, -2e-4, s2) - base).max() < 1e-16
+
+
+def test_magic_rates_pairing_and_shear_rate():
+    for nu in (0.01, 0.2, 1.0, 25.6):
+        s = oracle.rates(0, nu)
+        # nu = c_s^2 (1/s_nu - 1/2)
+        assert math.isclose(CS2 * (1 / s[7] - 0.5), nu, rel_tol=1e-14)
+        assert s[7] == s[8] == s[1] == s[2]
+        assert math.isclose((1 / s[7] - 0.5) * (1 / s[4] - 0.5), 3.0 / 16.0, rel_tol=1e-13)
+
+
+# ------------------------------------------------------------ lattice
+def test_rest_equilibrium_is_fixed_point():
+    cfg = wl.couette_only(20, 12, u=0.0, nu=0.1, init_couette=0)
+    s = oracle.Sim(cfg)
+    s.step(500)
+    w = oracle.feq(1.0, 0.0, 0.0)
+    assert np.abs(s.populations() - w[:, None, None]).max() <= 4e-16
+
+
+def test_linear_couette_is_exact_steady_state():
+    H = 20
+    y = np.arange(H) + 0.5
+    exact = -0.01 + 0.02 * y / H
+    # magic MRT pairing and BGK: exact to round-off.  The constant
+    # Lallemand-Luo rates leave an O(U^2) wall-layer deviation (~2e-7 U here).
+    for coll, tol in ((0, 1e-15), (2, 1e-14), (1, 1e-6 * 0.01)):
+        cfg = wl.couette_only(8, H, u=0.01, nu=0.2, init_couette=1)
+        cfg["collision"] = coll
+        s = oracle.Sim(cfg)
+        s.step(3000)
+        ux, uy, rho = s.fields()
+        assert np.abs(ux - exact[:, None]).max() < tol
+        assert np.abs(uy).max() < 1e-14 and np.abs(rho - 1).max() < max(tol, 1e-13) * 100
+
+
+def test_couette_from_rest_converges_to_linear_profile():
+    H = 16
+    y = np.arange(H) + 0.5
+    exact = -0.01 + 0.02 * y / H
+    s = oracle.Sim(wl.couette_only(4, H, u=0.01, nu=0.3, init_couette=0))
+    s.step(12000)
+    ux, _, _ = s.fields()
+    assert np.abs(ux - exact[:, None]).max() < 1e-10
+
+
+def _poiseuille_error(H, nu, coll, g=1e-6, steps=None):
+    cfg = wl.couette_only(4, H, u=0.0, nu=nu, init_couette=0)
+    cfg.update(gx=g, collision=coll)
+    s = oracle.Sim(cfg)
+    s.step(steps or int(12 * H * H / nu))
+    ux, uy, _ = s.fields()
+    y = np.arange(H) + 0.5
+    exact = g / (2 * nu) * y * (H - y)
+    return np.abs(ux[:, 0] - exact).max() / exact.max(), np.abs(uy).max()
+
+
+def test_body_force_poiseuille_exact_with_magic_rates():
+    # half-way bounce-back puts the no-slip wall exactly at y = 0, H for the
+    # magic pairing: the parabola is the exact discrete solution
+    for nu in (0.1, 1.0 / 6.0, 0.5):
+        err, uy = _poiseuille_error(16, nu, 0)
+        assert err < 1e-9 and uy < 1e-14
+
+
+def test_body_force_poiseuille_second_order_with_other_rates():
+    for coll, nu in ((1, 0.1), (2, 0.5)):
+        e16, _ = _poiseuille_error(16, nu, coll)
+        e32, _ = _poiseuille_error(32, nu, coll)
+        assert e16 > 1e-4                      # not exact: wall slip O(1/H^2)
+        assert 3.5 < e16 / e32 < 4.5           # second-order convergence
+
+
+def test_mass_exact_with_beads_forcing_and_moving_walls():
+    rng = np.random.default_rng(21)
+    cfg = wl.random_fiber(rng, 48, 32, n_beads=5, a=2.0, xi=1.0, gx=2e-6, gy=-1e-6)
+    s = oracle.Sim(cfg)
+    m0 = s.totals()[0]
+    s.step(400)
+    assert abs(s.totals()[0] - m0) / m0 < 1e-13
+
+
+# ------------------------------------------------------------ beads
+def _chain(rng, N, NF, a, noise):
+    R = np.zeros((N * NF, 2))
+    for f in range(NF):
+        th = rng.uniform(0, math.pi)
+        c = np.array([30.0 + 6.0 * f, 20.0])
+        for i in range(N):
+            R[f * N + i] = c + (i - (N - 1) / 2) * 2 * a * np.array([math.cos(th), math.sin(th)])
+    return R + rng.normal(0, noise, R.shape)
+
+
+@pytest.mark.parametrize("N,NF", [(2, 1), (3, 1), (4, 1), (5, 1), (9, 1), (7, 2)])
+def test_bead_forces_are_minus_energy_gradient(N, NF):
+    rng = np.random.default_rng(100 + N)
+    a = 2.0
+    ks, kb, kev = 3.0, 0.7, 2.5
+    R = _chain(rng, N, NF, a, 0.4)
+    F = oracle.bead_forces(R, N, NF, a, ks, kb, kev)
+    h = 1e-6
+    Ffd = np.zeros_like(R)
+    for b in range(N * NF):
+        for d in range(2):
+            Rp = R.copy(); Rp[b, d] += h
+            Rm = R.copy(); Rm[b, d] -= h
+            Ffd[b, d] = -(oracle.bead_energy(Rp, N, NF, a, ks, kb, kev)
+                          - oracle.bead_energy(Rm, N, NF, a, ks, kb, kev)) / (2 * h)
+    scale = np.abs(F).max()
+    assert np.abs(F - Ffd).max() <= 1e-7 * scale
+    # internal forces: no net force, no net torque
+    assert np.abs(F.sum(axis=0)).max() <= 1e-13 * scale
+    torque = np.sum(R[:, 0] * F[:, 1] - R[:, 1] * F[:, 0])
+    assert abs(torque) <= 1e-12 * scale * np.abs(R).max()
+
+
+def test_bending_alone_is_gradient_and_exercises_every_case():
+    # N = 8 uses Eqs. 12a-12e; springs and excluded volume off
+    rng = np.random.default_rng(5)
+    N, a = 8, 2.0
+    R = _chain(rng, N, 1, a, 0.5)
+    F = oracle.bead_forces(R, N, 1, a, 0.0, 1.3, 0.0)
+    h = 1e-6
+    for b in range(N):
+        for d in range(2):
+            Rp = R.copy(); Rp[b, d] += h
+            Rm = R.copy(); Rm[b, d] -= h
+            fd = -(oracle.bead_energy(Rp, N, 1, a, 0, 1.3, 0) - oracle.bead_energy(Rm, N, 1, a, 0, 1.3, 0)) / (2 * h)
+            assert abs(F[b, d] - fd) <= 1e-7 * np.abs(F).max()
+
+
+def test_straight_chain_at_rest_length_has_no_force():
+    N, a = 10, 4.0
+    R = np.array([[10.0 + 8.0 * i, 5.0] for i in range(N)])
+    F = oracle.bead_forces(R, N, 1, a, 50.0, 3.0, 2.0)
+    assert np.abs(F).max() == 0.0
+    # a bend raises the bending energy: -k_b sum t_i.t_{i+1} is minimal straight
+    Rb = R.copy(); Rb[5, 1] += 0.5
+    assert oracle.bead_energy(Rb, N, 1, a, 0, 3.0, 0) > oracle.bead_energy(R, N, 1, a, 0, 3.0, 0)
+
+
+def test_excluded_volume_only_for_non_bonded_overlap():
+    a = 2.0
+    # beads 0 and 2 of one fiber overlap (distance 1 < d = 4): repel
+    R = np.array([[0.0, 0.0], [3.0, 2.0], [1.0, 0.0]])
+    F = oracle.bead_forces(R, 3, 1, a, 0.0, 0.0, 5.0)
+    assert np.allclose(F[0], [-5.0 * 3.0, 0.0]) and np.allclose(F[2], [5.0 * 3.0, 0.0])
+    assert np.all(F[1] == 0.0)
+    # apart: zero exactly
+    R2 = np.array([[0.0, 0.0], [4.0, 0.0], [8.0, 0.0]])
+    assert np.abs(oracle.bead_forces(R2, 3, 1, a, 0.0, 0.0, 5.0)).max() == 0.0
+
+
+# ------------------------------------------------------------ phi, spreading, reduction
+def test_phi_profile_values():
+    a, xi, rcut, nx = 4.0, 1.0, 12.0, 100.0
+    assert math.isclose(oracle.phi(a, xi, rcut, nx, 10.0, 10.0, 10.0, 10.0), 0.5 * (math.tanh(4.0) + 1), rel_tol=1e-15)
+    assert math.isclose(oracle.phi(a, xi, rcut, nx, 14.0, 10.0, 10.0, 10.0), 0.5, rel_tol=1e-15)
+    assert oracle.phi(a, xi, rcut, nx, 22.0, 10.0, 10.0, 10.0) == 0.0
+    v = oracle.phi(a, xi, rcut, nx, 21.9, 10.0, 10.0, 10.0)
+    assert 0 < v < 2e-7
+    # periodic minimum image in x
+    assert oracle.phi(a, xi, rcut, nx, 99.5, 10.0, 1.5, 10.0) == oracle.phi(a, xi, rcut, nx, 3.5, 10.0, 1.5, 10.0)
+
+
+def test_spread_force_sums_to_bead_forces_and_viscosity_overlay():
+    rng = np.random.default_rng(31)
+    cfg = wl.random_fiber(rng, 64, 40, n_beads=6, a=2.0, xi=1.0, n_fibers=2, gx=0.0, gy=0.0)
+    s = oracle.Sim(cfg)
+    R, V, F, S = s.beads()
+    fx, fy, nu = s.overlay_fields()
+    # Eq. 4: each bead's phi_i F_i / int phi_i integrates back to F_i
+    assert abs(fx.sum() - F[:, 0].sum()) < 1e-13 * np.abs(F).max()
+    assert abs(fy.sum() - F[:, 1].sum()) < 1e-13 * np.abs(F).max()
+    # Eq. 1: fluid viscosity away from beads, ~ r_eta nu_f at bead centres
+    nu_f = s.derived()["nu_f"]
+    assert nu.min() == nu_f
+    j, i = int(R[0, 1]), int(R[0, 0]) % 64
+    assert nu[j, i] > 0.5 * cfg["visc_ratio"] * nu_f
+    # S_i, the lattice sum of phi, against the continuum integral of Eq. 2:
+    # phi = 1 / (1 + exp((r - a)/sigma)) with sigma = xi/2, so
+    # int phi dA = 2 pi sigma^2 (-Li2(-exp(a/sigma)))  (cutoff tail < 1e-6)
+    from scipy.special import spence
+    sig = cfg["xi"] / 2.0
+    exact = 2 * math.pi * sig * sig * (-spence(1.0 + math.exp(cfg["a"] / sig)))
+    assert np.all(np.abs(S / exact - 1) < 2e-3)
+
+
+def test_uniform_flow_gives_bead_velocity_exactly():
+    # walls moving with the fluid: uniform flow (U, 0) is an exact steady
+    # state; with no bead forces V_i must equal U to round-off (Eq. 5)
+    U = 0.013
+    cfg = wl.couette_only(40, 30, u=0.0, nu=0.2, init_couette=0)
+    cfg.update(u_bottom=U, u_top=U, n_beads=4, n_fibers=1, a=2.0, xi=1.0, k_s=0.0, k_b=0.0,
+               stiffness_K=0.0, k_ev=0.0, centres=[[20.0, 15.0]], theta0=[0.3])
+    s = oracle.Sim(cfg)
+    s.set_populations(np.broadcast_to(oracle.feq(1.0, U, 0.0)[:, None, None], (9, 30, 40)).copy())
+    R0 = s.beads()[0].copy()
+    s.step(6)
+    R, V, F, S = s.beads()
+    assert np.abs(V - [U, 0.0]).max() < 1e-16
+    assert np.abs(R - R0 - 5 * np.array([U, 0.0])).max() < 1e-13
+
+
+def test_support_integral_nearly_translation_invariant():
+    # lattice aliasing of int phi: a reported small number, not exact
+    vals = []
+    for dx in np.linspace(0, 1, 7):
+        cfg = wl.couette_only(64, 48, u=0.01, nu=0.2)
+        cfg.update(n_beads=1, n_fibers=1, a=4.0, xi=1.0, centres=[[30.0 + dx, 24.0 + 0.3 * dx]], theta0=[0.0])
+        vals.append(oracle.Sim(cfg).beads()[3][0])
+    vals = np.array(vals)
+    assert (vals.max() - vals.min()) / vals.mean() < 1e-3
+
+
+def test_derived_parameters_follow_definitions():
+    cfg = wl.single_fiber_small()
+    d = oracle.Sim(cfg).derived()
+    gd = 0.02 / 40
+    lc = 8 * 4.0
+    assert math.isclose(d["gamma_dot"], gd, rel_tol=1e-15)
+    assert math.isclose(d["nu_f"], gd * lc * lc / 1.0, rel_tol=1e-15)           # Re = gd lc^2 / nu
+    assert math.isclose(2 * d["k_b"] / (d["nu_f"] * gd * lc * lc), 3.3, rel_tol=1e-14)  # Eq. 18
