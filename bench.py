@@ -1,0 +1,308 @@
+"""Benchmark of the FPD-MRT time step (MLUPS and fraction of the HBM roofline).
+
+Workload: the two-fiber lattice, 4096 x 1024 cells, two 20-bead fibers
+(a = 4, xi = 1), r_eta = 50, K = 0.33, Re = 5, walls -/+0.01, seeded angles;
+synthetic, as the paper prints no input data.  One "step" is one full time
+step of the method (bead phase + fused collide/stream/bounce-back sweep).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision 0|1|2]
+    python bench.py --impl reference      # the FP64 CPU oracle on host cores
+
+Prints one JSON line (rank 0).  For N > 1 (torchrun) every rank runs its own
+instance of the workload (independent sweep points: weak scaling, no data
+exchange) and the value is the sum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import shutil
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PRECISION_NAMES = {0: "f64", 1: "f32", 2: "f32 (f16 storage)"}
+STORE_BYTES = {0: 8, 1: 4, 2: 2}
+L2_BYTES = 129 * 2 ** 20
+
+
+def measured_peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for name in ("fpd_lattice.cu", "fpd_device.cuh", "fpd_kernels.h"):
+        with open(os.path.join(ROOT, "paper_2212_14153_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(workload: str, precision: int):
+    """DRAM bytes per launch of the lattice kernel from the committed ncu
+    summary, if it was taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        e = d[f"{workload}:{precision}"]
+        if e.get("kernel_hash") != kernel_source_hash():
+            return None
+        return float(e["dram_bytes_per_launch_full"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.path = None
+        self.gpu = gpu_index
+        if shutil.which("nvidia-smi"):
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_gpu(args, rank: int, world: int):
+    import torch
+    from paper_2212_14153_gb300 import build, fpd, workloads
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    build.build()
+    cfg = workloads.two_fiber_large(seed=3 + rank, precision=args.precision)
+    cells = cfg["nx"] * cfg["ny"]
+    stream = torch.cuda.Stream()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    # ---- device-resident throughput (value) and live kernel timing
+    sim = fpd.Simulation(cfg, stream=stream.cuda_stream)
+    sim.step(args.warmup)
+    sim.sync()
+    sim.set_profiling(True)
+    barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local) if rank == 0 else None
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    sim.step(args.steps)
+    end.record(stream)
+    end.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    clocks = sampler.stop() if sampler else None
+    ms = start.elapsed_time(end)
+    kt = sim.kernel_times()
+    diag = sim.diag()
+    sim.close()
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    mlups = cells * args.steps * world / (ms * 1e-3) / 1e6
+
+    # ---- end to end through the public API with host buffers
+    e2e_steps = max(1, min(args.steps, args.e2e_steps))
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sim = fpd.Simulation(cfg, stream=stream.cuda_stream)
+    nb = sim.nb
+    for _ in range(e2e_steps):
+        sim.step(1)
+        R, V, F, S = sim.beads()
+    ux, uy, rho = sim.fields()
+    sim.close()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_mlups = cells * e2e_steps * world / e2e_s / 1e6
+    h2d_total = 200 + 8 * 2 * cfg["n_fibers"] * 2 + 8 * 2 * nb  # params, centres/angles, bead table
+    d2h_step = 8 * 7 * nb                                        # R, V, F, S every step
+    d2h_total = d2h_step * e2e_steps + 3 * 8 * cells             # + final u_x, u_y, rho
+
+    if rank == 0:
+        peaks = measured_peaks()
+        bpc = 18 * STORE_BYTES[args.precision]
+        lat_ms = kt["lattice_ms"] / max(kt["lattice_launches"], 1)
+        achieved = bpc * cells / (lat_ms * 1e-3) / 1e9
+        traffic = ncu_traffic(cfg["name"], args.precision)
+        gpu_launches = kt["lattice_launches"] + kt["bead_launches"]
+        line = {
+            "metric": "MLUPS (million lattice-cell updates per second) of the FPD-MRT step",
+            "value": round(mlups, 1),
+            "unit": "MLUPS",
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": ms / args.steps,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": {0: "f64", 1: "f32", 2: "f32"}[args.precision],
+            "data": "synthetic",
+            "config": {
+                "workload": cfg["name"], "nx": cfg["nx"], "ny": cfg["ny"], "fibers": cfg["n_fibers"],
+                "beads_per_fiber": cfg["n_beads"], "storage": {0: "f64", 1: "f32", 2: "f16x2^s"}[args.precision],
+                "bytes_per_cell_update": bpc, "per_gpu": "one independent instance",
+                "l2": f"state {bpc // 2 * cells / 2**20:.0f} MiB > 129 MiB L2, no flush",
+                "parallelism": f"replicas x{world}",
+            },
+            "roofline": {
+                "bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
+                "kernel": "k_lattice", "kernel_ms": lat_ms, "peak_source": peaks["source"],
+                "bead_kernel_ms": kt["bead_ms"] / max(kt["bead_launches"], 1),
+            },
+            "gpu_launches": gpu_launches,
+            "e2e": {"value": round(e2e_mlups, 1), "unit": "MLUPS", "h2d_bytes_per_step": h2d_total / e2e_steps,
+                    "d2h_bytes_per_step": d2h_total / e2e_steps, "steps": e2e_steps,
+                    "api": "fpd_create, fpd_step(1)+fpd_read_beads per step, fpd_read_fields, fpd_destroy"},
+            "clocks": clocks,
+            "mass_after": diag[0],
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(cfg, budget_s=args.cpu_seconds)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+# ------------------------------------------------------------------ CPU oracle
+def cpu_baseline(cfg: dict, budget_s: float = 12.0, steps: int | None = None) -> dict:
+    """The FP64 oracle, as it stands, on this host's cores: whole time steps of
+    the same workload until about budget_s seconds (or a fixed step count)."""
+    import oracle
+    cores = os.cpu_count() or 1
+    o = oracle.Sim(dict(cfg, threads=cores))
+    cells = cfg["nx"] * cfg["ny"]
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        o.step(1)
+        n += 1
+        el = time.perf_counter() - t0
+        if (steps is not None and n >= steps) or (steps is None and (el >= budget_s or n >= 1000)):
+            break
+    return {"value": round(cells * n / el / 1e6, 3), "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "sample": f"{n} full steps of {cfg['name']} ({cells} cells) in {el:.1f} s"}
+
+
+def run_reference(args, rank: int, world: int):
+    if rank != 0:
+        return
+    from paper_2212_14153_gb300 import workloads
+    import oracle
+    oracle.build()
+    cfg = workloads.two_fiber_large(precision=args.precision)
+    cores = os.cpu_count() or 1
+    o = oracle.Sim(dict(cfg, threads=cores))
+    cells = cfg["nx"] * cfg["ny"]
+    # each reference step is one full oracle time step of the same workload
+    ref_steps = max(1, min(args.steps, args.ref_steps))
+    ref_warm = max(0, min(args.warmup, 3))
+    o.step(ref_warm)
+    t0 = time.perf_counter()
+    o.step(ref_steps)
+    el = time.perf_counter() - t0
+    v = cells * ref_steps / el / 1e6
+    line = {
+        "metric": "MLUPS (million lattice-cell updates per second) of the FPD-MRT step",
+        "value": round(v, 3), "unit": "MLUPS", "n_gpus": world, "steps": ref_steps, "warmup": ref_warm,
+        "ms_per_step": el * 1e3 / ref_steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": cfg["name"], "nx": cfg["nx"], "ny": cfg["ny"], "fibers": cfg["n_fibers"],
+                   "beads_per_fiber": cfg["n_beads"], "storage": "f64 (A/B arrays)"},
+        "cpu_baseline": {"value": round(v, 3), "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                         "sample": f"{ref_steps} full steps of {cfg['name']} after {ref_warm} warm-up"},
+        "e2e": {"value": round(v, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10000)
+    ap.add_argument("--warmup", type=int, default=100)
+    ap.add_argument("--precision", type=int, default=1, choices=[0, 1, 2])
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=2000)
+    ap.add_argument("--ref-steps", type=int, default=20)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_gpu(args, rank, world)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,176 @@
+/*
+ * fpd.h -- C ABI of the GB300 (sm_103a) extended fluid-particle-dynamics
+ * (FPD) solver of arXiv 2212.14153: flexible bead-spring fibers in a confined
+ * Couette flow, computed with a D2Q9 multiple-relaxation-time lattice
+ * Boltzmann method in which every bead is a smoothed high-viscosity region.
+ *
+ * One call of fpd_step advances the method of Sec. 2.3 by one time step:
+ *   (3) of the previous step  V_i = int phi_i v / int phi_i  (Eq. 5) and
+ *       R_i <- R_i + dt V_i (forward Euler, dt = 1), skipped at step 0;
+ *   (1) phi_i from R_i (Eq. 2), bead forces F_i (Eqs. 11-12 + excluded
+ *       volume), force density f = sum_i phi_i F_i / int phi_i (Eq. 4),
+ *       viscosity eta = eta_f + sum_i (eta_s - eta_f) phi_i (Eq. 1);
+ *   (2) MRT collision with Guo forcing, streaming, and half-way moving-wall
+ *       bounce-back at y = 0 (speed u_bottom) and y = H (speed u_top), x
+ *       periodic (Sec. 4.1).
+ * Everything is in lattice units: dx = dt = 1, rho_0 = 1, c_s^2 = 1/3.
+ *
+ * Conventions of every entry point:
+ *  - Return value: an fpd_status (0 = FPD_OK, negative = error).  The text
+ *    of the last error of a handle is returned by fpd_last_error(handle);
+ *    fpd_last_error(NULL) returns the last error of fpd_create in the
+ *    calling thread.  No exception crosses this boundary.
+ *  - Host pointers are caller-owned and only read or written during the
+ *    call.  The library owns all device memory of a handle (allocated by
+ *    fpd_create, freed by fpd_destroy).
+ *  - Work runs on the CUDA stream given to fpd_create (NULL = the legacy
+ *    default stream).  fpd_step is asynchronous; the fpd_read_* calls and
+ *    fpd_sync synchronise the stream and report any device-side error.
+ *  - Handles are not thread-safe: one host thread at a time per handle.
+ */
+#ifndef FPD_H
+#define FPD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FPD_ABI_VERSION 1
+
+typedef enum {
+    FPD_OK = 0,
+    FPD_EINVAL = -1,   /* invalid argument or parameter set                 */
+    FPD_ENOMEM = -2,   /* device or host allocation failed                  */
+    FPD_ECUDA = -3,    /* a CUDA call failed (message has the CUDA error)   */
+    FPD_ETIMEOUT = -4, /* a bounded device-side wait gave up                */
+    FPD_ENAN = -5,     /* a non-finite value was found in the state         */
+    FPD_EBUSY = -6     /* no free slot or memory for the request            */
+} fpd_status;
+
+typedef enum {
+    FPD_F64 = 0,          /* FP64 storage and arithmetic (parity path)       */
+    FPD_F32 = 1,          /* FP32 storage of f_k - w_k, FP32 arithmetic      */
+    FPD_F32_F16STORE = 2  /* FP16 storage of (f_k - w_k) * 2^s_k, FP32 math  */
+} fpd_precision;
+
+typedef enum {
+    FPD_MRT_MAGIC = 0, /* s_e = s_eps = s_nu, (1/s_nu - 1/2)(1/s_q - 1/2) = 3/16 */
+    FPD_MRT_LL = 1,    /* constant s_e, s_eps, s_q (Lallemand-Luo set)        */
+    FPD_BGK = 2        /* every rate equal to s_nu (single relaxation time)   */
+} fpd_collision;
+
+/* Problem statement of Sec. 4.1 plus the numerical parameters of Sec. 2.
+ * Negative values select the documented default where one is stated. */
+typedef struct {
+    int32_t nx, ny;         /* lattice cells: L_x = nx (periodic), H = ny      */
+    double u_bottom;        /* wall speed at y = 0 (paper: -V0)                */
+    double u_top;           /* wall speed at y = H (paper: +V0)                */
+    double nu_f;            /* fluid kinematic viscosity; <= 0: from re        */
+    double re;              /* Re = gamma_dot l_c^2 / nu_f, gamma_dot =
+                               (u_top - u_bottom)/H, l_c = 2 a N; Re_ps = re/4 */
+    double visc_ratio;      /* r_eta = eta_s / eta_f (Eq. 1)                   */
+    double xi;              /* interface thickness of Eq. 2                    */
+    double bead_radius;     /* a; spring rest length l_0 = d = 2a              */
+    int32_t n_beads;        /* N beads per fiber (0: no fiber)                 */
+    int32_t n_fibers;       /* number of fibers                                */
+    double k_s;             /* spring constant of Eq. 9; < 0: 0.25 pi a^2 l0^2 */
+    double k_b;             /* bending constant of Eq. 9 (used if K <= 0)      */
+    double stiffness_K;     /* K = 2 k_b / (eta_f gamma_dot l_c^2) (Eq. 18);
+                               > 0 overrides k_b                               */
+    double k_ev;            /* excluded-volume stiffness; < 0: k_s / l0^2      */
+    double phi_cut;         /* phi = 0 where |r - R_i| >= a + phi_cut xi       */
+    double body_force_x;    /* uniform body-force density added to f           */
+    double body_force_y;
+    int32_t precision;      /* fpd_precision                                   */
+    int32_t collision;      /* fpd_collision                                   */
+    int32_t init_couette;   /* 1: start at equilibrium of the linear wall
+                               profile; 0: fluid at rest                       */
+    double s_e, s_eps, s_q; /* rates for FPD_MRT_LL                            */
+    const double *centre_xy;/* n_fibers x 2: fiber centres (ignored if bead_xy) */
+    const double *theta0;   /* n_fibers: fiber angles in radians               */
+    const double *bead_xy;  /* optional (n_fibers*n_beads) x 2 explicit R_i^0  */
+} fpd_params;
+
+typedef struct fpd_sim fpd_sim;
+
+/* ABI version (FPD_ABI_VERSION of the built library). */
+int fpd_version(void);
+
+/* Fill *p with defaults: 80 x 40, walls -/+0.01, re = 1, r_eta = 50, xi = 1,
+ * a = 2, no fiber, phi_cut = 8, FP64, magic MRT, Couette start. */
+void fpd_default_params(fpd_params *p);
+
+/* Validate p, derive nu_f, k_s, k_b, k_ev, allocate the state on the device,
+ * initialise the fluid (equilibrium at rho_0 = 1) and the fibers
+ * (R_i = c + (i - (N+1)/2) l_0 (cos theta, sin theta), i = 1..N, Sec. 4.1:
+ * fiber centred) and compute the first bead table.  stream: a cudaStream_t
+ * or NULL.  On success *out owns the state.  Errors: FPD_EINVAL (bad
+ * parameter, message names it), FPD_ENOMEM, FPD_ECUDA. */
+int fpd_create(const fpd_params *p, void *stream, fpd_sim **out);
+
+/* Enqueue n_steps >= 0 time steps (Sec. 2.3 items (1)-(3)).  Asynchronous:
+ * returns launch errors only. */
+int fpd_step(fpd_sim *s, int64_t n_steps);
+
+/* Block until all work of s has finished; report device-side errors. */
+int fpd_sync(fpd_sim *s);
+
+/* Copy the macroscopic fields to caller-owned host arrays of ny*nx doubles
+ * (row-major [j][i], cell centre (i + 1/2, j + 1/2)): velocity
+ * u = (sum_k f_k c_k + f/2) / rho with f the force density of the current
+ * bead table (the one used by the last collision), and rho = sum_k f_k.
+ * Any pointer may be NULL.  Synchronises. */
+int fpd_read_fields(fpd_sim *s, double *ux, double *uy, double *rho);
+
+/* Copy the bead table to caller-owned host arrays of n_fibers*n_beads
+ * entries (fiber-major): positions and velocities (x, y pairs) of the last
+ * advance (V = 0 before the first), forces F_i (Eqs. 11-12 + excluded
+ * volume, x, y pairs) and support integrals S_i = sum_x phi_i (one double
+ * each).  Positions are unwrapped in x.  Any pointer may be NULL.
+ * Synchronises. */
+int fpd_read_beads(fpd_sim *s, double *pos, double *vel, double *force, double *support);
+
+/* Copy the populations f_k (not the stored deviations) of the current time
+ * into a caller-owned host array of 9*ny*nx doubles, layout [k][j][i] with
+ * the velocity order (0,0) (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1) (-1,-1)
+ * (1,-1).  Synchronises. */
+int fpd_read_populations(fpd_sim *s, double *f);
+
+/* Replace the populations of the current time by a caller-owned host array
+ * of 9*ny*nx doubles (same layout as fpd_read_populations); stored at the
+ * handle's precision.  The bead table is unchanged.  Synchronises. */
+int fpd_write_populations(fpd_sim *s, const double *f);
+
+/* out[0] = total mass sum f, out[1..2] = momentum sum f c (without the half
+ * force), out[3] = completed steps.  FP64 reduction on the device.  Returns
+ * FPD_ENAN if the state holds a non-finite value.  Synchronises. */
+int fpd_diag(fpd_sim *s, double out[4]);
+
+/* Derived parameters: out[0] nu_f, [1] k_s, [2] k_b, [3] k_ev, [4] l_0,
+ * [5] support radius a + phi_cut xi, [6] gamma_dot, [7] stored bytes per
+ * cell update (2 x 9 x storage size). */
+int fpd_derived(const fpd_sim *s, double out[8]);
+
+/* Kernel timing (CUDA events around every launch on the handle's stream).
+ * on = 1 starts recording and clears the totals; 0 stops. */
+int fpd_set_profiling(fpd_sim *s, int on);
+
+/* Profiling totals: out[0] lattice-kernel milliseconds, out[1] lattice
+ * launches, out[2] bead-kernel milliseconds, out[3] bead launches.
+ * Synchronises. */
+int fpd_kernel_times(fpd_sim *s, double out[4]);
+
+/* Text of the last error on s (or of fpd_create in this thread if s is
+ * NULL); never NULL; valid until the next call on s. */
+const char *fpd_last_error(const fpd_sim *s);
+
+/* Free all device memory of s.  NULL-safe.  Synchronises. */
+int fpd_destroy(fpd_sim *s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FPD_H */

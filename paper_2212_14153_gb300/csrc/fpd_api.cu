@@ -1,0 +1,525 @@
+// fpd_api.cu -- the C ABI declared in include/fpd.h: parameter validation and
+// derivation, device state ownership, the per-step launch sequence, reads.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/fpd.h"
+#include "fpd_kernels.h"
+
+namespace {
+
+thread_local std::string g_create_error;
+
+}  // namespace
+
+struct fpd_sim {
+    fpd_params p{};
+    fpd::Inst inst{};
+    fpd::Inst *inst_d = nullptr;
+    int precision = 0;
+    size_t elem = 8;
+    void *pool = nullptr;           // 9 planes of pitch * ny elements
+    double *tabmem = nullptr;       // two bead tables
+    fpd::BeadTab tab[2]{};
+    unsigned *counters = nullptr;   // one per instance (bead-phase last-block)
+    double *scratch = nullptr;      // fields / populations / diagnostics
+    size_t scratch_bytes = 0;
+    cudaStream_t stream = nullptr;
+    int64_t nstep = 0;
+    double nu_f = 0, k_s = 0, k_b = 0, k_ev = 0, gamma_dot = 0;
+    std::string err;
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev_pool;
+    struct Rec {
+        cudaEvent_t a, b;
+        int kind;
+    };
+    std::vector<Rec> recs;
+    double ms[2] = {0, 0};
+    double launches[2] = {0, 0};
+};
+
+namespace {
+
+int fail(fpd_sim *s, int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (s) s->err = buf;
+    else g_create_error = buf;
+    return code;
+}
+
+int cuda_fail(fpd_sim *s, cudaError_t e, const char *what) {
+    return fail(s, FPD_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+size_t elem_size(int precision) { return precision == 0 ? 8 : (precision == 1 ? 4 : 2); }
+
+bool is_fin(double v) { return std::isfinite(v); }
+
+// Validate p and fill the derived constants (Sec. 2.3 and Eq. 18).
+int derive(fpd_sim *s, const fpd_params &p) {
+    if (p.nx < 1 || p.ny < 1) return fail(nullptr, FPD_EINVAL, "nx and ny must be >= 1 (got %d, %d)", p.nx, p.ny);
+    if ((int64_t)p.nx * p.ny > (int64_t)1 << 31)
+        return fail(nullptr, FPD_EINVAL, "lattice of %d x %d cells is too large", p.nx, p.ny);
+    if (p.precision < 0 || p.precision > 2) return fail(nullptr, FPD_EINVAL, "precision must be 0, 1 or 2");
+    if (p.collision < 0 || p.collision > 2) return fail(nullptr, FPD_EINVAL, "collision must be 0, 1 or 2");
+    if (p.n_beads < 0 || p.n_fibers < 0) return fail(nullptr, FPD_EINVAL, "n_beads and n_fibers must be >= 0");
+    const int nb = p.n_beads * p.n_fibers;
+    if (nb > fpd::kMaxBeads)
+        return fail(nullptr, FPD_EINVAL, "at most %d beads per simulation (got %d)", fpd::kMaxBeads, nb);
+    if (!is_fin(p.u_bottom) || !is_fin(p.u_top) || !is_fin(p.body_force_x) || !is_fin(p.body_force_y))
+        return fail(nullptr, FPD_EINVAL, "wall speeds and body force must be finite");
+    const double l0 = 2.0 * p.bead_radius;
+    const double gd = (p.u_top - p.u_bottom) / (double)p.ny;
+    const double lc = p.n_beads * l0;
+    double nu = p.nu_f;
+    if (!(nu > 0.0)) {
+        if (!(p.re > 0.0) || !(std::fabs(gd) > 0.0) || !(lc > 0.0))
+            return fail(nullptr, FPD_EINVAL,
+                        "nu_f <= 0 needs re > 0, moving walls and a fiber to derive nu_f = gamma_dot l_c^2 / re");
+        nu = std::fabs(gd) * lc * lc / p.re;
+    }
+    if (!is_fin(nu) || nu <= 0.0) return fail(nullptr, FPD_EINVAL, "fluid viscosity must be positive");
+    if (!(p.visc_ratio > 0.0) || !is_fin(p.visc_ratio)) return fail(nullptr, FPD_EINVAL, "visc_ratio must be > 0");
+    if (nb > 0) {
+        if (!(p.bead_radius > 0.0)) return fail(nullptr, FPD_EINVAL, "bead_radius must be > 0");
+        if (!(p.xi > 0.0)) return fail(nullptr, FPD_EINVAL, "xi must be > 0");
+        if (!(p.phi_cut > 0.0)) return fail(nullptr, FPD_EINVAL, "phi_cut must be > 0");
+        if (!p.bead_xy && (!p.centre_xy || !p.theta0))
+            return fail(nullptr, FPD_EINVAL, "fibers need centre_xy and theta0, or bead_xy");
+    }
+    s->nu_f = nu;
+    s->gamma_dot = gd;
+    s->k_s = (p.k_s < 0.0) ? 0.25 * M_PI * p.bead_radius * p.bead_radius * l0 * l0 : p.k_s;
+    s->k_b = (p.stiffness_K > 0.0) ? p.stiffness_K * nu * std::fabs(gd) * lc * lc / 2.0 : p.k_b;
+    s->k_ev = (p.k_ev < 0.0) ? s->k_s / (l0 * l0) : p.k_ev;
+
+    fpd::Inst &I = s->inst;
+    std::memset(&I, 0, sizeof I);
+    I.nx = p.nx;
+    I.ny = p.ny;
+    const size_t es = elem_size(p.precision);
+    const int align = (int)(128 / es);  // rows start on 128-byte boundaries
+    I.pitch = (p.nx + align - 1) / align * align;
+    I.precision = p.precision;
+    I.plane = (int64_t)I.pitch * p.ny;
+    I.pop_off = 0;
+    I.u_bot = p.u_bottom;
+    I.u_top = p.u_top;
+    I.nu_f = nu;
+    I.visc_ratio = p.visc_ratio;
+    I.a = p.bead_radius;
+    I.xi = p.xi > 0 ? p.xi : 1.0;
+    I.rcut = p.bead_radius + p.phi_cut * I.xi;
+    I.rcut2 = I.rcut * I.rcut;
+    I.l0 = l0;
+    I.gx = p.body_force_x;
+    I.gy = p.body_force_y;
+    I.k_s = s->k_s;
+    I.k_b = s->k_b;
+    I.k_ev = s->k_ev;
+    I.collision = p.collision;
+    I.n_beads = p.n_beads;
+    I.n_fibers = p.n_fibers;
+    I.nb = nb;
+    I.bead_off = 0;
+    I.s_e = p.s_e;
+    I.s_eps = p.s_eps;
+    I.s_q = p.s_q;
+    // FP16 storage scale: a power of two per plane (symmetric under k ->
+    // opp k) mapping w_k (6 U + 0.01), a bound of |f_k - w_k|, to 2^10.
+    const double U = std::fmax(std::fabs(p.u_bottom), std::fabs(p.u_top));
+    const double w[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+    for (int k = 0; k < 9; ++k) {
+        double sc = 1.0;
+        if (p.precision == 2) {
+            const double bound = w[k] * (6.0 * U + 0.01);
+            sc = std::ldexp(1.0, (int)std::floor(std::log2(1024.0 / bound)));
+        }
+        I.scale[k] = (float)sc;
+        I.inv_scale[k] = (float)(1.0 / sc);
+    }
+    return FPD_OK;
+}
+
+void free_all(fpd_sim *s) {
+    if (!s) return;
+    cudaFree(s->pool);
+    cudaFree(s->tabmem);
+    cudaFree(s->counters);
+    cudaFree(s->scratch);
+    cudaFree(s->inst_d);
+    for (auto e : s->ev_pool) cudaEventDestroy(e);
+    for (auto &r : s->recs) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    s->pool = s->tabmem = s->scratch = nullptr;
+}
+
+int ensure_scratch(fpd_sim *s, size_t bytes) {
+    if (s->scratch_bytes >= bytes) return FPD_OK;
+    cudaFree(s->scratch);
+    s->scratch = nullptr;
+    s->scratch_bytes = 0;
+    cudaError_t e = cudaMalloc(&s->scratch, bytes);
+    if (e != cudaSuccess) return fail(s, FPD_ENOMEM, "cudaMalloc of %zu scratch bytes: %s", bytes, cudaGetErrorString(e));
+    s->scratch_bytes = bytes;
+    return FPD_OK;
+}
+
+cudaEvent_t take_event(fpd_sim *s) {
+    if (!s->ev_pool.empty()) {
+        cudaEvent_t e = s->ev_pool.back();
+        s->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void harvest(fpd_sim *s) {
+    for (auto &r : s->recs) {
+        float ms = 0.f;
+        cudaEventSynchronize(r.b);
+        cudaEventElapsedTime(&ms, r.a, r.b);
+        s->ms[r.kind] += ms;
+        s->launches[r.kind] += 1;
+        s->ev_pool.push_back(r.a);
+        s->ev_pool.push_back(r.b);
+    }
+    s->recs.clear();
+}
+
+// current bead table: the one that drove the last collision (step 0: the
+// initial table)
+int cur_tab(const fpd_sim *s) { return s->nstep == 0 ? 0 : (int)((s->nstep - 1) & 1); }
+
+}  // namespace
+
+extern "C" {
+
+int fpd_version(void) { return FPD_ABI_VERSION; }
+
+void fpd_default_params(fpd_params *p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof *p);
+    p->nx = 80;
+    p->ny = 40;
+    p->u_bottom = -0.01;
+    p->u_top = 0.01;
+    p->nu_f = -1.0;
+    p->re = 1.0;
+    p->visc_ratio = 50.0;
+    p->xi = 1.0;
+    p->bead_radius = 2.0;
+    p->k_s = -1.0;
+    p->k_ev = -1.0;
+    p->phi_cut = 8.0;
+    p->precision = FPD_F64;
+    p->collision = FPD_MRT_MAGIC;
+    p->init_couette = 1;
+    p->s_e = 1.64;
+    p->s_eps = 1.54;
+    p->s_q = 1.9;
+}
+
+int fpd_create(const fpd_params *p, void *stream, fpd_sim **out) {
+    if (!p || !out) return fail(nullptr, FPD_EINVAL, "fpd_create: NULL argument");
+    *out = nullptr;
+    fpd_sim *s = new (std::nothrow) fpd_sim();
+    if (!s) return fail(nullptr, FPD_ENOMEM, "host allocation failed");
+    int rc = derive(s, *p);
+    if (rc != FPD_OK) {
+        delete s;
+        return rc;
+    }
+    s->p = *p;
+    s->p.centre_xy = s->p.theta0 = s->p.bead_xy = nullptr;
+    s->precision = p->precision;
+    s->elem = elem_size(p->precision);
+    s->stream = (cudaStream_t)stream;
+    const fpd::Inst &I = s->inst;
+    const int nb = I.nb;
+    cudaError_t e;
+#define FPD_TRY(call, what)                                 \
+    do {                                                    \
+        e = (call);                                         \
+        if (e != cudaSuccess) {                             \
+            int code = (e == cudaErrorMemoryAllocation) ? FPD_ENOMEM : FPD_ECUDA; \
+            fail(nullptr, code, "%s: %s", what, cudaGetErrorString(e)); \
+            free_all(s);                                    \
+            delete s;                                       \
+            return code;                                    \
+        }                                                   \
+    } while (0)
+    FPD_TRY(cudaMalloc(&s->pool, 9 * (size_t)I.plane * s->elem), "cudaMalloc populations");
+    FPD_TRY(cudaMemsetAsync(s->pool, 0, 9 * (size_t)I.plane * s->elem, s->stream), "cudaMemset populations");
+    const int nbm = nb > 0 ? nb : 1;
+    // two bead tables: 9 doubles then 6 floats per bead each
+    const size_t tab_bytes = (size_t)nbm * (fpd::kTabDoubles * sizeof(double) + fpd::kTabFloats * sizeof(float));
+    FPD_TRY(cudaMalloc(&s->tabmem, 2 * tab_bytes), "cudaMalloc bead tables");
+    FPD_TRY(cudaMemsetAsync(s->tabmem, 0, 2 * tab_bytes, s->stream), "cudaMemset tables");
+    for (int t = 0; t < 2; ++t) {
+        double *b = (double *)((char *)s->tabmem + t * tab_bytes);
+        float *f = (float *)(b + fpd::kTabDoubles * nbm);
+        s->tab[t] = fpd::BeadTab{b,           b + nbm,     b + 2 * nbm, b + 3 * nbm, b + 4 * nbm,
+                                 b + 5 * nbm, b + 6 * nbm, b + 7 * nbm, b + 8 * nbm, f,
+                                 f + nbm,     f + 2 * nbm, f + 3 * nbm, f + 4 * nbm, f + 5 * nbm};
+    }
+    FPD_TRY(cudaMalloc(&s->counters, sizeof(unsigned)), "cudaMalloc counters");
+    FPD_TRY(cudaMemsetAsync(s->counters, 0, sizeof(unsigned), s->stream), "cudaMemset counters");
+    FPD_TRY(cudaMalloc(&s->inst_d, sizeof(fpd::Inst)), "cudaMalloc instance");
+    FPD_TRY(cudaMemcpyAsync(s->inst_d, &I, sizeof I, cudaMemcpyHostToDevice, s->stream), "copy instance");
+    FPD_TRY(fpd::launch_init(s->precision, s->inst_d, I, s->pool, p->init_couette, s->stream), "init kernel");
+    if (nb > 0) {
+        // initial bead positions: R_i = c + (i - (N+1)/2) l0 (cos t, sin t)
+        std::vector<double> R(2 * nb);
+        if (p->bead_xy) {
+            for (int b = 0; b < 2 * nb; ++b) R[b] = p->bead_xy[b];
+        } else {
+            for (int f = 0; f < p->n_fibers; ++f)
+                for (int i = 1; i <= p->n_beads; ++i) {
+                    const double off = (i - (p->n_beads + 1) / 2.0) * I.l0;
+                    const int b = f * p->n_beads + i - 1;
+                    R[2 * b] = p->centre_xy[2 * f] + off * std::cos(p->theta0[f]);
+                    R[2 * b + 1] = p->centre_xy[2 * f + 1] + off * std::sin(p->theta0[f]);
+                }
+        }
+        for (int b = 0; b < 2 * nb; ++b)
+            if (!is_fin(R[b])) {
+                free_all(s);
+                delete s;
+                return fail(nullptr, FPD_EINVAL, "bead positions must be finite");
+            }
+        std::vector<double> Rx(nb), Ry(nb);
+        for (int b = 0; b < nb; ++b) {
+            Rx[b] = R[2 * b];
+            Ry[b] = R[2 * b + 1];
+        }
+        FPD_TRY(cudaMemcpyAsync(s->tab[0].Rx, Rx.data(), nb * sizeof(double), cudaMemcpyHostToDevice, s->stream),
+                "copy beads");
+        FPD_TRY(cudaMemcpyAsync(s->tab[0].Ry, Ry.data(), nb * sizeof(double), cudaMemcpyHostToDevice, s->stream),
+                "copy beads");
+        FPD_TRY(fpd::launch_beads(s->precision, s->inst_d, nullptr, nb, s->pool, s->tab[0], s->tab[0], 0, 0,
+                                  s->counters, s->stream),
+                "initial bead table");
+    }
+    FPD_TRY(cudaStreamSynchronize(s->stream), "fpd_create");
+#undef FPD_TRY
+    *out = s;
+    return FPD_OK;
+}
+
+int fpd_step(fpd_sim *s, int64_t n_steps) {
+    if (!s) return fail(nullptr, FPD_EINVAL, "fpd_step: NULL handle");
+    if (n_steps < 0) return fail(s, FPD_EINVAL, "n_steps must be >= 0");
+    const fpd::Inst &I = s->inst;
+    for (int64_t t = 0; t < n_steps; ++t) {
+        const int parity = (int)(s->nstep & 1);
+        const int tnew = (int)(s->nstep & 1);
+        cudaError_t e;
+        if (I.nb > 0 && s->nstep >= 1) {
+            cudaEvent_t a = nullptr, b = nullptr;
+            if (s->profiling) {
+                a = take_event(s);
+                b = take_event(s);
+                cudaEventRecord(a, s->stream);
+            }
+            e = fpd::launch_beads(s->precision, s->inst_d, nullptr, I.nb, s->pool, s->tab[tnew ^ 1], s->tab[tnew],
+                                  parity, 1, s->counters, s->stream);
+            if (e != cudaSuccess) return cuda_fail(s, e, "bead kernel launch");
+            if (s->profiling) {
+                cudaEventRecord(b, s->stream);
+                s->recs.push_back({a, b, 1});
+            }
+        }
+        cudaEvent_t a = nullptr, b = nullptr;
+        if (s->profiling) {
+            a = take_event(s);
+            b = take_event(s);
+            cudaEventRecord(a, s->stream);
+        }
+        e = fpd::launch_lattice(s->precision, s->inst_d, I, s->pool, s->tab[tnew], parity, s->stream);
+        if (e != cudaSuccess) return cuda_fail(s, e, "lattice kernel launch");
+        if (s->profiling) {
+            cudaEventRecord(b, s->stream);
+            s->recs.push_back({a, b, 0});
+            if (s->recs.size() > 4096) harvest(s);
+        }
+        s->nstep++;
+    }
+    return FPD_OK;
+}
+
+int fpd_sync(fpd_sim *s) {
+    if (!s) return fail(nullptr, FPD_EINVAL, "fpd_sync: NULL handle");
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "stream synchronize");
+    return FPD_OK;
+}
+
+int fpd_read_fields(fpd_sim *s, double *ux, double *uy, double *rho) {
+    if (!s) return fail(nullptr, FPD_EINVAL, "fpd_read_fields: NULL handle");
+    const fpd::Inst &I = s->inst;
+    const size_t n = (size_t)I.nx * I.ny;
+    int rc = ensure_scratch(s, 3 * n * sizeof(double));
+    if (rc) return rc;
+    cudaError_t e = fpd::launch_fields(s->precision, s->inst_d, I, s->pool, s->tab[cur_tab(s)], (int)(s->nstep & 1),
+                                       s->scratch, s->scratch + n, s->scratch + 2 * n, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "fields kernel");
+    double *dst[3] = {ux, uy, rho};
+    for (int i = 0; i < 3; ++i)
+        if (dst[i]) {
+            e = cudaMemcpyAsync(dst[i], s->scratch + i * n, n * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+            if (e != cudaSuccess) return cuda_fail(s, e, "copy fields");
+        }
+    return fpd_sync(s);
+}
+
+int fpd_read_beads(fpd_sim *s, double *pos, double *vel, double *force, double *support) {
+    if (!s) return fail(nullptr, FPD_EINVAL, "fpd_read_beads: NULL handle");
+    const int nb = s->inst.nb;
+    int rc = fpd_sync(s);
+    if (rc) return rc;
+    if (nb == 0) return FPD_OK;
+    const fpd::BeadTab &t = s->tab[cur_tab(s)];
+    std::vector<double> a(nb), b(nb);
+    auto pair = [&](double *dst, const double *dx, const double *dy) -> int {
+        if (!dst) return FPD_OK;
+        cudaError_t e = cudaMemcpy(a.data(), dx, nb * sizeof(double), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(b.data(), dy, nb * sizeof(double), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(s, e, "copy beads");
+        for (int i = 0; i < nb; ++i) {
+            dst[2 * i] = a[i];
+            dst[2 * i + 1] = b[i];
+        }
+        return FPD_OK;
+    };
+    if ((rc = pair(pos, t.Rx, t.Ry))) return rc;
+    // the initial table keeps V = 0 until the second step overwrites it
+    if ((rc = pair(vel, t.Vx, t.Vy))) return rc;
+    if ((rc = pair(force, t.Fx, t.Fy))) return rc;
+    if (support) {
+        cudaError_t e = cudaMemcpy(support, t.S, nb * sizeof(double), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(s, e, "copy support sums");
+    }
+    return FPD_OK;
+}
+
+int fpd_read_populations(fpd_sim *s, double *f) {
+    if (!s || !f) return fail(s, FPD_EINVAL, "fpd_read_populations: NULL argument");
+    const fpd::Inst &I = s->inst;
+    const size_t n = 9 * (size_t)I.nx * I.ny;
+    int rc = ensure_scratch(s, n * sizeof(double));
+    if (rc) return rc;
+    cudaError_t e = fpd::launch_read_pops(s->precision, s->inst_d, I, s->pool, (int)(s->nstep & 1), s->scratch,
+                                          s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "population read kernel");
+    e = cudaMemcpyAsync(f, s->scratch, n * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "copy populations");
+    return fpd_sync(s);
+}
+
+int fpd_write_populations(fpd_sim *s, const double *f) {
+    if (!s || !f) return fail(s, FPD_EINVAL, "fpd_write_populations: NULL argument");
+    const fpd::Inst &I = s->inst;
+    const size_t n = 9 * (size_t)I.nx * I.ny;
+    for (size_t i = 0; i < n; ++i)
+        if (!is_fin(f[i])) return fail(s, FPD_EINVAL, "populations must be finite");
+    int rc = ensure_scratch(s, n * sizeof(double));
+    if (rc) return rc;
+    cudaError_t e = cudaMemcpyAsync(s->scratch, f, n * sizeof(double), cudaMemcpyHostToDevice, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "copy populations");
+    e = fpd::launch_write_pops(s->precision, s->inst_d, I, s->pool, (int)(s->nstep & 1), s->scratch, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "population write kernel");
+    return fpd_sync(s);
+}
+
+int fpd_diag(fpd_sim *s, double out[4]) {
+    if (!s || !out) return fail(s, FPD_EINVAL, "fpd_diag: NULL argument");
+    const fpd::Inst &I = s->inst;
+    const int nb = fpd::diag_blocks(I);
+    int rc = ensure_scratch(s, 4 * (size_t)nb * sizeof(double));
+    if (rc) return rc;
+    cudaError_t e = fpd::launch_diag(s->precision, s->inst_d, I, s->pool, (int)(s->nstep & 1), s->scratch, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "diagnostics kernel");
+    std::vector<double> part(4 * (size_t)nb);
+    e = cudaMemcpyAsync(part.data(), s->scratch, part.size() * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "copy diagnostics");
+    if ((rc = fpd_sync(s))) return rc;
+    double m = 0, px = 0, py = 0, bad = 0;
+    for (int b = 0; b < nb; ++b) {
+        m += part[4 * b];
+        px += part[4 * b + 1];
+        py += part[4 * b + 2];
+        bad += part[4 * b + 3];
+    }
+    out[0] = (double)I.nx * I.ny + m;  // sum of w_k over cells is 1 per cell
+    out[1] = px;
+    out[2] = py;
+    out[3] = (double)s->nstep;
+    if (bad > 0 || !is_fin(m) || !is_fin(px) || !is_fin(py))
+        return fail(s, FPD_ENAN, "non-finite populations after %lld steps", (long long)s->nstep);
+    return FPD_OK;
+}
+
+int fpd_derived(const fpd_sim *s, double out[8]) {
+    if (!s || !out) return FPD_EINVAL;
+    out[0] = s->nu_f;
+    out[1] = s->k_s;
+    out[2] = s->k_b;
+    out[3] = s->k_ev;
+    out[4] = s->inst.l0;
+    out[5] = s->inst.rcut;
+    out[6] = s->gamma_dot;
+    out[7] = 18.0 * (double)s->elem;
+    return FPD_OK;
+}
+
+int fpd_set_profiling(fpd_sim *s, int on) {
+    if (!s) return fail(nullptr, FPD_EINVAL, "fpd_set_profiling: NULL handle");
+    harvest(s);
+    s->profiling = on != 0;
+    if (on) {
+        s->ms[0] = s->ms[1] = 0;
+        s->launches[0] = s->launches[1] = 0;
+    }
+    return FPD_OK;
+}
+
+int fpd_kernel_times(fpd_sim *s, double out[4]) {
+    if (!s || !out) return fail(s, FPD_EINVAL, "fpd_kernel_times: NULL argument");
+    harvest(s);
+    out[0] = s->ms[0];
+    out[1] = s->launches[0];
+    out[2] = s->ms[1];
+    out[3] = s->launches[1];
+    return FPD_OK;
+}
+
+const char *fpd_last_error(const fpd_sim *s) {
+    if (!s) return g_create_error.c_str();
+    return s->err.c_str();
+}
+
+int fpd_destroy(fpd_sim *s) {
+    if (!s) return FPD_OK;
+    cudaStreamSynchronize(s->stream);
+    free_all(s);
+    delete s;
+    return FPD_OK;
+}
+
+}  // extern "C"

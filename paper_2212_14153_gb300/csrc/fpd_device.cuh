@@ -1,0 +1,256 @@
+// fpd_device.cuh -- device-side building blocks of the FPD-MRT step:
+// D2Q9 constants, the in-place (AA) population access with half-way
+// moving-wall bounce-back, the bead support profile of Eq. 2 and the MRT
+// collision with Guo forcing written out in moment space.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fpd {
+
+// D2Q9 velocities in the order (0,0) (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1)
+// (-1,-1) (1,-1); weights 4/9, 1/9, 1/36.
+template <int k> struct Q {
+    static constexpr int cx = (k == 1 || k == 5 || k == 8) ? 1 : (k == 3 || k == 6 || k == 7) ? -1 : 0;
+    static constexpr int cy = (k == 2 || k == 5 || k == 6) ? 1 : (k == 4 || k == 7 || k == 8) ? -1 : 0;
+    static constexpr int opp = (k == 0) ? 0 : (k <= 4) ? ((k + 1) % 4 + 1) : ((k - 5 + 2) % 4 + 5);
+    static constexpr double w = (k == 0) ? 4.0 / 9.0 : (k <= 4) ? 1.0 / 9.0 : 1.0 / 36.0;
+};
+
+// Per-instance constants, device resident (an array of them for batches).
+struct Inst {
+    int32_t nx, ny, pitch, precision;
+    int64_t plane;        // elements per direction plane (pitch * ny)
+    int64_t pop_off;      // element offset of this instance's planes
+    double u_bot, u_top;  // wall speeds
+    double nu_f, visc_ratio, a, xi, rcut, rcut2, l0;
+    double gx, gy;        // uniform body force
+    double k_s, k_b, k_ev;
+    int32_t collision, n_beads, n_fibers, nb;
+    int32_t bead_off;     // offset of this instance's beads in the tables
+    int32_t pad_;
+    double s_e, s_eps, s_q;
+    float scale[9];       // FP16 storage: stored = (f_k - w_k) * scale[k]
+    float inv_scale[9];
+};
+
+// Bead table, structure of arrays.  FP64 state (Sec. 2.3 keeps R, V
+// off-lattice) plus an FP32 copy for the reduced-precision lattice sweep:
+// x wrapped into [0, nx) and both coordinates split as hi + lo floats.
+struct BeadTab {
+    double *Rx, *Ry, *Vx, *Vy, *Fx, *Fy, *S, *Gx, *Gy;  // G = F / S
+    float *xh, *xl, *yh, *yl, *gxf, *gyf;
+};
+constexpr int kTabDoubles = 9;  // per bead
+constexpr int kTabFloats = 6;
+
+// ---------------------------------------------------------------- storage
+template <class T> struct Store;
+template <> struct Store<double> {
+    static __device__ __forceinline__ double ld(const double *p, float) { return *p; }
+    static __device__ __forceinline__ void st(double *p, double v, float) { *p = v; }
+};
+template <> struct Store<float> {
+    static __device__ __forceinline__ float ld(const float *p, float) { return *p; }
+    static __device__ __forceinline__ void st(float *p, float v, float) { *p = v; }
+};
+template <> struct Store<__half> {
+    static __device__ __forceinline__ float ld(const __half *p, float inv_scale) {
+        return __half2float(*p) * inv_scale;
+    }
+    static __device__ __forceinline__ void st(__half *p, float v, float scale) {
+        *p = __float2half_rn(v * scale);
+    }
+};
+
+// -------------------------------------------------- AA-pattern population access
+// Storage A[k][y][x] holds deviations g_k = f_k - w_k.  With t the number of
+// completed steps, step t reads and writes:
+//   t even:  g_k(x) = A[k][x]               ->  A[opp k][x] = g*_k(x)
+//   t odd :  g_k(x) = A[opp k][x - c_k]     ->  A[k][x + c_k] = g*_k(x)
+// A neighbour beyond a wall is replaced by half-way bounce-back from the
+// same cell: arriving  g_k = g*_{opp k} + 6 w_k (c_k . u_w)  (read side of an
+// odd step) and leaving  g_{opp k} = g*_k - 6 w_k (c_k . u_w)  (write side).
+template <int k, class S, class R>
+__device__ __forceinline__ void load_one(const S *__restrict__ A, const Inst &I, int x, int y, int parity,
+                                         R &g) {
+    // FP16 storage: plane p is always encoded with scale[p] (scale[p] ==
+    // scale[opp p], so either content of a plane fits its range).
+    if (parity == 0) {
+        g = (R)Store<S>::ld(A + (int64_t)k * I.plane + (int64_t)y * I.pitch + x, I.inv_scale[k]);
+    } else {
+        const int ys = y - Q<k>::cy;
+        if (ys >= 0 && ys < I.ny) {
+            int xs = x - Q<k>::cx;
+            xs = (xs < 0) ? xs + I.nx : (xs >= I.nx ? xs - I.nx : xs);
+            g = (R)Store<S>::ld(A + (int64_t)Q<k>::opp * I.plane + (int64_t)ys * I.pitch + xs,
+                                I.inv_scale[Q<k>::opp]);
+        } else {
+            const double uw = (ys < 0) ? I.u_bot : I.u_top;
+            g = (R)Store<S>::ld(A + (int64_t)k * I.plane + (int64_t)y * I.pitch + x, I.inv_scale[k]) +
+                (R)(6.0 * Q<k>::w * Q<k>::cx * uw);
+        }
+    }
+}
+
+template <int k, class S, class R>
+__device__ __forceinline__ void store_one(S *__restrict__ A, const Inst &I, int x, int y, int parity, R g) {
+    if (parity == 0) {
+        Store<S>::st(A + (int64_t)Q<k>::opp * I.plane + (int64_t)y * I.pitch + x, g, I.scale[Q<k>::opp]);
+    } else {
+        const int yd = y + Q<k>::cy;
+        if (yd >= 0 && yd < I.ny) {
+            int xd = x + Q<k>::cx;
+            xd = (xd < 0) ? xd + I.nx : (xd >= I.nx ? xd - I.nx : xd);
+            Store<S>::st(A + (int64_t)k * I.plane + (int64_t)yd * I.pitch + xd, g, I.scale[k]);
+        } else {
+            const double uw = (yd < 0) ? I.u_bot : I.u_top;
+            Store<S>::st(A + (int64_t)Q<k>::opp * I.plane + (int64_t)y * I.pitch + x,
+                         g - (R)(6.0 * Q<k>::w * Q<k>::cx * uw), I.scale[Q<k>::opp]);
+        }
+    }
+}
+
+template <class S, class R>
+__device__ __forceinline__ void load_pops(const S *__restrict__ A, const Inst &I, int x, int y, int parity,
+                                          R g[9]) {
+    load_one<0>(A, I, x, y, parity, g[0]);
+    load_one<1>(A, I, x, y, parity, g[1]);
+    load_one<2>(A, I, x, y, parity, g[2]);
+    load_one<3>(A, I, x, y, parity, g[3]);
+    load_one<4>(A, I, x, y, parity, g[4]);
+    load_one<5>(A, I, x, y, parity, g[5]);
+    load_one<6>(A, I, x, y, parity, g[6]);
+    load_one<7>(A, I, x, y, parity, g[7]);
+    load_one<8>(A, I, x, y, parity, g[8]);
+}
+
+template <class S, class R>
+__device__ __forceinline__ void store_pops(S *__restrict__ A, const Inst &I, int x, int y, int parity,
+                                           const R g[9]) {
+    store_one<0>(A, I, x, y, parity, g[0]);
+    store_one<1>(A, I, x, y, parity, g[1]);
+    store_one<2>(A, I, x, y, parity, g[2]);
+    store_one<3>(A, I, x, y, parity, g[3]);
+    store_one<4>(A, I, x, y, parity, g[4]);
+    store_one<5>(A, I, x, y, parity, g[5]);
+    store_one<6>(A, I, x, y, parity, g[6]);
+    store_one<7>(A, I, x, y, parity, g[7]);
+    store_one<8>(A, I, x, y, parity, g[8]);
+}
+
+// ---------------------------------------------------------------- Eq. 2
+// Minimum-image separation in x and the hard support cutoff, with every
+// rounding spelled out (no contraction), so that the cutoff decision and the
+// distance equal those of a plain IEEE evaluation.
+__device__ __forceinline__ double min_image_rn(double d, double L) {
+    return __dsub_rn(d, __dmul_rn(L, floor(__dadd_rn(__ddiv_rn(d, L), 0.5))));
+}
+
+// phi_i at cell centre (xc, yc) of bead (Rx, Ry); 0 beyond the cutoff.
+__device__ __forceinline__ double phi_f64(const Inst &I, double xc, double yc, double Rx, double Ry) {
+    const double dx = min_image_rn(__dsub_rn(xc, Rx), (double)I.nx);
+    const double dy = __dsub_rn(yc, Ry);
+    const double r2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+    if (!(r2 < I.rcut2)) return 0.0;
+    const double r = sqrt(r2);
+    return 0.5 * (tanh((I.a - r) / I.xi) + 1.0);
+}
+
+// FP32 variant for the reduced-precision lattice path: dx, dy relative to a
+// tile origin already reduced to small numbers by the caller.
+__device__ __forceinline__ float phi_f32(float dx, float dy, float a, float inv_xi, float rcut2) {
+    const float r2 = dx * dx + dy * dy;
+    if (!(r2 < rcut2)) return 0.0f;
+    const float r = sqrtf(r2);
+    return 0.5f * (tanhf((a - r) * inv_xi) + 1.0f);
+}
+
+// ---------------------------------------------------------------- collision
+// MRT collision with Guo forcing on deviations g_k = f_k - w_k (rho_0 = 1).
+// Moments in the Lallemand-Luo basis (rho, e, eps, jx, qx, jy, qy, pxx, pxy),
+// with m = M g + (1, -2, 1, 0, ...).  With u = (j + F/2) / rho:
+//   m* = m - S (m - m_eq) + (I - S/2) M F_guo,   g* = M^-1 (m* - m_rest),
+// M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4).
+// Rates: s_e, s_eps, s_q as given, s_nu from the local viscosity.
+template <class R>
+__device__ __forceinline__ void collide(R g[9], R Fx, R Fy, R s_nu, R s_e, R s_eps, R s_q) {
+    const R g1 = g[1], g2 = g[2], g3 = g[3], g4 = g[4];
+    const R g5 = g[5], g6 = g[6], g7 = g[7], g8 = g[8];
+    const R ax = g1 + g2 + g3 + g4, dg = g5 + g6 + g7 + g8;
+    const R drho = g[0] + ax + dg;
+    const R e = (R)-4 * g[0] - ax + (R)2 * dg;
+    const R eps = (R)4 * g[0] - (R)2 * ax + dg;
+    const R d57 = g5 - g7, d68 = g6 - g8;
+    const R jx = g1 - g3 + d57 - d68;
+    const R jy = g2 - g4 + d57 + d68;
+    const R qx = (R)-2 * (g1 - g3) + d57 - d68;
+    const R qy = (R)-2 * (g2 - g4) + d57 + d68;
+    const R pxx = g1 - g2 + g3 - g4;
+    const R pxy = g5 - g6 + g7 - g8;
+
+    const R rho = (R)1 + drho;
+    const R irho = (R)1 / rho;
+    const R ux = (jx + (R)0.5 * Fx) * irho;
+    const R uy = (jy + (R)0.5 * Fy) * irho;
+    const R rux = rho * ux, ruy = rho * uy;
+    const R u2r = rho * (ux * ux + uy * uy);
+    const R uF = ux * Fx + uy * Fy;
+
+    // post-collision deviation moments
+    const R e_s = e - s_e * (e + (R)2 * drho - (R)3 * u2r) + ((R)1 - (R)0.5 * s_e) * (R)6 * uF;
+    const R eps_s = eps - s_eps * (eps - drho + (R)3 * u2r) - ((R)1 - (R)0.5 * s_eps) * (R)6 * uF;
+    const R jx_s = jx + Fx;
+    const R jy_s = jy + Fy;
+    const R qx_s = qx - s_q * (qx + rux) - ((R)1 - (R)0.5 * s_q) * Fx;
+    const R qy_s = qy - s_q * (qy + ruy) - ((R)1 - (R)0.5 * s_q) * Fy;
+    const R hn = (R)1 - (R)0.5 * s_nu;
+    const R pxx_s = pxx - s_nu * (pxx - rux * ux + ruy * uy) + hn * (R)2 * (ux * Fx - uy * Fy);
+    const R pxy_s = pxy - s_nu * (pxy - rux * uy) + hn * (ux * Fy + uy * Fx);
+
+    // back to populations: g*_k = sum_r M[r][k] m*_r / |M_r|^2
+    const R a0 = drho * (R)(1.0 / 9.0);
+    const R a1 = e_s * (R)(1.0 / 36.0);
+    const R a2 = eps_s * (R)(1.0 / 36.0);
+    const R a3 = jx_s * (R)(1.0 / 6.0);
+    const R a4 = qx_s * (R)(1.0 / 12.0);
+    const R a5 = jy_s * (R)(1.0 / 6.0);
+    const R a6 = qy_s * (R)(1.0 / 12.0);
+    const R a7 = pxx_s * (R)0.25;
+    const R a8 = pxy_s * (R)0.25;
+
+    const R base_ax = a0 - a1 - (R)2 * a2;
+    const R base_dg = a0 + (R)2 * a1 + a2;
+    const R xa = a3 - (R)2 * a4, ya = a5 - (R)2 * a6;
+    const R xd = a3 + a4, yd = a5 + a6;
+    g[0] = a0 - (R)4 * a1 + (R)4 * a2;
+    g[1] = base_ax + xa + a7;
+    g[2] = base_ax + ya - a7;
+    g[3] = base_ax - xa + a7;
+    g[4] = base_ax - ya - a7;
+    g[5] = base_dg + xd + yd + a8;
+    g[6] = base_dg - xd + yd - a8;
+    g[7] = base_dg - xd - yd + a8;
+    g[8] = base_dg + xd - yd - a8;
+}
+
+// Relaxation rates of one cell from its kinematic viscosity (Eq. 1 gives nu).
+template <class R>
+__device__ __forceinline__ void rates(int collision, R nu, R s_e_ll, R s_eps_ll, R s_q_ll, R &s_nu, R &s_e,
+                                      R &s_eps, R &s_q) {
+    s_nu = (R)1 / ((R)3 * nu + (R)0.5);
+    if (collision == 1) {
+        s_e = s_e_ll;
+        s_eps = s_eps_ll;
+        s_q = s_q_ll;
+    } else if (collision == 2) {
+        s_e = s_eps = s_q = s_nu;
+    } else {
+        s_e = s_eps = s_nu;
+        s_q = (R)1 / ((R)0.5 + (R)0.1875 / ((R)1 / s_nu - (R)0.5));
+    }
+}
+
+}  // namespace fpd

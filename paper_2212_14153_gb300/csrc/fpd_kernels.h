@@ -1,0 +1,43 @@
+// fpd_kernels.h -- host-side launch wrappers of the FPD kernels (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "fpd_device.cuh"
+
+namespace fpd {
+
+constexpr int kTileX = 32;       // lattice tile: 32 x 8 cells, one thread each
+constexpr int kTileY = 8;
+constexpr int kMaxBeads = 256;   // beads per instance (shared-memory tables)
+constexpr int kBeadThreads = 256;
+
+// One fused collide-stream-bounce-back sweep of a single instance (Sec. 2.3
+// item (2) with the item-(1) overlay of Eqs. 1, 2, 4 evaluated in hot tiles).
+cudaError_t launch_lattice(int precision, const Inst *inst_d, const Inst &inst_h, void *pool, BeadTab tab,
+                           int parity, cudaStream_t st);
+
+// Bead phase (items (3) then (1)): one CTA per bead.  advance = 0 only
+// computes S and F of tab_new from its own R (initialisation).
+cudaError_t launch_beads(int precision, const Inst *inst_d, const int *bead_inst, int nb_total,
+                         const void *pool, BeadTab tab_old, BeadTab tab_new, int parity, int advance,
+                         unsigned *counters, cudaStream_t st);
+
+cudaError_t launch_init(int precision, const Inst *inst_d, const Inst &inst_h, void *pool, int couette,
+                        cudaStream_t st);
+
+cudaError_t launch_fields(int precision, const Inst *inst_d, const Inst &inst_h, const void *pool, BeadTab tab,
+                          int parity, double *ux, double *uy, double *rho, cudaStream_t st);
+
+cudaError_t launch_read_pops(int precision, const Inst *inst_d, const Inst &inst_h, const void *pool,
+                             int parity, double *f, cudaStream_t st);
+cudaError_t launch_write_pops(int precision, const Inst *inst_d, const Inst &inst_h, void *pool, int parity,
+                              const double *f, cudaStream_t st);
+
+// FP64 partial sums (mass, px, py, non-finite count) per block into
+// partial[4 * nblocks]; returns the number of blocks used.
+int diag_blocks(const Inst &inst_h);
+cudaError_t launch_diag(int precision, const Inst *inst_d, const Inst &inst_h, const void *pool, int parity,
+                        double *partial, cudaStream_t st);
+
+}  // namespace fpd

@@ -1,0 +1,270 @@
+"""ctypes binding of the C ABI in ``include/fpd.h`` (names kept identical).
+
+Argument marshalling only: every step of the method runs in the CUDA
+library ``libfpd.so``.  There is no CPU fallback; importing the binding on a
+machine without the built library, or calling it without a GPU, raises.
+PyTorch is used only to obtain the current CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfpd.so")
+
+FPD_OK, FPD_EINVAL, FPD_ENOMEM, FPD_ECUDA, FPD_ETIMEOUT, FPD_ENAN, FPD_EBUSY = 0, -1, -2, -3, -4, -5, -6
+FPD_F64, FPD_F32, FPD_F32_F16STORE = 0, 1, 2
+FPD_MRT_MAGIC, FPD_MRT_LL, FPD_BGK = 0, 1, 2
+
+_DP = ctypes.POINTER(ctypes.c_double)
+
+
+class fpd_params(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+        ("u_bottom", ctypes.c_double), ("u_top", ctypes.c_double),
+        ("nu_f", ctypes.c_double), ("re", ctypes.c_double),
+        ("visc_ratio", ctypes.c_double), ("xi", ctypes.c_double),
+        ("bead_radius", ctypes.c_double),
+        ("n_beads", ctypes.c_int32), ("n_fibers", ctypes.c_int32),
+        ("k_s", ctypes.c_double), ("k_b", ctypes.c_double),
+        ("stiffness_K", ctypes.c_double), ("k_ev", ctypes.c_double),
+        ("phi_cut", ctypes.c_double),
+        ("body_force_x", ctypes.c_double), ("body_force_y", ctypes.c_double),
+        ("precision", ctypes.c_int32), ("collision", ctypes.c_int32),
+        ("init_couette", ctypes.c_int32),
+        ("s_e", ctypes.c_double), ("s_eps", ctypes.c_double), ("s_q", ctypes.c_double),
+        ("centre_xy", _DP), ("theta0", _DP), ("bead_xy", _DP),
+    ]
+
+
+class FpdError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"fpd error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+_lock = threading.Lock()
+
+# name -> (restype, argtypes); every symbol include/fpd.h declares
+SIGNATURES = {
+    "fpd_version": (ctypes.c_int, []),
+    "fpd_default_params": (None, [ctypes.POINTER(fpd_params)]),
+    "fpd_create": (ctypes.c_int, [ctypes.POINTER(fpd_params), ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "fpd_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
+    "fpd_sync": (ctypes.c_int, [ctypes.c_void_p]),
+    "fpd_read_fields": (ctypes.c_int, [ctypes.c_void_p, _DP, _DP, _DP]),
+    "fpd_read_beads": (ctypes.c_int, [ctypes.c_void_p, _DP, _DP, _DP, _DP]),
+    "fpd_read_populations": (ctypes.c_int, [ctypes.c_void_p, _DP]),
+    "fpd_write_populations": (ctypes.c_int, [ctypes.c_void_p, _DP]),
+    "fpd_diag": (ctypes.c_int, [ctypes.c_void_p, _DP]),
+    "fpd_derived": (ctypes.c_int, [ctypes.c_void_p, _DP]),
+    "fpd_set_profiling": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "fpd_kernel_times": (ctypes.c_int, [ctypes.c_void_p, _DP]),
+    "fpd_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "fpd_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+}
+
+
+def load_library(path: str = LIB_PATH):
+    """Load ``libfpd.so`` (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(path):
+                raise RuntimeError(f"CUDA library {path} is missing: run __graft_entry__.build() first")
+            lib = ctypes.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(_DP)
+
+
+def _check(rc: int, handle=None):
+    if rc != FPD_OK:
+        msg = load_library().fpd_last_error(handle)
+        raise FpdError(rc, msg.decode() if msg else "")
+
+
+# ------------------------------------------------------------ thin wrappers
+def fpd_version() -> int:
+    return load_library().fpd_version()
+
+
+def fpd_default_params() -> fpd_params:
+    p = fpd_params()
+    load_library().fpd_default_params(ctypes.byref(p))
+    return p
+
+
+def fpd_create(params: fpd_params, stream=None) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    rc = load_library().fpd_create(ctypes.byref(params), stream, ctypes.byref(h))
+    _check(rc, None)
+    return h
+
+
+def fpd_step(h, n_steps: int) -> None:
+    _check(load_library().fpd_step(h, int(n_steps)), h)
+
+
+def fpd_sync(h) -> None:
+    _check(load_library().fpd_sync(h), h)
+
+
+def fpd_read_fields(h, ux, uy, rho) -> None:
+    _check(load_library().fpd_read_fields(h, _ptr(ux), _ptr(uy), _ptr(rho)), h)
+
+
+def fpd_read_beads(h, pos, vel, force, support=None) -> None:
+    _check(load_library().fpd_read_beads(h, _ptr(pos), _ptr(vel), _ptr(force), _ptr(support)), h)
+
+
+def fpd_read_populations(h, f) -> None:
+    _check(load_library().fpd_read_populations(h, _ptr(f)), h)
+
+
+def fpd_write_populations(h, f) -> None:
+    _check(load_library().fpd_write_populations(h, _ptr(f)), h)
+
+
+def fpd_diag(h, out) -> None:
+    _check(load_library().fpd_diag(h, _ptr(out)), h)
+
+
+def fpd_derived(h, out) -> None:
+    _check(load_library().fpd_derived(h, _ptr(out)), h)
+
+
+def fpd_set_profiling(h, on: bool) -> None:
+    _check(load_library().fpd_set_profiling(h, 1 if on else 0), h)
+
+
+def fpd_kernel_times(h, out) -> None:
+    _check(load_library().fpd_kernel_times(h, _ptr(out)), h)
+
+
+def fpd_last_error(h=None) -> str:
+    msg = load_library().fpd_last_error(h)
+    return msg.decode() if msg else ""
+
+
+def fpd_destroy(h) -> None:
+    if h is not None and h.value:
+        load_library().fpd_destroy(h)
+
+
+# ------------------------------------------------------------ convenience
+def params_from_config(cfg: dict) -> tuple[fpd_params, list]:
+    """Fill fpd_params from a workload dict; returns the struct and the numpy
+    arrays it points to (keep them alive until fpd_create returns)."""
+    p = fpd_default_params()
+    simple = dict(nx="nx", ny="ny", u_bottom="u_bottom", u_top="u_top", nu_f="nu_f", re="re",
+                  visc_ratio="visc_ratio", xi="xi", a="bead_radius", n_beads="n_beads",
+                  n_fibers="n_fibers", k_s="k_s", k_b="k_b", stiffness_K="stiffness_K",
+                  k_ev="k_ev", phi_cut="phi_cut", gx="body_force_x", gy="body_force_y",
+                  precision="precision", collision="collision", init_couette="init_couette",
+                  s_e="s_e", s_eps="s_eps", s_q="s_q")
+    for k, field in simple.items():
+        if k in cfg:
+            setattr(p, field, cfg[k])
+    keep = []
+    nf = max(int(cfg.get("n_fibers", 0)), 1)
+    cen = np.ascontiguousarray(cfg.get("centres", np.zeros((nf, 2))), dtype=np.float64).reshape(-1)
+    th = np.ascontiguousarray(cfg.get("theta0", np.zeros(nf)), dtype=np.float64).reshape(-1)
+    keep += [cen, th]
+    p.centre_xy = _ptr(cen)
+    p.theta0 = _ptr(th)
+    if cfg.get("bead_xy") is not None:
+        bx = np.ascontiguousarray(cfg["bead_xy"], dtype=np.float64).reshape(-1)
+        keep.append(bx)
+        p.bead_xy = _ptr(bx)
+    return p, keep
+
+
+class Simulation:
+    """One FPD instance on the GPU, driven through the C ABI."""
+
+    def __init__(self, cfg: dict, stream=None):
+        if stream is None:
+            import torch
+            if not torch.cuda.is_available():
+                raise RuntimeError("no CUDA device: the FPD library runs on the GPU only")
+            stream = torch.cuda.current_stream().cuda_stream
+        self.cfg = dict(cfg)
+        p, keep = params_from_config(cfg)
+        self.h = fpd_create(p, stream)
+        self.nx, self.ny = p.nx, p.ny
+        self.nb = p.n_beads * p.n_fibers
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            fpd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n: int = 1):
+        fpd_step(self.h, n)
+
+    def sync(self):
+        fpd_sync(self.h)
+
+    def fields(self):
+        ux = np.zeros((self.ny, self.nx)); uy = np.zeros_like(ux); rho = np.zeros_like(ux)
+        fpd_read_fields(self.h, ux, uy, rho)
+        return ux, uy, rho
+
+    def beads(self):
+        n = max(self.nb, 1)
+        R = np.zeros((n, 2)); V = np.zeros((n, 2)); F = np.zeros((n, 2)); S = np.zeros(n)
+        fpd_read_beads(self.h, R, V, F, S)
+        k = self.nb
+        return R[:k], V[:k], F[:k], S[:k]
+
+    def populations(self):
+        f = np.zeros((9, self.ny, self.nx))
+        fpd_read_populations(self.h, f)
+        return f
+
+    def set_populations(self, f):
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        assert f.shape == (9, self.ny, self.nx)
+        fpd_write_populations(self.h, f)
+
+    def diag(self):
+        out = np.zeros(4)
+        fpd_diag(self.h, out)
+        return out
+
+    def derived(self) -> dict:
+        out = np.zeros(8)
+        fpd_derived(self.h, out)
+        keys = ["nu_f", "k_s", "k_b", "k_ev", "l0", "rcut", "gamma_dot", "bytes_per_cell"]
+        return dict(zip(keys, out.tolist()))
+
+    def set_profiling(self, on: bool):
+        fpd_set_profiling(self.h, on)
+
+    def kernel_times(self) -> dict:
+        out = np.zeros(4)
+        fpd_kernel_times(self.h, out)
+        return dict(lattice_ms=out[0], lattice_launches=int(out[1]), bead_ms=out[2], bead_launches=int(out[3]))

