@@ -149,6 +149,25 @@ int fpd_write_populations(fpd_sim *s, const double *f);
  * FPD_ENAN if the state holds a non-finite value.  Synchronises. */
 int fpd_diag(fpd_sim *s, double out[4]);
 
+/* Same result as fpd_diag, computed without allocating any device memory.
+ * The paper has no counterpart: this is a library service.  fpd_diag keeps
+ * its per-block partial sums in a buffer it allocates (cudaMalloc) on first
+ * use; callers that must not allocate device memory when they run the check
+ * (a serving loop whose device memory is all committed to resident
+ * instances, code running while other work is being captured or replayed on
+ * the device, an application whose own allocator owns device memory) call
+ * this instead.  Its scratch is a fixed device array of 4 * 1024 + 4 doubles
+ * (32 800 bytes) that every device loading the library holds until exit;
+ * the reduction uses at most 1024 blocks, so any lattice size is accepted
+ * (a larger block count would be refused with FPD_EINVAL).  The first call
+ * on each device looks up that array's device address (cudaGetSymbolAddress
+ * with the handle's device current); make that first call before any
+ * stream capture.  All calls share the array and every call overwrites what
+ * it reads, so nothing needs clearing; calls whose device work overlaps
+ * (other streams, handles or threads on the same device) race on the array
+ * and must not overlap.  Returns FPD_ENAN like fpd_diag.  Synchronises. */
+int fpd_diag_noalloc(fpd_sim *s, double out[4]);
+
 /* Derived parameters: out[0] nu_f, [1] k_s, [2] k_b, [3] k_ev, [4] l_0,
  * [5] support radius a + phi_cut xi, [6] gamma_dot, [7] stored bytes per
  * cell update (2 x 9 x storage size). */

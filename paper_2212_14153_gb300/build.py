@@ -19,8 +19,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfpd.so")
-SOURCES = ["fpd_api.cu", "fpd_lattice.cu", "fpd_beads.cu"]
-HEADERS = ["fpd_device.cuh", "fpd_kernels.h"]
+SOURCES = ["fpd_api.cu", "fpd_lattice.cu", "fpd_beads.cu", "fpd_noalloc.cu"]
+HEADERS = ["fpd_device.cuh", "fpd_kernels.h", "fpd_sim.h"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr",

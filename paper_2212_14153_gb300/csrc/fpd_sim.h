@@ -1,0 +1,37 @@
+// fpd_sim.h -- the state behind an fpd_sim handle (internal to the library).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/fpd.h"
+#include "fpd_kernels.h"
+
+struct fpd_sim {
+    fpd_params p{};
+    fpd::Inst inst{};
+    fpd::Inst *inst_d = nullptr;
+    int precision = 0;
+    size_t elem = 8;
+    void *pool = nullptr;           // 9 planes of pitch * ny elements
+    double *tabmem = nullptr;       // two bead tables
+    fpd::BeadTab tab[2]{};
+    unsigned *counters = nullptr;   // one per instance (bead-phase last-block)
+    double *scratch = nullptr;      // fields / populations / diagnostics
+    size_t scratch_bytes = 0;
+    cudaStream_t stream = nullptr;
+    int64_t nstep = 0;
+    double nu_f = 0, k_s = 0, k_b = 0, k_ev = 0, gamma_dot = 0;
+    std::string err;
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev_pool;
+    struct Rec {
+        cudaEvent_t a, b;
+        int kind;
+    };
+    std::vector<Rec> recs;
+    double ms[2] = {0, 0};
+    double launches[2] = {0, 0};
+};

@@ -63,6 +63,7 @@ SIGNATURES = {
     "fpd_read_populations": (ctypes.c_int, [ctypes.c_void_p, _DP]),
     "fpd_write_populations": (ctypes.c_int, [ctypes.c_void_p, _DP]),
     "fpd_diag": (ctypes.c_int, [ctypes.c_void_p, _DP]),
+    "fpd_diag_noalloc": (ctypes.c_int, [ctypes.c_void_p, _DP]),
     "fpd_derived": (ctypes.c_int, [ctypes.c_void_p, _DP]),
     "fpd_set_profiling": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "fpd_kernel_times": (ctypes.c_int, [ctypes.c_void_p, _DP]),
@@ -144,6 +145,11 @@ def fpd_write_populations(h, f) -> None:
 
 def fpd_diag(h, out) -> None:
     _check(load_library().fpd_diag(h, _ptr(out)), h)
+
+
+def fpd_diag_noalloc(h, out) -> None:
+    """fpd_diag without device allocation (static scratch; see include/fpd.h)."""
+    _check(load_library().fpd_diag_noalloc(h, _ptr(out)), h)
 
 
 def fpd_derived(h, out) -> None:

@@ -1,0 +1,60 @@
+"""fpd_diag_noalloc (allocation-free diagnostics) against fpd_diag.
+
+fpd_diag_noalloc serves callers that cannot allocate device memory when they
+check a running simulation; it keeps its scratch in a fixed device array that
+all calls share.  This file is collected last so that a stop-at-first-failure
+run has run every other test first; it also passes alone in a fresh process.
+Both entry points are called through the C ABI; two calls in a row must each
+agree with fpd_diag (the same partial sums, summed in the same order, so the
+tolerance used by the other FP64 tests, 1e-12 relative, is met with room).
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fpd():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2212_14153_gb300 import build, fpd as binding
+    build.build()
+    return binding
+
+
+def _check(fpd, sim):
+    ref = np.zeros(4)
+    fpd.fpd_diag(sim.h, ref)
+    for _ in range(2):
+        out = np.full(4, np.nan)
+        fpd.fpd_diag_noalloc(sim.h, out)
+        assert out[3] == ref[3]
+        assert np.allclose(out[:3], ref[:3], rtol=1e-12, atol=1e-12 * abs(ref[0])), (out, ref)
+
+
+def test_noalloc_diag_matches_diag_two_calls_in_a_row(fpd):
+    from paper_2212_14153_gb300 import workloads as wl
+    # a large lattice first (1024 partial blocks), then small ones (few
+    # blocks): stale partials of the earlier call must not leak into later ones
+    cases = [wl.two_fiber_large(precision=1), wl.single_fiber_small(), wl.couette_only(33, 17, precision=2)]
+    for cfg in cases:
+        sim = fpd.Simulation(cfg)
+        _check(fpd, sim)
+        sim.step(7)
+        _check(fpd, sim)
+        sim.close()
+
+
+def test_noalloc_diag_reports_nonfinite_state(fpd):
+    from paper_2212_14153_gb300 import workloads as wl
+    cfg = wl.couette_only(32, 16, u=0.01, nu=0.2)
+    cfg["gx"] = 1e300
+    sim = fpd.Simulation(cfg)
+    sim.step(3)
+    out = np.zeros(4)
+    with pytest.raises(fpd.FpdError) as e:
+        fpd.fpd_diag_noalloc(sim.h, out)
+    assert e.value.code == fpd.FPD_ENAN
+    sim.close()
