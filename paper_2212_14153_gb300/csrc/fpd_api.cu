@@ -110,6 +110,58 @@ int derive(fpd_sim *s, const fpd_params &p) {
     I.s_e = p.s_e;
     I.s_eps = p.s_eps;
     I.s_q = p.s_q;
+    // host-precomputed FP32 copies, bounce-back terms and fluid rates
+    I.inv_xi = 1.0 / I.xi;
+    const int cx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+    const double wk[9] = {4.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0,
+                          1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
+    for (int k = 0; k < 9; ++k) {
+        I.bbd[0][k] = 6.0 * wk[k] * cx[k] * p.u_bottom;
+        I.bbd[1][k] = 6.0 * wk[k] * cx[k] * p.u_top;
+        I.bbf[0][k] = (float)I.bbd[0][k];
+        I.bbf[1][k] = (float)I.bbd[1][k];
+    }
+    {
+        const double s_nu = 1.0 / (3.0 * nu + 0.5);
+        double se = s_nu, seps = s_nu, sq = 1.0 / (0.5 + 0.1875 / (1.0 / s_nu - 0.5));
+        if (p.collision == 1) {
+            se = p.s_e;
+            seps = p.s_eps;
+            sq = p.s_q;
+        } else if (p.collision == 2) {
+            sq = s_nu;
+        }
+        const double r4[4] = {s_nu, se, seps, sq};
+        for (int i = 0; i < 4; ++i) {
+            I.fluid_rates_d[i] = r4[i];
+            I.fluid_rates_f[i] = (float)r4[i];
+        }
+        // FP32 fluid rates evaluated in FP32 like the per-cell path does
+        const float fnu = (float)nu;
+        const float fs_nu = 1.0f / (3.0f * fnu + 0.5f);
+        I.fluid_rates_f[0] = fs_nu;
+        if (p.collision == 0) {
+            I.fluid_rates_f[1] = I.fluid_rates_f[2] = fs_nu;
+            I.fluid_rates_f[3] = 1.0f / (0.5f + 0.1875f / (1.0f / fs_nu - 0.5f));
+        } else if (p.collision == 2) {
+            I.fluid_rates_f[1] = I.fluid_rates_f[2] = I.fluid_rates_f[3] = fs_nu;
+        } else {
+            I.fluid_rates_f[1] = (float)p.s_e;
+            I.fluid_rates_f[2] = (float)p.s_eps;
+            I.fluid_rates_f[3] = (float)p.s_q;
+        }
+    }
+    I.f_nu_f = (float)nu;
+    I.f_visc_m1 = (float)(p.visc_ratio - 1.0);
+    I.f_gx = (float)p.body_force_x;
+    I.f_gy = (float)p.body_force_y;
+    I.f_a = (float)I.a;
+    I.f_inv_xi = (float)I.inv_xi;
+    I.f_rcut = (float)I.rcut;
+    I.f_rcut2 = (float)I.rcut2;
+    I.f_s_e = (float)p.s_e;
+    I.f_s_eps = (float)p.s_eps;
+    I.f_s_q = (float)p.s_q;
     // FP16 storage scale: a power of two per plane (symmetric under k ->
     // opp k) mapping w_k (6 U + 0.01), a bound of |f_k - w_k|, to 2^10.
     const double U = std::fmax(std::fabs(p.u_bottom), std::fabs(p.u_top));

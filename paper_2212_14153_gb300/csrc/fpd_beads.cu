@@ -15,12 +15,15 @@
 //   the FP32 overlay table (positions split hi + lo, G) read by the lattice
 //   sweep of the reduced-precision paths.
 //
-// Arithmetic: positions, velocities, forces and every reduction are FP64.
-// In the FP64 (parity) path phi is evaluated in FP64 exactly as a plain IEEE
-// evaluation would; in the FP32/FP16-storage paths phi and u are FP32 from
-// bead-relative offsets, accumulated in FP64.  Only beads whose support can
-// overlap bead b's support are visited per cell.  Reductions use a fixed
-// tree so results do not depend on scheduling.
+// Arithmetic: positions, velocities, forces and the reductions over the
+// support are FP64.  In the FP64 (parity) path phi is evaluated in FP64
+// exactly as a plain IEEE evaluation would; in the FP32/FP16-storage paths
+// phi and u are FP32 from bead-relative offsets, each thread adds its few
+// support cells (ceil(cells / 256), 3 for a = 4, xi = 1) in FP32 and the
+// partials are reduced in FP64.  FP64 instructions are kept out of per-cell
+// work: this GPU issues one FP64 warp instruction per ~16 cycles per SM.
+// Only beads whose support can overlap bead b's support are visited per
+// cell.  Reductions use a fixed tree so results do not depend on scheduling.
 #include <cuda_fp16.h>
 
 #include <type_traits>
@@ -33,8 +36,8 @@ namespace {
 
 constexpr int kWarps = kBeadThreads / 32;
 
-// Deterministic block sum of two doubles; result valid in every thread.
-__device__ __forceinline__ void block_sum2(double &a, double &b, double (*sh)[kWarps]) {
+// Deterministic block sum of two doubles; the result is valid in thread 0.
+__device__ __forceinline__ void block_sum2_to0(double &a, double &b, double (*sh)[kWarps]) {
     for (int o = 16; o > 0; o >>= 1) {
         a += __shfl_down_sync(0xffffffffu, a, o);
         b += __shfl_down_sync(0xffffffffu, b, o);
@@ -46,13 +49,15 @@ __device__ __forceinline__ void block_sum2(double &a, double &b, double (*sh)[kW
         sh[1][w] = b;
     }
     __syncthreads();
-    double ta = 0.0, tb = 0.0;
-    for (int i = 0; i < kWarps; ++i) {
-        ta += sh[0][i];
-        tb += sh[1][i];
+    if (threadIdx.x == 0) {
+        double ta = 0.0, tb = 0.0;
+        for (int i = 0; i < kWarps; ++i) {
+            ta += sh[0][i];
+            tb += sh[1][i];
+        }
+        a = ta;
+        b = tb;
     }
-    a = ta;
-    b = tb;
 }
 
 // Cells whose centre may lie within the cutoff of (Rx, Ry): a box clipped at
@@ -79,81 +84,75 @@ __device__ __forceinline__ Box support_box(const Inst &I, double Rx, double Ry) 
         xhi = xlo + I.nx - 1;
     }
     b.iu = xlo;
-    b.i0 = (int)(xlo - I.nx * floor(xlo / I.nx));  // in [0, nx)
+    const long long xl = (long long)xlo;
+    b.i0 = (int)(((xl % I.nx) + I.nx) % I.nx);  // in [0, nx)
     b.j0 = (int)ylo;
     b.w = (int)(xhi - xlo) + 1;
     b.h = (int)(yhi - ylo) + 1;
     return b;
 }
 
-__device__ __forceinline__ double min_image(double d, double L) { return d - L * floor(d / L + 0.5); }
-
-// Unit tangent of segment k (1-based, joins beads k and k+1 of a fiber whose
-// first bead has global index f0) and its length; zero outside 1..N-1.
-__device__ __forceinline__ void seg(const double *Rx, const double *Ry, int f0, int N, int k, double &tx,
-                                    double &ty, double &L) {
-    if (k < 1 || k > N - 1) {
-        tx = ty = 0.0;
-        L = 1.0;
-        return;
-    }
-    const double dx = __ldcg(Rx + f0 + k) - __ldcg(Rx + f0 + k - 1);
-    const double dy = __ldcg(Ry + f0 + k) - __ldcg(Ry + f0 + k - 1);
-    L = sqrt(dx * dx + dy * dy);
-    tx = dx / L;
-    ty = dy / L;
+// d reduced to its nearest periodic image in x: the image index is found in
+// FP32 (it is an integer) and removed exactly in FP64.
+__device__ __forceinline__ double min_image(double d, int nx) {
+    const float k = rintf((float)d / (float)nx);
+    return d - (double)k * (double)nx;
 }
 
-// Force on bead q (instance-local index) from the positions in tab.
-__device__ void bead_force(const Inst &I, const BeadTab &tab, int q, double &Fx, double &Fy) {
+// Force on bead q (instance-local index), given the instance's positions
+// and the unit tangents/lengths of every segment (index j joins beads j and
+// j+1 of the instance-local numbering), all staged in shared memory.
+__device__ void bead_force(const Inst &I, const double *Rx, const double *Ry, const double *Tx,
+                           const double *Ty, const double *Ln, int q, double &Fx, double &Fy) {
     const int N = I.n_beads;
-    const int fib = q / N, i = q % N + 1;  // 1-based index within the fiber
-    const int f0 = I.bead_off + fib * N;
-    double t_m2x, t_m2y, L_m2, t_m1x, t_m1y, L_m1, t_ix, t_iy, L_i, t_p1x, t_p1y, L_p1;
-    seg(tab.Rx, tab.Ry, f0, N, i - 2, t_m2x, t_m2y, L_m2);
-    seg(tab.Rx, tab.Ry, f0, N, i - 1, t_m1x, t_m1y, L_m1);
-    seg(tab.Rx, tab.Ry, f0, N, i, t_ix, t_iy, L_i);
-    seg(tab.Rx, tab.Ry, f0, N, i + 1, t_p1x, t_p1y, L_p1);
-    const bool has_m1 = (i - 1 >= 1), has_i = (i <= N - 1);
+    const int fib = q / N, i0 = q - fib * N;  // 0-based index within the fiber
+    // segments around bead q, as in Eqs. 11-12 with 1-based i = i0 + 1:
+    // t_{i-2}, t_{i-1} (ends at q), t_i (starts at q), t_{i+1}; missing = 0
+    const bool h_m2 = i0 >= 2, h_m1 = i0 >= 1, h_i = i0 <= N - 2, h_p1 = i0 + 1 <= N - 2;
+    const double tm2x = h_m2 ? Tx[q - 2] : 0.0, tm2y = h_m2 ? Ty[q - 2] : 0.0;
+    const double tm1x = h_m1 ? Tx[q - 1] : 0.0, tm1y = h_m1 ? Ty[q - 1] : 0.0;
+    const double tix = h_i ? Tx[q] : 0.0, tiy = h_i ? Ty[q] : 0.0;
+    const double tp1x = h_p1 ? Tx[q + 1] : 0.0, tp1y = h_p1 ? Ty[q + 1] : 0.0;
     const double ks = I.k_s / (I.l0 * I.l0);
     Fx = 0.0;
     Fy = 0.0;
-    // Eq. 11 (zero-padded tangents)
-    if (has_m1) {
-        Fx -= ks * (L_m1 - I.l0) * t_m1x;
-        Fy -= ks * (L_m1 - I.l0) * t_m1y;
+    if (h_m1) {
+        const double Lm1 = Ln[q - 1];
+        // Eq. 11, spring to the previous bead
+        Fx -= ks * (Lm1 - I.l0) * tm1x;
+        Fy -= ks * (Lm1 - I.l0) * tm1y;
+        // Eq. 12, first term: (t_i + t_{i-2}).(I - t_{i-1} t_{i-1}) / R_{i-1,i}
+        const double vx = tix + tm2x, vy = tiy + tm2y;
+        const double vt = vx * tm1x + vy * tm1y;
+        Fx += I.k_b * (vx - vt * tm1x) / Lm1;
+        Fy += I.k_b * (vy - vt * tm1y) / Lm1;
     }
-    if (has_i) {
-        Fx += ks * (L_i - I.l0) * t_ix;
-        Fy += ks * (L_i - I.l0) * t_iy;
-    }
-    // Eq. 12: k_b [ (t_i + t_{i-2}).(I - t_{i-1} t_{i-1}) / R_{i-1,i}
-    //              - (t_{i+1} + t_{i-1}).(I - t_i t_i) / R_{i,i+1} ]
-    if (has_m1) {
-        const double vx = t_ix + t_m2x, vy = t_iy + t_m2y;
-        const double vt = vx * t_m1x + vy * t_m1y;
-        Fx += I.k_b * (vx - vt * t_m1x) / L_m1;
-        Fy += I.k_b * (vy - vt * t_m1y) / L_m1;
-    }
-    if (has_i) {
-        const double vx = t_p1x + t_m1x, vy = t_p1y + t_m1y;
-        const double vt = vx * t_ix + vy * t_iy;
-        Fx -= I.k_b * (vx - vt * t_ix) / L_i;
-        Fy -= I.k_b * (vy - vt * t_iy) / L_i;
+    if (h_i) {
+        const double Li = Ln[q];
+        // Eq. 11, spring to the next bead
+        Fx += ks * (Li - I.l0) * tix;
+        Fy += ks * (Li - I.l0) * tiy;
+        // Eq. 12, second term: -(t_{i+1} + t_{i-1}).(I - t_i t_i) / R_{i,i+1}
+        const double vx = tp1x + tm1x, vy = tp1y + tm1y;
+        const double vt = vx * tix + vy * tiy;
+        Fx -= I.k_b * (vx - vt * tix) / Li;
+        Fy -= I.k_b * (vy - vt * tiy) / Li;
     }
     // excluded volume between beads that share no spring; an FP32 distance
     // test (1% margin) selects the pairs evaluated in FP64
     if (I.k_ev != 0.0) {
-        const double Rqx = __ldcg(tab.Rx + I.bead_off + q), Rqy = __ldcg(tab.Ry + I.bead_off + q);
+        const double Rqx = Rx[q], Rqy = Ry[q];
         const float l0f2 = (float)(I.l0 * I.l0) * 1.0201f;
+        const float fnx = (float)I.nx;
         for (int p = 0; p < I.nb; ++p) {
             if (p == q) continue;
             if (p / N == fib && abs(p - q) < 2) continue;
-            double dx = Rqx - __ldcg(tab.Rx + I.bead_off + p);
-            const double dy = Rqy - __ldcg(tab.Ry + I.bead_off + p);
-            dx = min_image(dx, (double)I.nx);
-            const float fx = (float)dx, fy = (float)dy;
+            float fx = (float)(Rqx - Rx[p]);
+            fx -= fnx * rintf(fx / fnx);
+            const float fy = (float)(Rqy - Ry[p]);
             if (fx * fx + fy * fy >= l0f2) continue;
+            const double dx = min_image(Rqx - Rx[p], I.nx);
+            const double dy = Rqy - Ry[p];
             const double r = sqrt(dx * dx + dy * dy);
             if (r < I.l0 && r > 0.0) {
                 const double m = I.k_ev * (I.l0 - r) / r;
@@ -170,11 +169,16 @@ __global__ void __launch_bounds__(kBeadThreads)
             const BeadTab told, const BeadTab tnew, int parity, int advance, unsigned *__restrict__ counters) {
     constexpr bool kF64 = std::is_same<S, double>::value;
     __shared__ Inst sI;
-    // beads whose support can overlap bead b's: old-table position (FP64
-    // path), offset R_b - R_q (FP32 paths) and spreading coefficients G
+    // neighbour beads: old-table position (FP64 path), offset R_b - R_q and
+    // spreading coefficients (FP32 paths); reused by the last CTA to stage
+    // positions, support sums and segment tangents
     __shared__ double s_rx[kMaxBeads], s_ry[kMaxBeads], s_gx[kMaxBeads], s_gy[kMaxBeads];
-    __shared__ float s_ox[kMaxBeads], s_oy[kMaxBeads];
+    __shared__ double s_tx[kMaxBeads], s_ty[kMaxBeads], s_ln[kMaxBeads];
+    __shared__ float s_ox[kMaxBeads], s_oy[kMaxBeads], s_gxf[kMaxBeads], s_gyf[kMaxBeads];
     __shared__ double sh[2][kWarps];
+    __shared__ double s_R[2];
+    __shared__ float s_rel[2];
+    __shared__ Box s_box;
     __shared__ int s_last, s_nn;
 
     const int b = blockIdx.x;
@@ -185,13 +189,21 @@ __global__ void __launch_bounds__(kBeadThreads)
     const Inst &I = sI;
     const S *A = pool + I.pop_off;
 
-    double Rx, Ry;
     if (advance) {
-        Rx = told.Rx[b];
-        Ry = told.Ry[b];
+        if (tid == 0) {
+            const double Rx = told.Rx[b], Ry = told.Ry[b];
+            const Box bx = support_box(I, Rx, Ry);
+            s_R[0] = Rx;
+            s_R[1] = Ry;
+            s_box = bx;
+            s_rel[0] = (float)(bx.iu + 0.5 - Rx);
+            s_rel[1] = (float)(bx.j0 + 0.5 - Ry);
+        }
+        __syncthreads();
+        const double Rx = s_R[0], Ry = s_R[1];
         if (tid < 32) {
-            const double reach = 2.0 * I.rcut + 1e-6;
-            const bool all = I.nx < 2.0 * reach + 2.0;  // small lattice: keep every bead
+            // beads whose support can overlap b's (FP32 screen, 1-cell margin)
+            const float reach = 2.0f * I.f_rcut + 1.0f, fnx = (float)I.nx;
             int n = 0;
             for (int base = 0; base < I.nb; base += 32) {
                 const int q = base + tid;
@@ -200,18 +212,23 @@ __global__ void __launch_bounds__(kBeadThreads)
                 if (q < I.nb) {
                     qx = told.Rx[I.bead_off + q];
                     qy = told.Ry[I.bead_off + q];
-                    const double dx = min_image(qx - Rx, (double)I.nx), dy = qy - Ry;
-                    hit = all || dx * dx + dy * dy < reach * reach;
+                    float dx = (float)(qx - Rx);
+                    dx -= fnx * rintf(dx / fnx);
+                    const float dy = (float)(qy - Ry);
+                    hit = dx * dx + dy * dy < reach * reach;
                 }
                 const unsigned m = __ballot_sync(0xffffffffu, hit);
                 if (hit) {
                     const int pos = n + __popc(m & ((1u << tid) - 1u));
                     s_rx[pos] = qx;
                     s_ry[pos] = qy;
-                    s_ox[pos] = (float)min_image(Rx - qx, (double)I.nx);
+                    s_ox[pos] = (float)min_image(Rx - qx, I.nx);
                     s_oy[pos] = (float)(Ry - qy);
-                    s_gx[pos] = told.Gx[I.bead_off + q];
-                    s_gy[pos] = told.Gy[I.bead_off + q];
+                    const double gx = told.Gx[I.bead_off + q], gy = told.Gy[I.bead_off + q];
+                    s_gx[pos] = gx;
+                    s_gy[pos] = gy;
+                    s_gxf[pos] = (float)gx;
+                    s_gyf[pos] = (float)gy;
                 }
                 n += __popc(m);
             }
@@ -219,18 +236,17 @@ __global__ void __launch_bounds__(kBeadThreads)
         }
         __syncthreads();
         const int nn = s_nn;
-        const Box bx = support_box(I, Rx, Ry);
-        // cell centre relative to R_b: (rel0x + column, rel0y + row)
-        const float rel0x = (float)(bx.iu + 0.5 - Rx), rel0y = (float)(bx.j0 + 0.5 - Ry);
-        const float af = (float)I.a, inv_xi = (float)(1.0 / I.xi), rc2 = (float)I.rcut2;
+        const Box bx = s_box;
+        const float rel0x = s_rel[0], rel0y = s_rel[1];
         const float hnx = 0.5f * (float)I.nx, fnx = (float)I.nx;
         double ax = 0.0, ay = 0.0;
+        float axf = 0.0f, ayf = 0.0f;  // FP32 paths: per-thread partials (few terms)
         for (int c = tid; c < bx.w * bx.h; c += blockDim.x) {
             const int cj = c / bx.w, ci = c - cj * bx.w;
             const int j = bx.j0 + cj;
             int i = bx.i0 + ci;
             i = (i >= I.nx) ? i - I.nx : i;
-            if (kF64) {
+            if constexpr (kF64) {
                 const double xc = i + 0.5, yc = j + 0.5;
                 const double phb = phi_f64(I, xc, yc, Rx, Ry);
                 if (phb == 0.0) continue;
@@ -254,60 +270,79 @@ __global__ void __launch_bounds__(kBeadThreads)
                 ay += phb * ((jy + 0.5 * fy) / rho);
             } else {
                 const float dx = rel0x + (float)ci, dy = rel0y + (float)cj;
-                const float phb = phi_f32(dx, dy, af, inv_xi, rc2);
+                const float phb = phi_f32(dx, dy, I.f_a, I.f_inv_xi, I.f_rcut2);
                 if (phb == 0.0f) continue;
                 float g[9];
                 load_pops<S, float>(A, I, i, j, parity, g);
                 const float rho = 1.0f + (((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8]);
                 const float jx = (g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]);
                 const float jy = (g[2] - g[4]) + (g[5] + g[6]) - (g[7] + g[8]);
-                float fx = (float)I.gx, fy = (float)I.gy;
+                float fx = I.f_gx, fy = I.f_gy;
                 for (int q = 0; q < nn; ++q) {
                     float ddx = dx + s_ox[q];
                     ddx = (ddx > hnx) ? ddx - fnx : ((ddx < -hnx) ? ddx + fnx : ddx);
-                    const float ph = phi_f32(ddx, dy + s_oy[q], af, inv_xi, rc2);
-                    fx += ph * (float)s_gx[q];
-                    fy += ph * (float)s_gy[q];
+                    const float ph = phi_f32(ddx, dy + s_oy[q], I.f_a, I.f_inv_xi, I.f_rcut2);
+                    fx += ph * s_gxf[q];
+                    fy += ph * s_gyf[q];
                 }
                 const float irho = 1.0f / rho;
-                ax += (double)(phb * ((jx + 0.5f * fx) * irho));
-                ay += (double)(phb * ((jy + 0.5f * fy) * irho));
+                axf += phb * ((jx + 0.5f * fx) * irho);
+                ayf += phb * ((jy + 0.5f * fy) * irho);
             }
         }
-        block_sum2(ax, ay, sh);
-        const double S_old = told.S[b];
-        const double Vx = ax / S_old, Vy = ay / S_old;
-        Rx += Vx;
-        Ry += Vy;
+        if constexpr (!kF64) {
+            ax = (double)axf;
+            ay = (double)ayf;
+        }
+        block_sum2_to0(ax, ay, sh);
         if (tid == 0) {
-            tnew.Rx[b] = Rx;
-            tnew.Ry[b] = Ry;
+            const double inv_S = 1.0 / told.S[b];
+            const double Vx = ax * inv_S, Vy = ay * inv_S;
+            const double Rnx = Rx + Vx, Rny = Ry + Vy;
+            tnew.Rx[b] = Rnx;
+            tnew.Ry[b] = Rny;
             tnew.Vx[b] = Vx;
             tnew.Vy[b] = Vy;
+            const Box nb_ = support_box(I, Rnx, Rny);
+            s_R[0] = Rnx;
+            s_R[1] = Rny;
+            s_box = nb_;
+            s_rel[0] = (float)(nb_.iu + 0.5 - Rnx);
+            s_rel[1] = (float)(nb_.j0 + 0.5 - Rny);
         }
-    } else {
-        Rx = tnew.Rx[b];
-        Ry = tnew.Ry[b];
+    } else if (tid == 0) {
+        const double Rx = tnew.Rx[b], Ry = tnew.Ry[b];
+        const Box bx = support_box(I, Rx, Ry);
+        s_R[0] = Rx;
+        s_R[1] = Ry;
+        s_box = bx;
+        s_rel[0] = (float)(bx.iu + 0.5 - Rx);
+        s_rel[1] = (float)(bx.j0 + 0.5 - Ry);
     }
+    __syncthreads();
 
     // S_b = sum_x phi_b at the new position
     {
-        const Box bx = support_box(I, Rx, Ry);
-        const float rel0x = (float)(bx.iu + 0.5 - Rx), rel0y = (float)(bx.j0 + 0.5 - Ry);
-        const float af = (float)I.a, inv_xi = (float)(1.0 / I.xi), rc2 = (float)I.rcut2;
-        double s = 0.0, dummy = 0.0;
+        const double Rx = s_R[0], Ry = s_R[1];
+        const Box bx = s_box;
+        const float rel0x = s_rel[0], rel0y = s_rel[1];
+        double acc = 0.0, dummy = 0.0;
+        float part = 0.0f;
         for (int c = tid; c < bx.w * bx.h; c += blockDim.x) {
             const int cj = c / bx.w, ci = c - cj * bx.w;
-            if (kF64) {
+            if constexpr (kF64) {
                 int i = bx.i0 + ci;
                 i = (i >= I.nx) ? i - I.nx : i;
-                s += phi_f64(I, i + 0.5, bx.j0 + cj + 0.5, Rx, Ry);
+                acc += phi_f64(I, i + 0.5, bx.j0 + cj + 0.5, Rx, Ry);
             } else {
-                s += (double)phi_f32(rel0x + (float)ci, rel0y + (float)cj, af, inv_xi, rc2);
+                // each thread sums at most a few terms in FP32 before the
+                // FP64 block reduction
+                part += phi_f32(rel0x + (float)ci, rel0y + (float)cj, I.f_a, I.f_inv_xi, I.f_rcut2);
             }
         }
-        block_sum2(s, dummy, sh);
-        if (tid == 0) tnew.S[b] = s;
+        if constexpr (!kF64) acc = (double)part;
+        block_sum2_to0(acc, dummy, sh);
+        if (tid == 0) tnew.S[b] = acc;
     }
 
     // the last CTA of this instance computes the forces of all its beads
@@ -320,20 +355,40 @@ __global__ void __launch_bounds__(kBeadThreads)
     __syncthreads();
     if (!s_last) return;
     __threadfence();
+    // stage the instance's new positions and support sums (written by every
+    // CTA; the L2-coherent loads see them), then every segment once
+    for (int q = tid; q < I.nb; q += blockDim.x) {
+        s_rx[q] = __ldcg(tnew.Rx + I.bead_off + q);
+        s_ry[q] = __ldcg(tnew.Ry + I.bead_off + q);
+        s_gx[q] = __ldcg(tnew.S + I.bead_off + q);
+    }
+    __syncthreads();
+    for (int q = tid; q < I.nb; q += blockDim.x) {
+        if ((q + 1) % I.n_beads != 0) {
+            const double dx = s_rx[q + 1] - s_rx[q], dy = s_ry[q + 1] - s_ry[q];
+            const double L = sqrt(dx * dx + dy * dy);
+            const double iL = 1.0 / L;
+            s_tx[q] = dx * iL;
+            s_ty[q] = dy * iL;
+            s_ln[q] = L;
+        }
+    }
+    __syncthreads();
     for (int q = tid; q < I.nb; q += blockDim.x) {
         double Fx, Fy;
-        bead_force(I, tnew, q, Fx, Fy);
+        bead_force(I, s_rx, s_ry, s_tx, s_ty, s_ln, q, Fx, Fy);
         const int gq = I.bead_off + q;
-        const double Sq = __ldcg(tnew.S + gq);
-        const double Gx = Fx / Sq, Gy = Fy / Sq;
+        const double inv_S = 1.0 / s_gx[q];
+        const double Gx = Fx * inv_S, Gy = Fy * inv_S;
         tnew.Fx[gq] = Fx;
         tnew.Fy[gq] = Fy;
         tnew.Gx[gq] = Gx;
         tnew.Gy[gq] = Gy;
         // FP32 overlay table: x wrapped into [0, nx), split into hi + lo
-        const double rx = __ldcg(tnew.Rx + gq);
-        const double xw = rx - I.nx * floor(rx / I.nx);
-        const double yw = __ldcg(tnew.Ry + gq);
+        const double rx = s_rx[q];
+        double xw = rx - (double)floorf((float)rx / (float)I.nx) * (double)I.nx;
+        xw = (xw < 0.0) ? xw + I.nx : ((xw >= I.nx) ? xw - I.nx : xw);
+        const double yw = s_ry[q];
         const float xh = (float)xw, yh = (float)yw;
         tnew.xh[gq] = xh;
         tnew.xl[gq] = (float)(xw - (double)xh);

@@ -34,7 +34,24 @@ struct Inst {
     double s_e, s_eps, s_q;
     float scale[9];       // FP16 storage: stored = (f_k - w_k) * scale[k]
     float inv_scale[9];
+    // Host-precomputed terms, so that no kernel converts or divides doubles
+    // per cell (FP64 throughput is a small fraction of FP32 on this GPU):
+    double inv_xi;
+    double bbd[2][9];     // 6 w_k c_kx u_wall, [0] bottom wall, [1] top wall
+    double fluid_rates_d[4];  // s_nu, s_e, s_eps, s_q where Phi = 0
+    float bbf[2][9];
+    float fluid_rates_f[4];
+    float f_nu_f, f_visc_m1, f_gx, f_gy, f_a, f_inv_xi, f_rcut, f_rcut2;
+    float f_s_e, f_s_eps, f_s_q;
 };
+
+template <class R> __device__ __forceinline__ R bb_term(const Inst &I, int wall, int k);
+template <> __device__ __forceinline__ double bb_term<double>(const Inst &I, int wall, int k) {
+    return I.bbd[wall][k];
+}
+template <> __device__ __forceinline__ float bb_term<float>(const Inst &I, int wall, int k) {
+    return I.bbf[wall][k];
+}
 
 // Bead table, structure of arrays.  FP64 state (Sec. 2.3 keeps R, V
 // off-lattice) plus an FP32 copy for the reduced-precision lattice sweep:
@@ -88,9 +105,8 @@ __device__ __forceinline__ void load_one(const S *__restrict__ A, const Inst &I,
             g = (R)Store<S>::ld(A + (int64_t)Q<k>::opp * I.plane + (int64_t)ys * I.pitch + xs,
                                 I.inv_scale[Q<k>::opp]);
         } else {
-            const double uw = (ys < 0) ? I.u_bot : I.u_top;
             g = (R)Store<S>::ld(A + (int64_t)k * I.plane + (int64_t)y * I.pitch + x, I.inv_scale[k]) +
-                (R)(6.0 * Q<k>::w * Q<k>::cx * uw);
+                bb_term<R>(I, ys < 0 ? 0 : 1, k);
         }
     }
 }
@@ -106,9 +122,8 @@ __device__ __forceinline__ void store_one(S *__restrict__ A, const Inst &I, int 
             xd = (xd < 0) ? xd + I.nx : (xd >= I.nx ? xd - I.nx : xd);
             Store<S>::st(A + (int64_t)k * I.plane + (int64_t)yd * I.pitch + xd, g, I.scale[k]);
         } else {
-            const double uw = (yd < 0) ? I.u_bot : I.u_top;
             Store<S>::st(A + (int64_t)Q<k>::opp * I.plane + (int64_t)y * I.pitch + x,
-                         g - (R)(6.0 * Q<k>::w * Q<k>::cx * uw), I.scale[Q<k>::opp]);
+                         g - bb_term<R>(I, yd < 0 ? 0 : 1, k), I.scale[Q<k>::opp]);
         }
     }
 }

@@ -53,7 +53,13 @@ __global__ void __launch_bounds__(kTileX *kTileY)
 
     const int x0 = blockIdx.x * kTileX, y0 = blockIdx.y * kTileY;
     const int tx = threadIdx.x, ty = threadIdx.y;
+    const int x = x0 + tx, y = y0 + ty;
+    const bool valid = x < I.nx && y < I.ny;
     S *A = pool + I.pop_off;
+
+    // the population loads do not depend on the bead list: issue them first
+    R g[9];
+    if (valid) load_pops<S, R>(A, I, x, y, parity, g);
 
     if (ty == 0) {
         // list the beads whose support reaches this tile, in bead order
@@ -92,7 +98,7 @@ __global__ void __launch_bounds__(kTileX *kTileY)
                     float ad = fminf(fabsf(d), fminf(fabsf(d - fnx), fabsf(d + fnx)));
                     const float dxr = fmaxf(0.f, ad - 0.5f * (kTileX - 1));
                     const float dyr = fmaxf(0.f, fabsf(yh - ((float)y0 + 0.5f * kTileY)) - 0.5f * (kTileY - 1));
-                    const float reach = (float)I.rcut + 0.05f;
+                    const float reach = I.f_rcut + 0.05f;
                     hit = dxr * dxr + dyr * dyr < reach * reach;
                 }
                 const unsigned mask = __ballot_sync(0xffffffffu, hit);
@@ -111,46 +117,61 @@ __global__ void __launch_bounds__(kTileX *kTileY)
         if (tx == 0) s_n = n;
     }
     __syncthreads();
+    if (!valid) return;
 
-    const int x = x0 + tx, y = y0 + ty;
-    if (x >= I.nx || y >= I.ny) return;
-
-    R g[9];
-    load_pops<S, R>(A, I, x, y, parity, g);
-
-    R Fx = (R)I.gx, Fy = (R)I.gy, Phi = (R)0;
     const int nhot = s_n;
+    R s_nu, s_e, s_eps, s_q, Fx, Fy;
     if constexpr (kF64) {
-        const double xc = x + 0.5, yc = y + 0.5;
-        for (int q = 0; q < nhot; ++q) {
-            const double ph = phi_f64(I, xc, yc, s_bx[q], s_by[q]);
-            if (ph != 0.0) {
+        Fx = I.gx;
+        Fy = I.gy;
+        if (nhot == 0) {
+            s_nu = I.fluid_rates_d[0];
+            s_e = I.fluid_rates_d[1];
+            s_eps = I.fluid_rates_d[2];
+            s_q = I.fluid_rates_d[3];
+        } else {
+            double Phi = 0.0;
+            const double xc = x + 0.5, yc = y + 0.5;
+            for (int q = 0; q < nhot; ++q) {
+                const double ph = phi_f64(I, xc, yc, s_bx[q], s_by[q]);
+                if (ph != 0.0) {
+                    Phi += ph;
+                    Fx += ph * s_gx[q];
+                    Fy += ph * s_gy[q];
+                }
+            }
+            const double nu = I.nu_f * (1.0 + (I.visc_ratio - 1.0) * Phi);
+            rates<double>(I.collision, nu, I.s_e, I.s_eps, I.s_q, s_nu, s_e, s_eps, s_q);
+        }
+    } else {
+        Fx = I.f_gx;
+        Fy = I.f_gy;
+        if (nhot == 0) {
+            s_nu = I.fluid_rates_f[0];
+            s_e = I.fluid_rates_f[1];
+            s_eps = I.fluid_rates_f[2];
+            s_q = I.fluid_rates_f[3];
+        } else {
+            float Phi = 0.f;
+            const float hnx = 0.5f * I.nx, fnx = (float)I.nx;
+            const float xc = (float)x + 0.5f, yc = (float)y + 0.5f;
+            for (int q = 0; q < nhot; ++q) {
+                // (x_c - R_x) with R_x = hi + lo; the periodic shift is
+                // applied to the cell centre first so that xc - hi is exact
+                float xcl = xc;
+                const float d0 = xcl - s_bx[q];
+                xcl = (d0 > hnx) ? xcl - fnx : ((d0 < -hnx) ? xcl + fnx : xcl);
+                const float dx = (xcl - s_bx[q]) - s_xl[q];
+                const float dy = (yc - s_by[q]) - s_yl[q];
+                const float ph = phi_f32(dx, dy, I.f_a, I.f_inv_xi, I.f_rcut2);
                 Phi += ph;
                 Fx += ph * s_gx[q];
                 Fy += ph * s_gy[q];
             }
-        }
-    } else {
-        const float a = (float)I.a, inv_xi = (float)(1.0 / I.xi), rc2 = (float)I.rcut2;
-        const float hnx = 0.5f * I.nx, fnx = (float)I.nx;
-        const float xc = (float)x + 0.5f, yc = (float)y + 0.5f;
-        for (int q = 0; q < nhot; ++q) {
-            // (x_c - R_x) with R_x = hi + lo; the periodic shift is applied
-            // to the cell centre first so that xc - hi is exact
-            float xcl = xc;
-            const float d0 = xcl - s_bx[q];
-            xcl = (d0 > hnx) ? xcl - fnx : ((d0 < -hnx) ? xcl + fnx : xcl);
-            const float dx = (xcl - s_bx[q]) - s_xl[q];
-            const float dy = (yc - s_by[q]) - s_yl[q];
-            const float ph = phi_f32(dx, dy, a, inv_xi, rc2);
-            Phi += ph;
-            Fx += ph * s_gx[q];
-            Fy += ph * s_gy[q];
+            const float nu = I.f_nu_f * (1.0f + I.f_visc_m1 * Phi);
+            rates<float>(I.collision, nu, I.f_s_e, I.f_s_eps, I.f_s_q, s_nu, s_e, s_eps, s_q);
         }
     }
-    const R nu = (R)I.nu_f * ((R)1 + ((R)I.visc_ratio - (R)1) * Phi);
-    R s_nu, s_e, s_eps, s_q;
-    rates<R>(I.collision, nu, (R)I.s_e, (R)I.s_eps, (R)I.s_q, s_nu, s_e, s_eps, s_q);
     collide<R>(g, Fx, Fy, s_nu, s_e, s_eps, s_q);
     store_pops<S, R>(A, I, x, y, parity, g);
 }
