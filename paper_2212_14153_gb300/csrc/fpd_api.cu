@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdint>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -87,7 +88,14 @@ int derive(fpd_sim *s, const fpd_params &p) {
     I.pitch = (p.nx + align - 1) / align * align;
     I.precision = p.precision;
     I.plane = (int64_t)I.pitch * p.ny;
+    if (9 * I.plane > (int64_t)INT32_MAX)
+        return fail(nullptr, FPD_EINVAL, "lattice of %d x %d cells exceeds 32-bit element offsets", p.nx, p.ny);
+    I.plane32 = (int32_t)I.plane;
     I.pop_off = 0;
+    I.ntx = (p.nx + fpd::kTileX - 1) / fpd::kTileX;
+    I.nty = (p.ny + fpd::kTileY - 1) / fpd::kTileY;
+    I.tile_base = 0;
+    I.mask_words = nb > 0 ? (nb + 31) / 32 : 1;
     I.u_bot = p.u_bottom;
     I.u_top = p.u_top;
     I.nu_f = nu;
@@ -183,6 +191,7 @@ void free_all(fpd_sim *s) {
     cudaFree(s->pool);
     cudaFree(s->tabmem);
     cudaFree(s->counters);
+    cudaFree(s->masks[0]);
     cudaFree(s->scratch);
     cudaFree(s->inst_d);
     for (auto e : s->ev_pool) cudaEventDestroy(e);
@@ -304,6 +313,11 @@ int fpd_create(const fpd_params *p, void *stream, fpd_sim **out) {
                                  b + 5 * nbm, b + 6 * nbm, b + 7 * nbm, b + 8 * nbm, f,
                                  f + nbm,     f + 2 * nbm, f + 3 * nbm, f + 4 * nbm, f + 5 * nbm};
     }
+    // tile masks for both step parities, zeroed
+    const size_t mask_words = (size_t)I.ntx * I.nty * I.mask_words;
+    FPD_TRY(cudaMalloc(&s->masks[0], 2 * mask_words * sizeof(unsigned)), "cudaMalloc tile masks");
+    s->masks[1] = s->masks[0] + mask_words;
+    FPD_TRY(cudaMemsetAsync(s->masks[0], 0, 2 * mask_words * sizeof(unsigned), s->stream), "cudaMemset masks");
     FPD_TRY(cudaMalloc(&s->counters, sizeof(unsigned)), "cudaMalloc counters");
     FPD_TRY(cudaMemsetAsync(s->counters, 0, sizeof(unsigned), s->stream), "cudaMemset counters");
     FPD_TRY(cudaMalloc(&s->inst_d, sizeof(fpd::Inst)), "cudaMalloc instance");
@@ -338,8 +352,8 @@ int fpd_create(const fpd_params *p, void *stream, fpd_sim **out) {
                 "copy beads");
         FPD_TRY(cudaMemcpyAsync(s->tab[0].Ry, Ry.data(), nb * sizeof(double), cudaMemcpyHostToDevice, s->stream),
                 "copy beads");
-        FPD_TRY(fpd::launch_beads(s->precision, s->inst_d, nullptr, nb, s->pool, s->tab[0], s->tab[0], 0, 0,
-                                  s->counters, s->stream),
+        FPD_TRY(fpd::launch_beads(s->precision, s->inst_d, nullptr, nb, s->pool, s->tab[0], s->tab[0],
+                                  s->masks[0], 0, 0, s->counters, s->stream),
                 "initial bead table");
     }
     FPD_TRY(cudaStreamSynchronize(s->stream), "fpd_create");
@@ -364,7 +378,7 @@ int fpd_step(fpd_sim *s, int64_t n_steps) {
                 cudaEventRecord(a, s->stream);
             }
             e = fpd::launch_beads(s->precision, s->inst_d, nullptr, I.nb, s->pool, s->tab[tnew ^ 1], s->tab[tnew],
-                                  parity, 1, s->counters, s->stream);
+                                  s->masks[tnew], parity, 1, s->counters, s->stream);
             if (e != cudaSuccess) return cuda_fail(s, e, "bead kernel launch");
             if (s->profiling) {
                 cudaEventRecord(b, s->stream);
@@ -377,7 +391,8 @@ int fpd_step(fpd_sim *s, int64_t n_steps) {
             b = take_event(s);
             cudaEventRecord(a, s->stream);
         }
-        e = fpd::launch_lattice(s->precision, s->inst_d, I, s->pool, s->tab[tnew], parity, s->stream);
+        e = fpd::launch_lattice(s->precision, s->inst_d, I, s->pool, s->tab[tnew], s->masks[tnew],
+                                s->masks[tnew ^ 1], parity, s->stream);
         if (e != cudaSuccess) return cuda_fail(s, e, "lattice kernel launch");
         if (s->profiling) {
             cudaEventRecord(b, s->stream);
@@ -402,8 +417,10 @@ int fpd_read_fields(fpd_sim *s, double *ux, double *uy, double *rho) {
     const size_t n = (size_t)I.nx * I.ny;
     int rc = ensure_scratch(s, 3 * n * sizeof(double));
     if (rc) return rc;
-    cudaError_t e = fpd::launch_fields(s->precision, s->inst_d, I, s->pool, s->tab[cur_tab(s)], (int)(s->nstep & 1),
-                                       s->scratch, s->scratch + n, s->scratch + 2 * n, s->stream);
+    const int ct = cur_tab(s);
+    cudaError_t e = fpd::launch_fields(s->precision, s->inst_d, I, s->pool, s->tab[ct], s->masks[ct],
+                                       (int)(s->nstep & 1), s->scratch, s->scratch + n, s->scratch + 2 * n,
+                                       s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "fields kernel");
     double *dst[3] = {ux, uy, rho};
     for (int i = 0; i < 3; ++i)

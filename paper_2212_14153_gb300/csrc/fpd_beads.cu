@@ -166,7 +166,8 @@ __device__ void bead_force(const Inst &I, const double *Rx, const double *Ry, co
 template <class S>
 __global__ void __launch_bounds__(kBeadThreads)
     k_beads(const Inst *__restrict__ insts, const int *__restrict__ bead_inst, const S *__restrict__ pool,
-            const BeadTab told, const BeadTab tnew, int parity, int advance, unsigned *__restrict__ counters) {
+            const BeadTab told, const BeadTab tnew, unsigned *__restrict__ mask_write, int parity, int advance,
+            unsigned *__restrict__ counters) {
     constexpr bool kF64 = std::is_same<S, double>::value;
     __shared__ Inst sI;
     // neighbour beads: old-table position (FP64 path), offset R_b - R_q and
@@ -251,7 +252,7 @@ __global__ void __launch_bounds__(kBeadThreads)
                 const double phb = phi_f64(I, xc, yc, Rx, Ry);
                 if (phb == 0.0) continue;
                 double g[9];
-                load_pops<S, double>(A, I, i, j, parity, g);
+                load_pops<S, double>(A, I, make_cell(I, i, j), parity, g);
                 double dr = 0.0;
 #pragma unroll
                 for (int k = 0; k < 9; ++k) dr += g[k];
@@ -273,7 +274,7 @@ __global__ void __launch_bounds__(kBeadThreads)
                 const float phb = phi_f32(dx, dy, I.f_a, I.f_inv_xi, I.f_rcut2);
                 if (phb == 0.0f) continue;
                 float g[9];
-                load_pops<S, float>(A, I, i, j, parity, g);
+                load_pops<S, float>(A, I, make_cell(I, i, j), parity, g);
                 const float rho = 1.0f + (((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8]);
                 const float jx = (g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]);
                 const float jy = (g[2] - g[4]) + (g[5] + g[6]) - (g[7] + g[8]);
@@ -320,6 +321,24 @@ __global__ void __launch_bounds__(kBeadThreads)
         s_rel[1] = (float)(bx.j0 + 0.5 - Ry);
     }
     __syncthreads();
+
+    // mark bead b in the mask of every lattice tile its support box reaches
+    // (one atomicOr per tile row and tile column the box starts in)
+    {
+        const Box bx = s_box;
+        const int lb = b - I.bead_off;
+        const unsigned bit = 1u << (lb & 31);
+        const int tr0 = bx.j0 / kTileY;
+        const int nrows = bx.h > 0 ? (bx.j0 + bx.h - 1) / kTileY - tr0 + 1 : 0;
+        for (int t = tid; t < nrows * bx.w; t += blockDim.x) {
+            const int r = tr0 + t / bx.w, ci = t - (t / bx.w) * bx.w;
+            int col = bx.i0 + ci;
+            col = (col >= I.nx) ? col - I.nx : col;
+            if (ci != 0 && (col % kTileX) != 0) continue;
+            const int tile = I.tile_base + r * I.ntx + col / kTileX;
+            atomicOr(mask_write + tile * I.mask_words + (lb >> 5), bit);
+        }
+    }
 
     // S_b = sum_x phi_b at the new position
     {
@@ -403,21 +422,21 @@ __global__ void __launch_bounds__(kBeadThreads)
 }  // namespace
 
 cudaError_t launch_beads(int precision, const Inst *inst_d, const int *bead_inst, int nb_total, const void *pool,
-                         BeadTab tab_old, BeadTab tab_new, int parity, int advance, unsigned *counters,
-                         cudaStream_t st) {
+                         BeadTab tab_old, BeadTab tab_new, unsigned *mask_write, int parity, int advance,
+                         unsigned *counters, cudaStream_t st) {
     if (nb_total <= 0) return cudaSuccess;
     switch (precision) {
         case 0:
             k_beads<double><<<nb_total, kBeadThreads, 0, st>>>(inst_d, bead_inst, (const double *)pool, tab_old,
-                                                              tab_new, parity, advance, counters);
+                                                              tab_new, mask_write, parity, advance, counters);
             break;
         case 1:
             k_beads<float><<<nb_total, kBeadThreads, 0, st>>>(inst_d, bead_inst, (const float *)pool, tab_old,
-                                                             tab_new, parity, advance, counters);
+                                                             tab_new, mask_write, parity, advance, counters);
             break;
         case 2:
             k_beads<__half><<<nb_total, kBeadThreads, 0, st>>>(inst_d, bead_inst, (const __half *)pool, tab_old,
-                                                              tab_new, parity, advance, counters);
+                                                              tab_new, mask_write, parity, advance, counters);
             break;
         default:
             return cudaErrorInvalidValue;

@@ -30,7 +30,10 @@ struct Inst {
     double k_s, k_b, k_ev;
     int32_t collision, n_beads, n_fibers, nb;
     int32_t bead_off;     // offset of this instance's beads in the tables
-    int32_t pad_;
+    int32_t plane32;      // plane as int: 9 planes of an instance fit in int32
+    int32_t ntx, nty;     // lattice tiles (kTileX x kTileY cells) in x and y
+    int32_t tile_base;    // first tile of this instance in the tile-mask arrays
+    int32_t mask_words;   // 32-bit words per tile mask: ceil(nb / 32), >= 1
     double s_e, s_eps, s_q;
     float scale[9];       // FP16 storage: stored = (f_k - w_k) * scale[k]
     float inv_scale[9];
@@ -90,70 +93,92 @@ template <> struct Store<__half> {
 // A neighbour beyond a wall is replaced by half-way bounce-back from the
 // same cell: arriving  g_k = g*_{opp k} + 6 w_k (c_k . u_w)  (read side of an
 // odd step) and leaving  g_{opp k} = g*_k - 6 w_k (c_k . u_w)  (write side).
+// FP16 storage: plane p is always encoded with scale[p] (scale[p] ==
+// scale[opp p], so either content of a plane fits its range).
+
+// A cell with its periodic x neighbours and the element offsets of its row
+// and the rows above and below (those of a wall row are never used).
+struct Cell {
+    int x, xm, xp;  // column, column to the left / right (periodic)
+    int r0, rm, rp; // element offsets of rows y, y - 1, y + 1
+    bool bot, top;  // first / last fluid row (wall half a cell beyond)
+};
+__device__ __forceinline__ Cell make_cell(const Inst &I, int x, int y) {
+    Cell c;
+    c.x = x;
+    c.xm = (x == 0) ? I.nx - 1 : x - 1;
+    c.xp = (x == I.nx - 1) ? 0 : x + 1;
+    c.r0 = y * I.pitch;
+    c.rm = c.r0 - I.pitch;
+    c.rp = c.r0 + I.pitch;
+    c.bot = (y == 0);
+    c.top = (y == I.ny - 1);
+    return c;
+}
+
 template <int k, class S, class R>
-__device__ __forceinline__ void load_one(const S *__restrict__ A, const Inst &I, int x, int y, int parity,
-                                         R &g) {
-    // FP16 storage: plane p is always encoded with scale[p] (scale[p] ==
-    // scale[opp p], so either content of a plane fits its range).
+__device__ __forceinline__ void load_one(const S *__restrict__ A, const Inst &I, const Cell &C, int parity, R &g) {
+    constexpr int cx = Q<k>::cx, cy = Q<k>::cy, o = Q<k>::opp;
     if (parity == 0) {
-        g = (R)Store<S>::ld(A + (int64_t)k * I.plane + (int64_t)y * I.pitch + x, I.inv_scale[k]);
+        g = (R)Store<S>::ld(A + (k * I.plane32 + C.r0 + C.x), I.inv_scale[k]);
     } else {
-        const int ys = y - Q<k>::cy;
-        if (ys >= 0 && ys < I.ny) {
-            int xs = x - Q<k>::cx;
-            xs = (xs < 0) ? xs + I.nx : (xs >= I.nx ? xs - I.nx : xs);
-            g = (R)Store<S>::ld(A + (int64_t)Q<k>::opp * I.plane + (int64_t)ys * I.pitch + xs,
-                                I.inv_scale[Q<k>::opp]);
+        // source cell x - c_k; beyond a wall when it is row -1 or row ny
+        const bool wall = (cy > 0 && C.bot) || (cy < 0 && C.top);
+        if (wall) {
+            g = (R)Store<S>::ld(A + (k * I.plane32 + C.r0 + C.x), I.inv_scale[k]) +
+                bb_term<R>(I, cy > 0 ? 0 : 1, k);
         } else {
-            g = (R)Store<S>::ld(A + (int64_t)k * I.plane + (int64_t)y * I.pitch + x, I.inv_scale[k]) +
-                bb_term<R>(I, ys < 0 ? 0 : 1, k);
+            const int rs = cy > 0 ? C.rm : (cy < 0 ? C.rp : C.r0);
+            const int xs = cx > 0 ? C.xm : (cx < 0 ? C.xp : C.x);
+            g = (R)Store<S>::ld(A + (o * I.plane32 + rs + xs), I.inv_scale[o]);
         }
     }
 }
 
 template <int k, class S, class R>
-__device__ __forceinline__ void store_one(S *__restrict__ A, const Inst &I, int x, int y, int parity, R g) {
+__device__ __forceinline__ void store_one(S *__restrict__ A, const Inst &I, const Cell &C, int parity, R g) {
+    constexpr int cx = Q<k>::cx, cy = Q<k>::cy, o = Q<k>::opp;
     if (parity == 0) {
-        Store<S>::st(A + (int64_t)Q<k>::opp * I.plane + (int64_t)y * I.pitch + x, g, I.scale[Q<k>::opp]);
+        Store<S>::st(A + (o * I.plane32 + C.r0 + C.x), g, I.scale[o]);
     } else {
-        const int yd = y + Q<k>::cy;
-        if (yd >= 0 && yd < I.ny) {
-            int xd = x + Q<k>::cx;
-            xd = (xd < 0) ? xd + I.nx : (xd >= I.nx ? xd - I.nx : xd);
-            Store<S>::st(A + (int64_t)k * I.plane + (int64_t)yd * I.pitch + xd, g, I.scale[k]);
+        // destination cell x + c_k; beyond a wall when it is row ny or row -1
+        const bool wall = (cy > 0 && C.top) || (cy < 0 && C.bot);
+        if (wall) {
+            Store<S>::st(A + (o * I.plane32 + C.r0 + C.x), g - bb_term<R>(I, cy > 0 ? 1 : 0, k), I.scale[o]);
         } else {
-            Store<S>::st(A + (int64_t)Q<k>::opp * I.plane + (int64_t)y * I.pitch + x,
-                         g - bb_term<R>(I, yd < 0 ? 0 : 1, k), I.scale[Q<k>::opp]);
+            const int rd = cy > 0 ? C.rp : (cy < 0 ? C.rm : C.r0);
+            const int xd = cx > 0 ? C.xp : (cx < 0 ? C.xm : C.x);
+            Store<S>::st(A + (k * I.plane32 + rd + xd), g, I.scale[k]);
         }
     }
 }
 
 template <class S, class R>
-__device__ __forceinline__ void load_pops(const S *__restrict__ A, const Inst &I, int x, int y, int parity,
+__device__ __forceinline__ void load_pops(const S *__restrict__ A, const Inst &I, const Cell &C, int parity,
                                           R g[9]) {
-    load_one<0>(A, I, x, y, parity, g[0]);
-    load_one<1>(A, I, x, y, parity, g[1]);
-    load_one<2>(A, I, x, y, parity, g[2]);
-    load_one<3>(A, I, x, y, parity, g[3]);
-    load_one<4>(A, I, x, y, parity, g[4]);
-    load_one<5>(A, I, x, y, parity, g[5]);
-    load_one<6>(A, I, x, y, parity, g[6]);
-    load_one<7>(A, I, x, y, parity, g[7]);
-    load_one<8>(A, I, x, y, parity, g[8]);
+    load_one<0>(A, I, C, parity, g[0]);
+    load_one<1>(A, I, C, parity, g[1]);
+    load_one<2>(A, I, C, parity, g[2]);
+    load_one<3>(A, I, C, parity, g[3]);
+    load_one<4>(A, I, C, parity, g[4]);
+    load_one<5>(A, I, C, parity, g[5]);
+    load_one<6>(A, I, C, parity, g[6]);
+    load_one<7>(A, I, C, parity, g[7]);
+    load_one<8>(A, I, C, parity, g[8]);
 }
 
 template <class S, class R>
-__device__ __forceinline__ void store_pops(S *__restrict__ A, const Inst &I, int x, int y, int parity,
+__device__ __forceinline__ void store_pops(S *__restrict__ A, const Inst &I, const Cell &C, int parity,
                                            const R g[9]) {
-    store_one<0>(A, I, x, y, parity, g[0]);
-    store_one<1>(A, I, x, y, parity, g[1]);
-    store_one<2>(A, I, x, y, parity, g[2]);
-    store_one<3>(A, I, x, y, parity, g[3]);
-    store_one<4>(A, I, x, y, parity, g[4]);
-    store_one<5>(A, I, x, y, parity, g[5]);
-    store_one<6>(A, I, x, y, parity, g[6]);
-    store_one<7>(A, I, x, y, parity, g[7]);
-    store_one<8>(A, I, x, y, parity, g[8]);
+    store_one<0>(A, I, C, parity, g[0]);
+    store_one<1>(A, I, C, parity, g[1]);
+    store_one<2>(A, I, C, parity, g[2]);
+    store_one<3>(A, I, C, parity, g[3]);
+    store_one<4>(A, I, C, parity, g[4]);
+    store_one<5>(A, I, C, parity, g[5]);
+    store_one<6>(A, I, C, parity, g[6]);
+    store_one<7>(A, I, C, parity, g[7]);
+    store_one<8>(A, I, C, parity, g[8]);
 }
 
 // ---------------------------------------------------------------- Eq. 2

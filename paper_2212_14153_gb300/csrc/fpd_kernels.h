@@ -14,20 +14,24 @@ constexpr int kBeadThreads = 256;
 
 // One fused collide-stream-bounce-back sweep of a single instance (Sec. 2.3
 // item (2) with the item-(1) overlay of Eqs. 1, 2, 4 evaluated in hot tiles).
+// mask_read: the per-tile bead masks written by the bead phase of this step;
+// mask_clear: the other mask buffer, zeroed for the next bead phase.
 cudaError_t launch_lattice(int precision, const Inst *inst_d, const Inst &inst_h, void *pool, BeadTab tab,
-                           int parity, cudaStream_t st);
+                           const unsigned *mask_read, unsigned *mask_clear, int parity, cudaStream_t st);
 
 // Bead phase (items (3) then (1)): one CTA per bead.  advance = 0 only
-// computes S and F of tab_new from its own R (initialisation).
+// computes S and F of tab_new from its own R (initialisation).  Every bead
+// ORs its bit into the mask of each lattice tile its support reaches
+// (mask_write, zeroed beforehand).
 cudaError_t launch_beads(int precision, const Inst *inst_d, const int *bead_inst, int nb_total,
-                         const void *pool, BeadTab tab_old, BeadTab tab_new, int parity, int advance,
-                         unsigned *counters, cudaStream_t st);
+                         const void *pool, BeadTab tab_old, BeadTab tab_new, unsigned *mask_write, int parity,
+                         int advance, unsigned *counters, cudaStream_t st);
 
 cudaError_t launch_init(int precision, const Inst *inst_d, const Inst &inst_h, void *pool, int couette,
                         cudaStream_t st);
 
 cudaError_t launch_fields(int precision, const Inst *inst_d, const Inst &inst_h, const void *pool, BeadTab tab,
-                          int parity, double *ux, double *uy, double *rho, cudaStream_t st);
+                          const unsigned *mask, int parity, double *ux, double *uy, double *rho, cudaStream_t st);
 
 cudaError_t launch_read_pops(int precision, const Inst *inst_d, const Inst &inst_h, const void *pool,
                              int parity, double *f, cudaStream_t st);

@@ -19,6 +19,7 @@ struct fpd_sim {
     double *tabmem = nullptr;       // two bead tables
     fpd::BeadTab tab[2]{};
     unsigned *counters = nullptr;   // one per instance (bead-phase last-block)
+    unsigned *masks[2] = {nullptr, nullptr};  // per-tile bead masks, by step parity
     double *scratch = nullptr;      // fields / populations / diagnostics
     size_t scratch_bytes = 0;
     cudaStream_t stream = nullptr;
