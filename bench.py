@@ -7,6 +7,8 @@ step of the method (bead phase + fused collide/stream/bounce-back sweep).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision 0|1|2]
     python bench.py --impl reference      # the FP64 CPU oracle on host cores
+    python bench.py --workload sweep --steps 500 --warmup 5   # batched vs plain loop
+    python bench.py --workload serve --instances 200          # continuous batching
 
 Prints one JSON line (rank 0).  For N > 1 (torchrun) every rank runs its own
 instance of the workload (independent sweep points: weak scaling, no data
@@ -25,6 +27,8 @@ import subprocess
 import sys
 import tempfile
 import time
+
+import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -134,11 +138,11 @@ def run_gpu(args, rank: int, world: int):
         if world > 1:
             torch.distributed.barrier()
 
-    # ---- device-resident throughput (value) and live kernel timing
+    # ---- device-resident throughput (value): consecutive launches overlap
+    # (programmatic dependent launch), so no per-kernel events in this region
     sim = fpd.Simulation(cfg, stream=stream.cuda_stream)
     sim.step(args.warmup)
     sim.sync()
-    sim.set_profiling(True)
     barrier()
     torch.cuda.synchronize()
     sampler = ClockSampler(local) if rank == 0 else None
@@ -152,7 +156,12 @@ def run_gpu(args, rank: int, world: int):
     torch.cuda.synchronize()
     clocks = sampler.stop() if sampler else None
     ms = start.elapsed_time(end)
+    # ---- live per-kernel durations: a second timed region of the same
+    # length with CUDA events around every launch on the library's stream
+    sim.set_profiling(True)
+    sim.step(args.steps)
     kt = sim.kernel_times()
+    sim.set_profiling(False)
     diag = sim.diag()
     sim.close()
     if world > 1:
@@ -189,7 +198,7 @@ def run_gpu(args, rank: int, world: int):
         lat_ms = kt["lattice_ms"] / max(kt["lattice_launches"], 1)
         achieved = bpc * cells / (lat_ms * 1e-3) / 1e9
         traffic = ncu_traffic(cfg["name"], args.precision)
-        gpu_launches = kt["lattice_launches"] + kt["bead_launches"]
+        gpu_launches = kt["lattice_launches"] + kt["bead_launches"]  # per timed region
         line = {
             "metric": "MLUPS (million lattice-cell updates per second) of the FPD-MRT step",
             "value": round(mlups, 1),
@@ -282,6 +291,106 @@ def run_reference(args, rank: int, world: int):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ sweep / serving
+def run_sweep(args, rank: int, world: int):
+    """Batched sweep: independent instances (H ~ U{32..256}, width 2H, C, Re,
+    K, a, N drawn as in the shape-diagram sweep) advanced by one batched
+    launch pair per step, against the plain loop that runs the same instances
+    one at a time with the same kernels and precision."""
+    import torch
+    from paper_2212_14153_gb300 import build, fpd, serve, workloads
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    build.build()
+    inst = workloads.batched_sweep(n=args.instances, seed=4 + rank, precision=args.precision)
+    cells = [c["nx"] * c["ny"] for c in inst]
+    stream = torch.cuda.Stream()
+    S, W = args.steps, args.warmup
+    pool = sum(serve.state_bytes(c, args.precision) + 4096 for c in inst)
+    nbeads = sum(c["n_beads"] * c["n_fibers"] for c in inst)
+    b = fpd.Batch(args.precision, len(inst), pool, nbeads, stream=stream.cuda_stream)
+    for c in inst:
+        b.add(c, W + S)
+    b.run(W)
+    b.sync()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    done = 0
+    while done < S:
+        d = b.run(S - done)
+        if d == 0:
+            break
+        done += d
+    ev1.record(stream)
+    ev1.synchronize()
+    t_batch = ev0.elapsed_time(ev1) * 1e-3
+    b.close()
+    batched = sum(cells) * S / t_batch / 1e6
+    # plain loop: each instance alone, one after the other
+    t_plain = 0.0
+    for c in inst:
+        sim = fpd.Simulation(c, stream=stream.cuda_stream)
+        sim.step(W)
+        sim.sync()
+        ev0.record(stream)
+        sim.step(S)
+        ev1.record(stream)
+        ev1.synchronize()
+        t_plain += ev0.elapsed_time(ev1) * 1e-3
+        sim.close()
+    plain = sum(cells) * S / t_plain / 1e6
+    line = {
+        "metric": "aggregate MLUPS, batched sweep vs plain one-instance-at-a-time loop",
+        "value": round(batched, 1), "unit": "MLUPS", "plain_loop": round(plain, 1),
+        "speedup": round(batched / plain, 2), "n_gpus": 1, "steps": S, "warmup": W,
+        "higher_is_better": True, "dtype": {0: "f64", 1: "f32", 2: "f32"}[args.precision], "data": "synthetic",
+        "config": {"workload": "batched_sweep", "instances": len(inst), "cells": sum(cells), "beads": nbeads,
+                   "H": [min(c["ny"] for c in inst), max(c["ny"] for c in inst)],
+                   "accuracy": "each instance bit-identical to its alone run"},
+        "batched_s": t_batch, "plain_s": t_plain,
+    }
+    print(json.dumps(line), flush=True)
+    return batched
+
+
+def run_serve(args, rank: int, world: int):
+    """Serving: Poisson arrivals of sweep-point requests at 0.5x and 1.2x the
+    measured batched capacity; continuous batching under an HBM cap."""
+    import torch
+    from paper_2212_14153_gb300 import build, serve, workloads
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    build.build()
+    out = []
+    probe = workloads.serving_requests(args.instances, 1.0, seed=5, steps_lo=args.serve_steps_lo,
+                                       steps_hi=args.serve_steps_hi, precision=args.precision)
+    work = np.mean([r["nx"] * r["ny"] * r["steps"] for r in probe])
+    capacity = args.capacity_mlups * 1e6 / work  # requests / s the batch can sustain
+    for load in (0.5, 1.2):
+        reqs = workloads.serving_requests(args.instances, load * capacity, seed=5, steps_lo=args.serve_steps_lo,
+                                          steps_hi=args.serve_steps_hi, precision=args.precision)
+        pool = sum(serve.state_bytes(r, args.precision) + 4096 for r in reqs)
+        nbeads = sum(r["n_beads"] * r["n_fibers"] for r in reqs)
+        srv = serve.Server(args.precision, max_slots=args.max_slots, cap_bytes=args.cap_bytes,
+                           pool_bytes=min(pool, args.cap_bytes), max_beads=nbeads, chunk=args.chunk)
+        rs = [serve.Request(i, r, r["steps"], r["arrival_s"]) for i, r in enumerate(reqs)]
+        res = srv.serve(rs)
+        srv.close()
+        res["load"] = load
+        res["rate_per_s"] = load * capacity
+        out.append(res)
+    line = {
+        "metric": "serving: p50/p99 time-to-result and aggregate MLUPS under Poisson arrivals",
+        "value": round(out[0]["aggregate_mlups"], 1), "unit": "MLUPS", "n_gpus": 1,
+        "higher_is_better": True, "dtype": {0: "f64", 1: "f32", 2: "f32"}[args.precision], "data": "synthetic",
+        "config": {"workload": "serving", "requests": args.instances,
+                   "steps_per_request": [args.serve_steps_lo, args.serve_steps_hi], "chunk": args.chunk,
+                   "cap_bytes": args.cap_bytes, "capacity_mlups_assumed": args.capacity_mlups},
+        "loads": out,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -293,6 +402,14 @@ def main():
     ap.add_argument("--ref-steps", type=int, default=20)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="two_fiber", choices=["two_fiber", "sweep", "serve"])
+    ap.add_argument("--instances", type=int, default=512)
+    ap.add_argument("--serve-steps-lo", type=int, default=5000)
+    ap.add_argument("--serve-steps-hi", type=int, default=50000)
+    ap.add_argument("--capacity-mlups", type=float, default=40000.0)
+    ap.add_argument("--cap-bytes", type=int, default=150 << 30)
+    ap.add_argument("--max-slots", type=int, default=512)
+    ap.add_argument("--chunk", type=int, default=500)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -300,6 +417,10 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload == "sweep":
+        run_sweep(args, rank, world)
+    elif args.workload == "serve":
+        run_serve(args, rank, world)
     else:
         run_gpu(args, rank, world)
 

@@ -182,6 +182,67 @@ int fpd_set_profiling(fpd_sim *s, int on);
  * Synchronises. */
 int fpd_kernel_times(fpd_sim *s, double out[4]);
 
+/* ------------------------------------------------------------------------
+ * Batched instances.  Many independent instances (points of a confinement /
+ * Reynolds-number / stiffness sweep, or serving requests) of possibly
+ * different lattice sizes share one device pool and advance together: each
+ * time step is one bead-phase launch over the beads of all active instances
+ * and one lattice sweep over a packed list of all their tiles.  Instances
+ * never interact, and an instance computes the same numbers alone or in a
+ * batch (the same kernels, per-instance reductions in a fixed order).
+ * ------------------------------------------------------------------------ */
+typedef struct fpd_batch fpd_batch;
+
+/* Create an empty batch: every instance uses `precision`; at most
+ * max_slots instances at a time; a device pool of pool_bytes for their
+ * populations and room for max_beads beads in total.  stream: cudaStream_t
+ * or NULL.  Errors: FPD_EINVAL, FPD_ENOMEM, FPD_ECUDA. */
+int fpd_batch_create(int32_t precision, int32_t max_slots, int64_t pool_bytes, int32_t max_beads, void *stream,
+                     fpd_batch **out);
+
+/* Admit an instance (same parameters and placement rules as fpd_create)
+ * that is to run n_steps time steps; *slot receives its slot index.  It
+ * starts at its own step 0 on the next fpd_batch_run.  FPD_EBUSY when no slot
+ * or no contiguous pool / bead room is free; FPD_EINVAL for bad parameters
+ * or a precision other than the batch's. */
+int fpd_batch_add(fpd_batch *b, const fpd_params *p, int64_t n_steps, int32_t *slot);
+
+/* Advance every active instance by the same number of steps: max_steps, or
+ * fewer so that no instance passes its requested count (*steps_done gets
+ * the count).  Instances that reach their count become finished.  Enqueues
+ * the work asynchronously (the call may synchronise after admissions). */
+int fpd_batch_run(fpd_batch *b, int64_t max_steps, int64_t *steps_done);
+
+/* Block until the batch's work has finished. */
+int fpd_batch_sync(fpd_batch *b);
+
+/* Synchronise, then list up to `capacity` finished instances not listed
+ * before (done_slots may be NULL to only count them). */
+int fpd_batch_poll(fpd_batch *b, int32_t *done_slots, int32_t capacity, int32_t *n_done);
+
+/* out = {nx, ny, beads, steps done, steps requested, state (0 free,
+ * 1 running, 2 finished)}. */
+int fpd_batch_slot_info(fpd_batch *b, int32_t slot, int64_t out[6]);
+
+/* As fpd_read_fields / fpd_read_beads / fpd_read_populations for one slot
+ * (running or finished).  Synchronise. */
+int fpd_batch_read_fields(fpd_batch *b, int32_t slot, double *ux, double *uy, double *rho);
+int fpd_batch_read_beads(fpd_batch *b, int32_t slot, double *pos, double *vel, double *force, double *support);
+int fpd_batch_read_populations(fpd_batch *b, int32_t slot, double *f);
+
+/* Release a slot and its pool and bead room. */
+int fpd_batch_remove(fpd_batch *b, int32_t slot);
+
+/* out = {running instances, their cells, finished instances, pool bytes in
+ * use, pool bytes, global steps, cell updates done, beads in use}. */
+int fpd_batch_stats(fpd_batch *b, double out[8]);
+
+/* Text of the batch's last error; never NULL. */
+const char *fpd_batch_last_error(const fpd_batch *b);
+
+/* Free the batch (NULL-safe).  Synchronises. */
+int fpd_batch_destroy(fpd_batch *b);
+
 /* Text of the last error on s (or of fpd_create in this thread if s is
  * NULL); never NULL; valid until the next call on s. */
 const char *fpd_last_error(const fpd_sim *s);

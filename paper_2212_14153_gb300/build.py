@@ -19,7 +19,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfpd.so")
-SOURCES = ["fpd_api.cu", "fpd_lattice.cu", "fpd_beads.cu", "fpd_noalloc.cu"]
+SOURCES = ["fpd_api.cu", "fpd_lattice.cu", "fpd_beads.cu", "fpd_noalloc.cu", "fpd_batch.cu"]
 HEADERS = ["fpd_device.cuh", "fpd_kernels.h", "fpd_sim.h"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -167,6 +167,12 @@ int derive(fpd_sim *s, const fpd_params &p) {
     I.f_inv_xi = (float)I.inv_xi;
     I.f_rcut = (float)I.rcut;
     I.f_rcut2 = (float)I.rcut2;
+    I.ks_l02 = s->k_s / (l0 * l0);
+    I.f_ks_l02 = (float)I.ks_l02;
+    I.f_kb = (float)s->k_b;
+    I.f_kev = (float)s->k_ev;
+    I.f_l0 = (float)l0;
+    I.f_inv_nx = (float)(1.0 / p.nx);
     I.f_s_e = (float)p.s_e;
     I.f_s_eps = (float)p.s_eps;
     I.f_s_q = (float)p.s_q;
@@ -242,6 +248,37 @@ void harvest(fpd_sim *s) {
 int cur_tab(const fpd_sim *s) { return s->nstep == 0 ? 0 : (int)((s->nstep - 1) & 1); }
 
 }  // namespace
+
+namespace fpd {
+
+int derive_params(fpd_sim *s, const fpd_params &p) { return derive(s, p); }
+
+const char *create_error() { return g_create_error.c_str(); }
+
+bool initial_beads(const fpd_params &p, double l0, std::vector<double> &Rx, std::vector<double> &Ry) {
+    // R_i = c + (i - (N+1)/2) l0 (cos theta, sin theta), i = 1..N (Sec. 4.1:
+    // the fiber centred on c), or the explicit positions
+    const int nb = p.n_beads * p.n_fibers;
+    Rx.assign(nb, 0.0);
+    Ry.assign(nb, 0.0);
+    for (int f = 0; f < p.n_fibers; ++f)
+        for (int i = 1; i <= p.n_beads; ++i) {
+            const int b = f * p.n_beads + i - 1;
+            if (p.bead_xy) {
+                Rx[b] = p.bead_xy[2 * b];
+                Ry[b] = p.bead_xy[2 * b + 1];
+            } else {
+                const double off = (i - (p.n_beads + 1) / 2.0) * l0;
+                Rx[b] = p.centre_xy[2 * f] + off * std::cos(p.theta0[f]);
+                Ry[b] = p.centre_xy[2 * f + 1] + off * std::sin(p.theta0[f]);
+            }
+        }
+    for (int b = 0; b < nb; ++b)
+        if (!is_fin(Rx[b]) || !is_fin(Ry[b])) return false;
+    return true;
+}
+
+}  // namespace fpd
 
 extern "C" {
 
@@ -324,36 +361,18 @@ int fpd_create(const fpd_params *p, void *stream, fpd_sim **out) {
     FPD_TRY(cudaMemcpyAsync(s->inst_d, &I, sizeof I, cudaMemcpyHostToDevice, s->stream), "copy instance");
     FPD_TRY(fpd::launch_init(s->precision, s->inst_d, I, s->pool, p->init_couette, s->stream), "init kernel");
     if (nb > 0) {
-        // initial bead positions: R_i = c + (i - (N+1)/2) l0 (cos t, sin t)
-        std::vector<double> R(2 * nb);
-        if (p->bead_xy) {
-            for (int b = 0; b < 2 * nb; ++b) R[b] = p->bead_xy[b];
-        } else {
-            for (int f = 0; f < p->n_fibers; ++f)
-                for (int i = 1; i <= p->n_beads; ++i) {
-                    const double off = (i - (p->n_beads + 1) / 2.0) * I.l0;
-                    const int b = f * p->n_beads + i - 1;
-                    R[2 * b] = p->centre_xy[2 * f] + off * std::cos(p->theta0[f]);
-                    R[2 * b + 1] = p->centre_xy[2 * f + 1] + off * std::sin(p->theta0[f]);
-                }
-        }
-        for (int b = 0; b < 2 * nb; ++b)
-            if (!is_fin(R[b])) {
-                free_all(s);
-                delete s;
-                return fail(nullptr, FPD_EINVAL, "bead positions must be finite");
-            }
-        std::vector<double> Rx(nb), Ry(nb);
-        for (int b = 0; b < nb; ++b) {
-            Rx[b] = R[2 * b];
-            Ry[b] = R[2 * b + 1];
+        std::vector<double> Rx, Ry;
+        if (!fpd::initial_beads(*p, I.l0, Rx, Ry)) {
+            free_all(s);
+            delete s;
+            return fail(nullptr, FPD_EINVAL, "bead positions must be finite");
         }
         FPD_TRY(cudaMemcpyAsync(s->tab[0].Rx, Rx.data(), nb * sizeof(double), cudaMemcpyHostToDevice, s->stream),
                 "copy beads");
         FPD_TRY(cudaMemcpyAsync(s->tab[0].Ry, Ry.data(), nb * sizeof(double), cudaMemcpyHostToDevice, s->stream),
                 "copy beads");
-        FPD_TRY(fpd::launch_beads(s->precision, s->inst_d, nullptr, nb, s->pool, s->tab[0], s->tab[0],
-                                  s->masks[0], 0, 0, s->counters, s->stream),
+        FPD_TRY(fpd::launch_beads(s->precision, s->inst_d, nullptr, nb, s->pool, s->tab[0], s->tab[1],
+                                  s->masks[0], 0, 0, s->counters, 0, s->stream),
                 "initial bead table");
     }
     FPD_TRY(cudaStreamSynchronize(s->stream), "fpd_create");
@@ -377,8 +396,8 @@ int fpd_step(fpd_sim *s, int64_t n_steps) {
                 b = take_event(s);
                 cudaEventRecord(a, s->stream);
             }
-            e = fpd::launch_beads(s->precision, s->inst_d, nullptr, I.nb, s->pool, s->tab[tnew ^ 1], s->tab[tnew],
-                                  s->masks[tnew], parity, 1, s->counters, s->stream);
+            e = fpd::launch_beads(s->precision, s->inst_d, nullptr, I.nb, s->pool, s->tab[0], s->tab[1],
+                                  s->masks[tnew], parity, 1, s->counters, s->profiling ? 0 : 1, s->stream);
             if (e != cudaSuccess) return cuda_fail(s, e, "bead kernel launch");
             if (s->profiling) {
                 cudaEventRecord(b, s->stream);
@@ -391,8 +410,9 @@ int fpd_step(fpd_sim *s, int64_t n_steps) {
             b = take_event(s);
             cudaEventRecord(a, s->stream);
         }
+        const int after_beads = (I.nb > 0 && s->nstep >= 1 && !s->profiling) ? 1 : 0;
         e = fpd::launch_lattice(s->precision, s->inst_d, I, s->pool, s->tab[tnew], s->masks[tnew],
-                                s->masks[tnew ^ 1], parity, s->stream);
+                                s->masks[tnew ^ 1], parity, after_beads, s->stream);
         if (e != cudaSuccess) return cuda_fail(s, e, "lattice kernel launch");
         if (s->profiling) {
             cudaEventRecord(b, s->stream);

@@ -60,6 +60,56 @@ __device__ __forceinline__ void block_sum2_to0(double &a, double &b, double (*sh
     }
 }
 
+// Error-free sum of two floats (Knuth): s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// Block sum of two FP32 partials with FP64-level accuracy: compensated
+// (hi, lo) float pairs inside each warp, FP64 across the warps.  The FP64
+// pipe of this GPU issues a warp instruction only every few tens of cycles,
+// so FP64 is kept to the final per-warp terms.  Result valid in thread 0.
+__device__ __forceinline__ void block_sum2f_to0(float a, float b, double &ra, double &rb, double (*sh)[kWarps]) {
+    float ah = a, al = 0.f, bh = b, bl = 0.f;
+    for (int o = 16; o > 0; o >>= 1) {
+        const float oah = __shfl_down_sync(0xffffffffu, ah, o), oal = __shfl_down_sync(0xffffffffu, al, o);
+        const float obh = __shfl_down_sync(0xffffffffu, bh, o), obl = __shfl_down_sync(0xffffffffu, bl, o);
+        float s, e;
+        two_sum(ah, oah, s, e);
+        e += al + oal;
+        two_sum(s, e, ah, al);
+        two_sum(bh, obh, s, e);
+        e += bl + obl;
+        two_sum(s, e, bh, bl);
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    float *shf = (float *)sh;  // 4 * kWarps floats fit in the 2 * kWarps doubles
+    __syncthreads();
+    if (l == 0) {
+        shf[4 * w + 0] = ah;
+        shf[4 * w + 1] = al;
+        shf[4 * w + 2] = bh;
+        shf[4 * w + 3] = bl;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float th = shf[0], tl = shf[1], uh = shf[2], ul = shf[3];
+        for (int i = 1; i < kWarps; ++i) {
+            float s, e;
+            two_sum(th, shf[4 * i], s, e);
+            e += tl + shf[4 * i + 1];
+            two_sum(s, e, th, tl);
+            two_sum(uh, shf[4 * i + 2], s, e);
+            e += ul + shf[4 * i + 3];
+            two_sum(s, e, uh, ul);
+        }
+        ra = (double)th + (double)tl;
+        rb = (double)uh + (double)ul;
+    }
+}
+
 // Cells whose centre may lie within the cutoff of (Rx, Ry): a box clipped at
 // the walls; in x it wraps periodically, or spans the lattice once.  iu is
 // the unwrapped x index of the first column (column c sits at iu + c).
@@ -74,36 +124,68 @@ __device__ __forceinline__ Box support_box(const Inst &I, double Rx, double Ry) 
     // a non-finite or far-away bead has no support cells (the NaN then shows
     // up in the diagnostics, not as an out-of-range index)
     if (!isfinite(Rx) || !isfinite(Ry) || fabs(Rx) > 1.0e9 || fabs(Ry) > 1.0e9) return b;
-    const double ylo = fmax(floor(Ry - I.rcut - 0.5) - 1.0, 0.0);
-    const double yhi = fmin(ceil(Ry + I.rcut - 0.5) + 1.0, (double)(I.ny - 1));
-    if (yhi < ylo) return b;
-    double xlo = floor(Rx - I.rcut - 0.5) - 1.0, xhi = ceil(Rx + I.rcut - 0.5) + 1.0;
-    if (xhi - xlo + 1.0 >= (double)I.nx) {
-        // the support spans the lattice: the nx columns around Rx, once each
-        xlo = floor(Rx - 0.5 * I.nx);
-        xhi = xlo + I.nx - 1;
+    int ylo, yhi, xlo, xhi;
+    if (fabs(Rx) < 1.0e6 && fabs(Ry) < 1.0e6) {
+        // bounds with one cell of margin: FP32 rounding (< 0.07 here) cannot
+        // drop a cell whose centre lies within the cutoff
+        const float rx = (float)Rx, ry = (float)Ry, rc = I.f_rcut;
+        ylo = (int)floorf(ry - rc - 0.5f) - 1;
+        yhi = (int)ceilf(ry + rc - 0.5f) + 1;
+        xlo = (int)floorf(rx - rc - 0.5f) - 1;
+        xhi = (int)ceilf(rx + rc - 0.5f) + 1;
+        if (xhi - xlo + 1 >= I.nx) {
+            xlo = (int)floorf(rx - 0.5f * (float)I.nx);
+            xhi = xlo + I.nx - 1;
+        }
+    } else {
+        ylo = (int)floor(Ry - I.rcut - 0.5) - 1;
+        yhi = (int)ceil(Ry + I.rcut - 0.5) + 1;
+        const double xl = floor(Rx - I.rcut - 0.5) - 1.0, xh = ceil(Rx + I.rcut - 0.5) + 1.0;
+        if (xh - xl + 1.0 >= (double)I.nx) {
+            const double x0 = floor(Rx - 0.5 * I.nx);
+            b.iu = x0;
+            const long long xi = (long long)x0;
+            b.i0 = (int)(((xi % I.nx) + I.nx) % I.nx);
+            b.w = I.nx;
+        } else {
+            b.iu = xl;
+            const long long xi = (long long)xl;
+            b.i0 = (int)(((xi % I.nx) + I.nx) % I.nx);
+            b.w = (int)(xh - xl) + 1;
+        }
+        ylo = ylo < 0 ? 0 : ylo;
+        yhi = yhi > I.ny - 1 ? I.ny - 1 : yhi;
+        if (yhi < ylo) {
+            b.w = 0;
+            return b;
+        }
+        b.j0 = ylo;
+        b.h = yhi - ylo + 1;
+        return b;
     }
-    b.iu = xlo;
-    const long long xl = (long long)xlo;
-    b.i0 = (int)(((xl % I.nx) + I.nx) % I.nx);  // in [0, nx)
-    b.j0 = (int)ylo;
-    b.w = (int)(xhi - xlo) + 1;
-    b.h = (int)(yhi - ylo) + 1;
+    ylo = ylo < 0 ? 0 : ylo;
+    yhi = yhi > I.ny - 1 ? I.ny - 1 : yhi;
+    if (yhi < ylo) return b;
+    b.iu = (double)xlo;
+    b.i0 = ((xlo % I.nx) + I.nx) % I.nx;  // in [0, nx)
+    b.j0 = ylo;
+    b.w = xhi - xlo + 1;
+    b.h = yhi - ylo + 1;
     return b;
 }
 
 // d reduced to its nearest periodic image in x: the image index is found in
 // FP32 (it is an integer) and removed exactly in FP64.
-__device__ __forceinline__ double min_image(double d, int nx) {
-    const float k = rintf((float)d / (float)nx);
+__device__ __forceinline__ double min_image(double d, int nx, float inv_nx) {
+    const float k = rintf((float)d * inv_nx);
     return d - (double)k * (double)nx;
 }
 
 // Force on bead q (instance-local index), given the instance's positions
 // and the unit tangents/lengths of every segment (index j joins beads j and
 // j+1 of the instance-local numbering), all staged in shared memory.
-__device__ void bead_force(const Inst &I, const double *Rx, const double *Ry, const double *Tx,
-                           const double *Ty, const double *Ln, int q, double &Fx, double &Fy) {
+__device__ void bead_force(const Inst &I, const double *Rx, const double *Ry, const float *Xf, const float *Yf,
+                           const double *Tx, const double *Ty, const double *Ln, int q, double &Fx, double &Fy) {
     const int N = I.n_beads;
     const int fib = q / N, i0 = q - fib * N;  // 0-based index within the fiber
     // segments around bead q, as in Eqs. 11-12 with 1-based i = i0 + 1:
@@ -113,7 +195,7 @@ __device__ void bead_force(const Inst &I, const double *Rx, const double *Ry, co
     const double tm1x = h_m1 ? Tx[q - 1] : 0.0, tm1y = h_m1 ? Ty[q - 1] : 0.0;
     const double tix = h_i ? Tx[q] : 0.0, tiy = h_i ? Ty[q] : 0.0;
     const double tp1x = h_p1 ? Tx[q + 1] : 0.0, tp1y = h_p1 ? Ty[q + 1] : 0.0;
-    const double ks = I.k_s / (I.l0 * I.l0);
+    const double ks = I.ks_l02;
     Fx = 0.0;
     Fy = 0.0;
     if (h_m1) {
@@ -144,14 +226,15 @@ __device__ void bead_force(const Inst &I, const double *Rx, const double *Ry, co
         const double Rqx = Rx[q], Rqy = Ry[q];
         const float l0f2 = (float)(I.l0 * I.l0) * 1.0201f;
         const float fnx = (float)I.nx;
+        const float xq = Xf[q], yq = Yf[q];
+        const int lo = fib * N;
         for (int p = 0; p < I.nb; ++p) {
-            if (p == q) continue;
-            if (p / N == fib && abs(p - q) < 2) continue;
-            float fx = (float)(Rqx - Rx[p]);
-            fx -= fnx * rintf(fx / fnx);
-            const float fy = (float)(Rqy - Ry[p]);
+            float fx = xq - Xf[p];
+            fx -= fnx * rintf(fx * I.f_inv_nx);
+            const float fy = yq - Yf[p];
             if (fx * fx + fy * fy >= l0f2) continue;
-            const double dx = min_image(Rqx - Rx[p], I.nx);
+            if (p == q || (p >= lo && p < lo + N && abs(p - q) < 2)) continue;
+            const double dx = min_image(Rqx - Rx[p], I.nx, I.f_inv_nx);
             const double dy = Rqy - Ry[p];
             const double r = sqrt(dx * dx + dy * dy);
             if (r < I.l0 && r > 0.0) {
@@ -163,10 +246,70 @@ __device__ void bead_force(const Inst &I, const double *Rx, const double *Ry, co
     }
 }
 
+// FP32 version of bead_force for the reduced-precision paths.  Positions
+// stay FP64; each segment's tangent and length are FP32, and its stretch
+// L - l0 = (|d|^2 - l0^2) / (L + l0) is formed from the FP64 |d|^2 so that
+// the small strain of a stiff spring does not cancel away in FP32.
+__device__ void bead_force_f32(const Inst &I, const double *Rx, const double *Ry, const float *Xf, const float *Yf,
+                               const float *Tx, const float *Ty, const float *Ln, const float *Dl, int q, float &Fx,
+                               float &Fy) {
+    const int N = I.n_beads;
+    const int fib = q / N, i0 = q - fib * N;
+    const bool h_m2 = i0 >= 2, h_m1 = i0 >= 1, h_i = i0 <= N - 2, h_p1 = i0 + 1 <= N - 2;
+    const float tm2x = h_m2 ? Tx[q - 2] : 0.f, tm2y = h_m2 ? Ty[q - 2] : 0.f;
+    const float tm1x = h_m1 ? Tx[q - 1] : 0.f, tm1y = h_m1 ? Ty[q - 1] : 0.f;
+    const float tix = h_i ? Tx[q] : 0.f, tiy = h_i ? Ty[q] : 0.f;
+    const float tp1x = h_p1 ? Tx[q + 1] : 0.f, tp1y = h_p1 ? Ty[q + 1] : 0.f;
+    const float ks = I.f_ks_l02, kb = I.f_kb;
+    Fx = 0.f;
+    Fy = 0.f;
+    if (h_m1) {
+        const float Lm1 = Ln[q - 1], dl = Dl[q - 1];
+        Fx -= ks * dl * tm1x;
+        Fy -= ks * dl * tm1y;
+        const float vx = tix + tm2x, vy = tiy + tm2y;
+        const float vt = vx * tm1x + vy * tm1y;
+        Fx += kb * (vx - vt * tm1x) / Lm1;
+        Fy += kb * (vy - vt * tm1y) / Lm1;
+    }
+    if (h_i) {
+        const float Li = Ln[q], dl = Dl[q];
+        Fx += ks * dl * tix;
+        Fy += ks * dl * tiy;
+        const float vx = tp1x + tm1x, vy = tp1y + tm1y;
+        const float vt = vx * tix + vy * tiy;
+        Fx -= kb * (vx - vt * tix) / Li;
+        Fy -= kb * (vy - vt * tiy) / Li;
+    }
+    if (I.k_ev != 0.0) {
+        // Xf, Yf: positions relative to bead 0 of the instance in FP32 (a
+        // screen with 1% margin); a candidate pair is evaluated from the
+        // FP64 positions
+        const float l0 = I.f_l0, l0s2 = l0 * l0 * 1.0201f, kev = I.f_kev;
+        const float fnx = (float)I.nx;
+        const float xq = Xf[q], yq = Yf[q];
+        const int lo = fib * N;
+        for (int p = 0; p < I.nb; ++p) {
+            float fx = xq - Xf[p];
+            fx -= fnx * rintf(fx * I.f_inv_nx);
+            const float fy = yq - Yf[p];
+            if (fx * fx + fy * fy >= l0s2) continue;
+            if (p == q || (p >= lo && p < lo + N && abs(p - q) < 2)) continue;
+            const double dx = min_image(Rx[q] - Rx[p], I.nx, I.f_inv_nx), dy = Ry[q] - Ry[p];
+            const float r = sqrtf((float)(dx * dx + dy * dy));
+            if (r < l0 && r > 0.f) {
+                const float m = kev * (l0 - r) / r;
+                Fx += m * (float)dx;
+                Fy += m * (float)dy;
+            }
+        }
+    }
+}
+
 template <class S>
 __global__ void __launch_bounds__(kBeadThreads)
-    k_beads(const Inst *__restrict__ insts, const int *__restrict__ bead_inst, const S *__restrict__ pool,
-            const BeadTab told, const BeadTab tnew, unsigned *__restrict__ mask_write, int parity, int advance,
+    k_beads(const Inst *__restrict__ insts, const int2 *__restrict__ blist, const S *__restrict__ pool,
+            const BeadTab tab0, const BeadTab tab1, unsigned *__restrict__ mask_write, int gparity, int advance,
             unsigned *__restrict__ counters) {
     constexpr bool kF64 = std::is_same<S, double>::value;
     __shared__ Inst sI;
@@ -176,19 +319,31 @@ __global__ void __launch_bounds__(kBeadThreads)
     __shared__ double s_rx[kMaxBeads], s_ry[kMaxBeads], s_gx[kMaxBeads], s_gy[kMaxBeads];
     __shared__ double s_tx[kMaxBeads], s_ty[kMaxBeads], s_ln[kMaxBeads];
     __shared__ float s_ox[kMaxBeads], s_oy[kMaxBeads], s_gxf[kMaxBeads], s_gyf[kMaxBeads];
+    __shared__ float s_xf[kMaxBeads], s_yf[kMaxBeads];
     __shared__ double sh[2][kWarps];
     __shared__ double s_R[2];
     __shared__ float s_rel[2];
     __shared__ Box s_box;
     __shared__ int s_last, s_nn;
 
-    const int b = blockIdx.x;
-    const int ii = bead_inst ? bead_inst[b] : 0;
+    // blist[i] = (instance slot, global bead index); NULL: instance 0, bead i
+    const int2 bi = blist ? blist[blockIdx.x] : make_int2(0, (int)blockIdx.x);
+    const int ii = bi.x, b = bi.y;
     const int tid = threadIdx.x;
-    if (tid == 0) sI = insts[ii];
+    {
+        // cooperative copy of the instance record (one 32-bit word a thread)
+        static_assert(sizeof(Inst) % 4 == 0, "Inst is copied as 32-bit words");
+        const unsigned *src = (const unsigned *)(insts + ii);
+        unsigned *dst = (unsigned *)&sI;
+        for (int wd = tid; wd < (int)(sizeof(Inst) / 4); wd += blockDim.x) dst[wd] = src[wd];
+    }
     __syncthreads();
     const Inst &I = sI;
     const S *A = pool + I.pop_off;
+    // this instance's step parity selects the table pair and the layout
+    const int parity = gparity ^ I.par_xor;
+    const BeadTab &told = parity ? tab0 : tab1;
+    const BeadTab &tnew = parity ? tab1 : tab0;
 
     if (advance) {
         if (tid == 0) {
@@ -214,7 +369,7 @@ __global__ void __launch_bounds__(kBeadThreads)
                     qx = told.Rx[I.bead_off + q];
                     qy = told.Ry[I.bead_off + q];
                     float dx = (float)(qx - Rx);
-                    dx -= fnx * rintf(dx / fnx);
+                    dx -= fnx * rintf(dx * I.f_inv_nx);
                     const float dy = (float)(qy - Ry);
                     hit = dx * dx + dy * dy < reach * reach;
                 }
@@ -223,7 +378,7 @@ __global__ void __launch_bounds__(kBeadThreads)
                     const int pos = n + __popc(m & ((1u << tid) - 1u));
                     s_rx[pos] = qx;
                     s_ry[pos] = qy;
-                    s_ox[pos] = (float)min_image(Rx - qx, I.nx);
+                    s_ox[pos] = (float)min_image(Rx - qx, I.nx, I.f_inv_nx);
                     s_oy[pos] = (float)(Ry - qy);
                     const double gx = told.Gx[I.bead_off + q], gy = told.Gy[I.bead_off + q];
                     s_gx[pos] = gx;
@@ -236,6 +391,10 @@ __global__ void __launch_bounds__(kBeadThreads)
             if (tid == 0) s_nn = n;
         }
         __syncthreads();
+        // everything above read only the previous bead table; the
+        // populations below come from the sweep that precedes this launch
+        pdl_wait();
+        pdl_trigger();
         const int nn = s_nn;
         const Box bx = s_box;
         const float rel0x = s_rel[0], rel0y = s_rel[1];
@@ -291,11 +450,8 @@ __global__ void __launch_bounds__(kBeadThreads)
                 ayf += phb * ((jy + 0.5f * fy) * irho);
             }
         }
-        if constexpr (!kF64) {
-            ax = (double)axf;
-            ay = (double)ayf;
-        }
-        block_sum2_to0(ax, ay, sh);
+        if constexpr (kF64) block_sum2_to0(ax, ay, sh);
+        else block_sum2f_to0(axf, ayf, ax, ay, sh);
         if (tid == 0) {
             const double inv_S = 1.0 / told.S[b];
             const double Vx = ax * inv_S, Vy = ay * inv_S;
@@ -312,6 +468,8 @@ __global__ void __launch_bounds__(kBeadThreads)
             s_rel[1] = (float)(nb_.j0 + 0.5 - Rny);
         }
     } else if (tid == 0) {
+        pdl_wait();
+        pdl_trigger();
         const double Rx = tnew.Rx[b], Ry = tnew.Ry[b];
         const Box bx = support_box(I, Rx, Ry);
         s_R[0] = Rx;
@@ -359,8 +517,8 @@ __global__ void __launch_bounds__(kBeadThreads)
                 part += phi_f32(rel0x + (float)ci, rel0y + (float)cj, I.f_a, I.f_inv_xi, I.f_rcut2);
             }
         }
-        if constexpr (!kF64) acc = (double)part;
-        block_sum2_to0(acc, dummy, sh);
+        if constexpr (kF64) block_sum2_to0(acc, dummy, sh);
+        else block_sum2f_to0(part, 0.0f, acc, dummy, sh);
         if (tid == 0) tnew.S[b] = acc;
     }
 
@@ -383,29 +541,53 @@ __global__ void __launch_bounds__(kBeadThreads)
     }
     __syncthreads();
     for (int q = tid; q < I.nb; q += blockDim.x) {
+        s_xf[q] = (float)(s_rx[q] - s_rx[0]);
+        s_yf[q] = (float)(s_ry[q] - s_ry[0]);
+    }
+    for (int q = tid; q < I.nb; q += blockDim.x) {
         if ((q + 1) % I.n_beads != 0) {
             const double dx = s_rx[q + 1] - s_rx[q], dy = s_ry[q + 1] - s_ry[q];
-            const double L = sqrt(dx * dx + dy * dy);
-            const double iL = 1.0 / L;
-            s_tx[q] = dx * iL;
-            s_ty[q] = dy * iL;
-            s_ln[q] = L;
+            if constexpr (kF64) {
+                const double L = sqrt(dx * dx + dy * dy);
+                const double iL = 1.0 / L;
+                s_tx[q] = dx * iL;
+                s_ty[q] = dy * iL;
+                s_ln[q] = L;
+            } else {
+                const double d2 = dx * dx + dy * dy;
+                const float L = sqrtf((float)d2);
+                s_ox[q] = (float)dx / L;                                // tangent x
+                s_oy[q] = (float)dy / L;                                // tangent y
+                s_gxf[q] = L;                                           // length
+                s_gyf[q] = (float)(d2 - I.l0 * I.l0) / (L + I.f_l0);  // L - l0
+            }
         }
     }
     __syncthreads();
     for (int q = tid; q < I.nb; q += blockDim.x) {
-        double Fx, Fy;
-        bead_force(I, s_rx, s_ry, s_tx, s_ty, s_ln, q, Fx, Fy);
+        double Fx, Fy, Gx, Gy;
+        if constexpr (kF64) {
+            bead_force(I, s_rx, s_ry, s_xf, s_yf, s_tx, s_ty, s_ln, q, Fx, Fy);
+            const double inv_S = 1.0 / s_gx[q];
+            Gx = Fx * inv_S;
+            Gy = Fy * inv_S;
+        } else {
+            float fx, fy;
+            bead_force_f32(I, s_rx, s_ry, s_xf, s_yf, s_ox, s_oy, s_gxf, s_gyf, q, fx, fy);
+            const float inv_S = 1.0f / (float)s_gx[q];
+            Fx = fx;
+            Fy = fy;
+            Gx = fx * inv_S;
+            Gy = fy * inv_S;
+        }
         const int gq = I.bead_off + q;
-        const double inv_S = 1.0 / s_gx[q];
-        const double Gx = Fx * inv_S, Gy = Fy * inv_S;
         tnew.Fx[gq] = Fx;
         tnew.Fy[gq] = Fy;
         tnew.Gx[gq] = Gx;
         tnew.Gy[gq] = Gy;
         // FP32 overlay table: x wrapped into [0, nx), split into hi + lo
         const double rx = s_rx[q];
-        double xw = rx - (double)floorf((float)rx / (float)I.nx) * (double)I.nx;
+        double xw = rx - (double)floorf((float)rx * I.f_inv_nx) * (double)I.nx;
         xw = (xw < 0.0) ? xw + I.nx : ((xw >= I.nx) ? xw - I.nx : xw);
         const double yw = s_ry[q];
         const float xh = (float)xw, yh = (float)yw;
@@ -421,27 +603,31 @@ __global__ void __launch_bounds__(kBeadThreads)
 
 }  // namespace
 
-cudaError_t launch_beads(int precision, const Inst *inst_d, const int *bead_inst, int nb_total, const void *pool,
-                         BeadTab tab_old, BeadTab tab_new, unsigned *mask_write, int parity, int advance,
-                         unsigned *counters, cudaStream_t st) {
+cudaError_t launch_beads(int precision, const Inst *inst_d, const int2 *blist, int nb_total, const void *pool,
+                         BeadTab tab0, BeadTab tab1, unsigned *mask_write, int gparity, int advance,
+                         unsigned *counters, int pdl, cudaStream_t st) {
     if (nb_total <= 0) return cudaSuccess;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nb_total);
+    cfg.blockDim = dim3(kBeadThreads);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
     switch (precision) {
         case 0:
-            k_beads<double><<<nb_total, kBeadThreads, 0, st>>>(inst_d, bead_inst, (const double *)pool, tab_old,
-                                                              tab_new, mask_write, parity, advance, counters);
-            break;
+            return cudaLaunchKernelEx(&cfg, k_beads<double>, inst_d, blist, (const double *)pool, tab0, tab1,
+                                      mask_write, gparity, advance, counters);
         case 1:
-            k_beads<float><<<nb_total, kBeadThreads, 0, st>>>(inst_d, bead_inst, (const float *)pool, tab_old,
-                                                             tab_new, mask_write, parity, advance, counters);
-            break;
+            return cudaLaunchKernelEx(&cfg, k_beads<float>, inst_d, blist, (const float *)pool, tab0, tab1,
+                                      mask_write, gparity, advance, counters);
         case 2:
-            k_beads<__half><<<nb_total, kBeadThreads, 0, st>>>(inst_d, bead_inst, (const __half *)pool, tab_old,
-                                                              tab_new, mask_write, parity, advance, counters);
-            break;
-        default:
-            return cudaErrorInvalidValue;
+            return cudaLaunchKernelEx(&cfg, k_beads<__half>, inst_d, blist, (const __half *)pool, tab0, tab1,
+                                      mask_write, gparity, advance, counters);
     }
-    return cudaGetLastError();
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace fpd

@@ -34,6 +34,8 @@ struct Inst {
     int32_t ntx, nty;     // lattice tiles (kTileX x kTileY cells) in x and y
     int32_t tile_base;    // first tile of this instance in the tile-mask arrays
     int32_t mask_words;   // 32-bit words per tile mask: ceil(nb / 32), >= 1
+    int32_t par_xor;      // local step parity = global step parity ^ par_xor
+    int32_t pad1_;
     double s_e, s_eps, s_q;
     float scale[9];       // FP16 storage: stored = (f_k - w_k) * scale[k]
     float inv_scale[9];
@@ -46,6 +48,9 @@ struct Inst {
     float fluid_rates_f[4];
     float f_nu_f, f_visc_m1, f_gx, f_gy, f_a, f_inv_xi, f_rcut, f_rcut2;
     float f_s_e, f_s_eps, f_s_q;
+    // bead-force constants: k_s / l0^2, k_b, k_ev, l0, 1 / nx
+    double ks_l02;
+    float f_ks_l02, f_kb, f_kev, f_l0, f_inv_nx;
 };
 
 template <class R> __device__ __forceinline__ R bb_term(const Inst &I, int wall, int k);
@@ -65,6 +70,16 @@ struct BeadTab {
 };
 constexpr int kTabDoubles = 9;  // per bead
 constexpr int kTabFloats = 6;
+
+// ------------------------------------------------- programmatic dependent launch
+// A kernel launched with programmatic stream serialization may start while
+// its predecessor in the stream is still running.  Every kernel of the step
+// sequence therefore touches, before pdl_wait(), only data whose producers
+// are at least two launches back, and signals its own dependents only after
+// pdl_wait() has returned (so the chain stays transitively ordered).  Both
+// instructions are no-ops for a kernel launched without the attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 // ---------------------------------------------------------------- storage
 template <class T> struct Store;

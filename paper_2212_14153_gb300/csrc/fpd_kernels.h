@@ -16,16 +16,32 @@ constexpr int kBeadThreads = 256;
 // item (2) with the item-(1) overlay of Eqs. 1, 2, 4 evaluated in hot tiles).
 // mask_read: the per-tile bead masks written by the bead phase of this step;
 // mask_clear: the other mask buffer, zeroed for the next bead phase.
+// after_beads = 1 when the previous launch on the stream is the bead phase
+// of the same step: the sweep is then launched as a programmatic dependent
+// of it and loads its populations before waiting for it.
 cudaError_t launch_lattice(int precision, const Inst *inst_d, const Inst &inst_h, void *pool, BeadTab tab,
-                           const unsigned *mask_read, unsigned *mask_clear, int parity, cudaStream_t st);
+                           const unsigned *mask_read, unsigned *mask_clear, int parity, int after_beads,
+                           cudaStream_t st);
 
-// Bead phase (items (3) then (1)): one CTA per bead.  advance = 0 only
-// computes S and F of tab_new from its own R (initialisation).  Every bead
-// ORs its bit into the mask of each lattice tile its support reaches
-// (mask_write, zeroed beforehand).
-cudaError_t launch_beads(int precision, const Inst *inst_d, const int *bead_inst, int nb_total,
-                         const void *pool, BeadTab tab_old, BeadTab tab_new, unsigned *mask_write, int parity,
-                         int advance, unsigned *counters, cudaStream_t st);
+// Bead phase (items (3) then (1)): one CTA per bead of any instance
+// (blist[i] = (instance slot, global bead index); NULL = instance 0, bead i;
+// every bead of an instance must be in the same launch).  With the instance's
+// step parity p = gparity ^ par_xor it reads table p ^ 1 and writes table p
+// (tab0 / tab1); advance = 0 only computes S and F of table p from its own R
+// (initialisation).  Every bead ORs its bit into the mask of each lattice
+// tile its support reaches (mask_write, zeroed beforehand).
+// pdl = 1 launches the bead phase as a programmatic dependent of the
+// previous sweep: its prologue (instance record, neighbour list, support
+// box, all from the previous bead table) overlaps the sweep's tail.
+cudaError_t launch_beads(int precision, const Inst *inst_d, const int2 *blist, int nb_total,
+                         const void *pool, BeadTab tab0, BeadTab tab1, unsigned *mask_write, int gparity,
+                         int advance, unsigned *counters, int pdl, cudaStream_t st);
+
+// Batched sweep over a packed tile list of many instances (tiles[t] =
+// (slot, by << 16 | bx)); each instance at its own parity.
+cudaError_t launch_lattice_batch(int precision, const Inst *insts, const int2 *tiles, int ntiles, void *pool,
+                                 BeadTab tab0, BeadTab tab1, const unsigned *mask_read, unsigned *mask_clear,
+                                 int gparity, int after_beads, cudaStream_t st);
 
 cudaError_t launch_init(int precision, const Inst *inst_d, const Inst &inst_h, void *pool, int couette,
                         cudaStream_t st);

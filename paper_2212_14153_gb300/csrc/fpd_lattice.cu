@@ -26,23 +26,30 @@ template <> struct Real<double> { using type = double; };
 
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 
+// One cell of the sweep: tile (bx, by) of instance I, at the instance's
+// step parity; the CTA's thread (threadIdx.x, threadIdx.y) owns one cell.
 template <class S>
-__global__ void __launch_bounds__(kTileX *kTileY)
-    k_lattice(const Inst I, S *__restrict__ pool, const BeadTab tab, const unsigned *__restrict__ mask_read,
-              unsigned *__restrict__ mask_clear, const int parity) {
+__device__ __forceinline__ void lattice_cell(const Inst &I, S *__restrict__ pool, const BeadTab &tab,
+                                             const unsigned *__restrict__ mask_read, unsigned *__restrict__ mask_clear,
+                                             const int bx, const int by, const int parity, const int early_load) {
     using R = typename Real<S>::type;
     constexpr bool kF64 = std::is_same<R, double>::value;
-    const int x = blockIdx.x * kTileX + threadIdx.x, y = blockIdx.y * kTileY + threadIdx.y;
-    const int tile = I.tile_base + blockIdx.y * I.ntx + blockIdx.x;
+    const int x = bx * kTileX + threadIdx.x, y = by * kTileY + threadIdx.y;
+    const int tile = I.tile_base + by * I.ntx + bx;
     const int W = I.mask_words;
+    const bool valid = x < I.nx && y < I.ny;
+    S *A = pool + I.pop_off;
+    const Cell C = make_cell(I, x, valid ? y : 0);
+    R g[9];
+    // populations come from the previous sweep; when the bead phase runs
+    // between the two sweeps they may be loaded before waiting on it
+    if (early_load && valid) load_pops<S, R>(A, I, C, parity, g);
+    pdl_wait();
+    pdl_trigger();
     if (threadIdx.x == 0 && threadIdx.y == 0)  // the other parity's mask, for the next bead phase
         for (int w = 0; w < W; ++w) mask_clear[tile * W + w] = 0u;
-    if (x >= I.nx || y >= I.ny) return;
-    S *A = pool + I.pop_off;
-    const Cell C = make_cell(I, x, y);
-    R g[9];
-    load_pops<S, R>(A, I, C, parity, g);
-
+    if (!valid) return;
+    if (!early_load) load_pops<S, R>(A, I, C, parity, g);
     const unsigned *m = mask_read + tile * W;
     unsigned any = 0u;
     for (int w = 0; w < W; ++w) any |= m[w];
@@ -113,6 +120,35 @@ __global__ void __launch_bounds__(kTileX *kTileY)
     store_pops<S, R>(A, I, C, parity, g);
 }
 
+template <class S>
+__global__ void __launch_bounds__(kTileX *kTileY)
+    k_lattice(const Inst I, S *__restrict__ pool, const BeadTab tab, const unsigned *__restrict__ mask_read,
+              unsigned *__restrict__ mask_clear, const int parity, const int early_load) {
+    lattice_cell<S>(I, pool, tab, mask_read, mask_clear, blockIdx.x, blockIdx.y, parity, early_load);
+}
+
+// Batched sweep over a packed tile list: tiles[t] = (instance slot,
+// by << 16 | bx).  Each instance reads table and layout of its own parity
+// (global parity ^ par_xor); the record is copied to shared memory per CTA.
+template <class S>
+__global__ void __launch_bounds__(kTileX *kTileY)
+    k_lattice_batch(const Inst *__restrict__ insts, const int2 *__restrict__ tiles, S *__restrict__ pool,
+                    const BeadTab tab0, const BeadTab tab1, const unsigned *__restrict__ mask_read,
+                    unsigned *__restrict__ mask_clear, const int gparity, const int early_load) {
+    __shared__ Inst sI;
+    const int2 t = tiles[blockIdx.x];
+    {
+        const unsigned *src = (const unsigned *)(insts + t.x);
+        unsigned *dst = (unsigned *)&sI;
+        const int tid = threadIdx.y * kTileX + threadIdx.x;
+        for (int wd = tid; wd < (int)(sizeof(Inst) / 4); wd += kTileX * kTileY) dst[wd] = src[wd];
+    }
+    __syncthreads();
+    const int parity = gparity ^ sI.par_xor;
+    lattice_cell<S>(sI, pool, parity ? tab1 : tab0, mask_read, mask_clear, t.y & 0xffff, t.y >> 16, parity,
+                    early_load);
+}
+
 // Equilibrium start: f_k = f_k^eq(rho = 1, u = (u_wall(y), 0)) with the
 // linear wall profile, or the rest state; stored as deviations for parity 0.
 template <class S>
@@ -141,7 +177,9 @@ __device__ __forceinline__ void overlay_f64(const Inst &I, const BeadTab &tab, c
     const int tile = I.tile_base + (y / kTileY) * I.ntx + x / kTileX;
     const double xc = x + 0.5, yc = y + 0.5;
     for (int w = 0; w < I.mask_words; ++w) {
-        unsigned bits = mask[tile * I.mask_words + w];
+        // without masks every bead of the instance is visited (cutoff exact)
+        const int left = I.nb - 32 * w;
+        unsigned bits = mask ? mask[tile * I.mask_words + w] : (left >= 32 ? 0xffffffffu : ((1u << left) - 1u));
         while (bits) {
             const int q = I.bead_off + 32 * w + __ffs(bits) - 1;
             bits &= bits - 1u;
@@ -269,19 +307,55 @@ __global__ void __launch_bounds__(kDiagThreads)
 // ---------------------------------------------------------------- launchers
 template <class S>
 static cudaError_t lattice_t(const Inst &I, void *pool, BeadTab tab, const unsigned *mask_read,
-                             unsigned *mask_clear, int parity, cudaStream_t st) {
-    dim3 block(kTileX, kTileY);
-    dim3 grid(I.ntx, I.nty);
-    k_lattice<S><<<grid, block, 0, st>>>(I, (S *)pool, tab, mask_read, mask_clear, parity);
-    return cudaGetLastError();
+                             unsigned *mask_clear, int parity, int after_beads, cudaStream_t st) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(I.ntx, I.nty);
+    cfg.blockDim = dim3(kTileX, kTileY);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = after_beads ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k_lattice<S>, I, (S *)pool, tab, mask_read, mask_clear, parity, after_beads);
 }
 
 cudaError_t launch_lattice(int precision, const Inst *, const Inst &inst_h, void *pool, BeadTab tab,
-                           const unsigned *mask_read, unsigned *mask_clear, int parity, cudaStream_t st) {
+                           const unsigned *mask_read, unsigned *mask_clear, int parity, int after_beads,
+                           cudaStream_t st) {
     switch (precision) {
-        case 0: return lattice_t<double>(inst_h, pool, tab, mask_read, mask_clear, parity, st);
-        case 1: return lattice_t<float>(inst_h, pool, tab, mask_read, mask_clear, parity, st);
-        case 2: return lattice_t<__half>(inst_h, pool, tab, mask_read, mask_clear, parity, st);
+        case 0: return lattice_t<double>(inst_h, pool, tab, mask_read, mask_clear, parity, after_beads, st);
+        case 1: return lattice_t<float>(inst_h, pool, tab, mask_read, mask_clear, parity, after_beads, st);
+        case 2: return lattice_t<__half>(inst_h, pool, tab, mask_read, mask_clear, parity, after_beads, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <class S>
+static cudaError_t lattice_batch_t(const Inst *insts, const int2 *tiles, int ntiles, void *pool, BeadTab tab0,
+                                   BeadTab tab1, const unsigned *mask_read, unsigned *mask_clear, int gparity,
+                                   int after_beads, cudaStream_t st) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(ntiles);
+    cfg.blockDim = dim3(kTileX, kTileY);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = after_beads ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k_lattice_batch<S>, insts, tiles, (S *)pool, tab0, tab1, mask_read, mask_clear,
+                              gparity, after_beads);
+}
+
+cudaError_t launch_lattice_batch(int precision, const Inst *insts, const int2 *tiles, int ntiles, void *pool,
+                                 BeadTab tab0, BeadTab tab1, const unsigned *mask_read, unsigned *mask_clear,
+                                 int gparity, int after_beads, cudaStream_t st) {
+    if (ntiles <= 0) return cudaSuccess;
+    switch (precision) {
+        case 0: return lattice_batch_t<double>(insts, tiles, ntiles, pool, tab0, tab1, mask_read, mask_clear, gparity, after_beads, st);
+        case 1: return lattice_batch_t<float>(insts, tiles, ntiles, pool, tab0, tab1, mask_read, mask_clear, gparity, after_beads, st);
+        case 2: return lattice_batch_t<__half>(insts, tiles, ntiles, pool, tab0, tab1, mask_read, mask_clear, gparity, after_beads, st);
     }
     return cudaErrorInvalidValue;
 }

@@ -36,3 +36,12 @@ struct fpd_sim {
     double ms[2] = {0, 0};
     double launches[2] = {0, 0};
 };
+
+namespace fpd {
+// Validate p and fill s->inst and the derived constants of s (no device
+// work).  On error the text is available from create_error().
+int derive_params(fpd_sim *s, const fpd_params &p);
+const char *create_error();
+// Initial bead positions of p (false if any is not finite).
+bool initial_beads(const fpd_params &p, double l0, std::vector<double> &Rx, std::vector<double> &Ry);
+}  // namespace fpd

@@ -69,6 +69,22 @@ SIGNATURES = {
     "fpd_kernel_times": (ctypes.c_int, [ctypes.c_void_p, _DP]),
     "fpd_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "fpd_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "fpd_batch_create": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32,
+                                        ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "fpd_batch_add": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(fpd_params), ctypes.c_int64,
+                                     ctypes.POINTER(ctypes.c_int32)]),
+    "fpd_batch_run": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
+    "fpd_batch_sync": (ctypes.c_int, [ctypes.c_void_p]),
+    "fpd_batch_poll": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32,
+                                      ctypes.POINTER(ctypes.c_int32)]),
+    "fpd_batch_slot_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64)]),
+    "fpd_batch_read_fields": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, _DP, _DP, _DP]),
+    "fpd_batch_read_beads": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, _DP, _DP, _DP, _DP]),
+    "fpd_batch_read_populations": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, _DP]),
+    "fpd_batch_remove": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "fpd_batch_stats": (ctypes.c_int, [ctypes.c_void_p, _DP]),
+    "fpd_batch_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "fpd_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
 }
 
 
@@ -274,3 +290,147 @@ class Simulation:
         out = np.zeros(4)
         fpd_kernel_times(self.h, out)
         return dict(lattice_ms=out[0], lattice_launches=int(out[1]), bead_ms=out[2], bead_launches=int(out[3]))
+
+
+# ------------------------------------------------------------ batches
+def _bcheck(rc: int, b):
+    if rc != FPD_OK:
+        msg = load_library().fpd_batch_last_error(b)
+        raise FpdError(rc, msg.decode() if msg else "")
+
+
+def fpd_batch_create(precision: int, max_slots: int, pool_bytes: int, max_beads: int, stream=None):
+    h = ctypes.c_void_p()
+    rc = load_library().fpd_batch_create(int(precision), int(max_slots), int(pool_bytes), int(max_beads), stream,
+                                         ctypes.byref(h))
+    if rc != FPD_OK:
+        raise FpdError(rc, "fpd_batch_create failed")
+    return h
+
+
+def fpd_batch_add(b, params: fpd_params, n_steps: int) -> int:
+    slot = ctypes.c_int32(-1)
+    _bcheck(load_library().fpd_batch_add(b, ctypes.byref(params), int(n_steps), ctypes.byref(slot)), b)
+    return slot.value
+
+
+def fpd_batch_run(b, max_steps: int) -> int:
+    done = ctypes.c_int64(0)
+    _bcheck(load_library().fpd_batch_run(b, int(max_steps), ctypes.byref(done)), b)
+    return done.value
+
+
+def fpd_batch_sync(b) -> None:
+    _bcheck(load_library().fpd_batch_sync(b), b)
+
+
+def fpd_batch_poll(b, capacity: int = 4096) -> list:
+    arr = (ctypes.c_int32 * capacity)()
+    n = ctypes.c_int32(0)
+    _bcheck(load_library().fpd_batch_poll(b, arr, capacity, ctypes.byref(n)), b)
+    return [arr[i] for i in range(n.value)]
+
+
+def fpd_batch_slot_info(b, slot: int) -> dict:
+    out = (ctypes.c_int64 * 6)()
+    _bcheck(load_library().fpd_batch_slot_info(b, int(slot), out), b)
+    return dict(nx=out[0], ny=out[1], beads=out[2], steps_done=out[3], steps_req=out[4], state=out[5])
+
+
+def fpd_batch_read_fields(b, slot: int, ux, uy, rho) -> None:
+    _bcheck(load_library().fpd_batch_read_fields(b, int(slot), _ptr(ux), _ptr(uy), _ptr(rho)), b)
+
+
+def fpd_batch_read_beads(b, slot: int, pos, vel, force, support=None) -> None:
+    _bcheck(load_library().fpd_batch_read_beads(b, int(slot), _ptr(pos), _ptr(vel), _ptr(force), _ptr(support)), b)
+
+
+def fpd_batch_read_populations(b, slot: int, f) -> None:
+    _bcheck(load_library().fpd_batch_read_populations(b, int(slot), _ptr(f)), b)
+
+
+def fpd_batch_remove(b, slot: int) -> None:
+    _bcheck(load_library().fpd_batch_remove(b, int(slot)), b)
+
+
+def fpd_batch_stats(b) -> dict:
+    out = np.zeros(8)
+    _bcheck(load_library().fpd_batch_stats(b, _ptr(out)), b)
+    keys = ["running", "cells", "finished", "pool_used", "pool_bytes", "global_steps", "cell_updates", "beads"]
+    return dict(zip(keys, out.tolist()))
+
+
+def fpd_batch_last_error(b) -> str:
+    msg = load_library().fpd_batch_last_error(b)
+    return msg.decode() if msg else ""
+
+
+def fpd_batch_destroy(b) -> None:
+    if b is not None and b.value:
+        load_library().fpd_batch_destroy(b)
+
+
+class Batch:
+    """Many FPD instances advanced together on the GPU (C ABI fpd_batch_*)."""
+
+    def __init__(self, precision: int, max_slots: int, pool_bytes: int, max_beads: int, stream=None):
+        if stream is None:
+            import torch
+            if not torch.cuda.is_available():
+                raise RuntimeError("no CUDA device: the FPD library runs on the GPU only")
+            stream = torch.cuda.current_stream().cuda_stream
+        self.h = fpd_batch_create(precision, max_slots, pool_bytes, max_beads, stream)
+        self.precision = precision
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            fpd_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add(self, cfg: dict, n_steps: int) -> int:
+        p, keep = params_from_config(cfg)
+        return fpd_batch_add(self.h, p, n_steps)
+
+    def run(self, max_steps: int) -> int:
+        return fpd_batch_run(self.h, max_steps)
+
+    def sync(self):
+        fpd_batch_sync(self.h)
+
+    def poll(self) -> list:
+        return fpd_batch_poll(self.h)
+
+    def info(self, slot: int) -> dict:
+        return fpd_batch_slot_info(self.h, slot)
+
+    def fields(self, slot: int):
+        i = self.info(slot)
+        ux = np.zeros((i["ny"], i["nx"])); uy = np.zeros_like(ux); rho = np.zeros_like(ux)
+        fpd_batch_read_fields(self.h, slot, ux, uy, rho)
+        return ux, uy, rho
+
+    def beads(self, slot: int):
+        i = self.info(slot)
+        n = max(i["beads"], 1)
+        R = np.zeros((n, 2)); V = np.zeros((n, 2)); F = np.zeros((n, 2)); S = np.zeros(n)
+        fpd_batch_read_beads(self.h, slot, R, V, F, S)
+        k = i["beads"]
+        return R[:k], V[:k], F[:k], S[:k]
+
+    def populations(self, slot: int):
+        i = self.info(slot)
+        f = np.zeros((9, i["ny"], i["nx"]))
+        fpd_batch_read_populations(self.h, slot, f)
+        return f
+
+    def remove(self, slot: int):
+        fpd_batch_remove(self.h, slot)
+
+    def stats(self) -> dict:
+        return fpd_batch_stats(self.h)

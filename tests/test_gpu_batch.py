@@ -1,0 +1,130 @@
+"""Batched engine (fpd_batch_*): many instances advanced by the same launches.
+
+Every instance must give exactly the numbers it gives alone (the kernels never
+mix instances and reduce per instance in a fixed order), whatever its
+companions, its slot, its pool offset, or the global step at which it was
+admitted.  Compared bit for bit with the single-instance API.
+"""
+import numpy as np
+import pytest
+
+from paper_2212_14153_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fpd():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2212_14153_gb300 import build, fpd as binding
+    build.build()
+    return binding
+
+
+def _cases(precision):
+    rng = np.random.default_rng(40 + precision)
+    return [
+        wl.random_fiber(rng, 70, 37, n_beads=5, a=2.0, xi=1.0, precision=precision),
+        wl.random_fiber(rng, 96, 48, n_beads=6, a=2.0, xi=0.5, n_fibers=2, precision=precision),
+        wl.couette_only(40, 24, u=0.01, nu=0.2, precision=precision),
+        wl.random_fiber(rng, 33, 17, n_beads=4, a=2.0, xi=1.0, precision=precision, collision=1),
+    ]
+
+
+def _alone(fpd, cfg, steps):
+    s = fpd.Simulation(cfg)
+    s.step(steps)
+    out = s.populations(), s.beads()
+    s.close()
+    return out
+
+
+def _same(a, b):
+    fa, ba = a
+    fb, bb = b
+    assert np.array_equal(fa, fb)
+    for x, y in zip(ba, bb):
+        assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_batch_equals_alone_bit_for_bit(fpd, precision):
+    cases = _cases(precision)
+    steps = [41, 60, 17, 33]
+    b = fpd.Batch(precision, max_slots=8, pool_bytes=64 << 20, max_beads=256)
+    slots = [b.add(c, n) for c, n in zip(cases, steps)]
+    total = 0
+    while True:
+        d = b.run(1000)
+        if d == 0:
+            break
+        total += d
+    assert total == max(steps)
+    done = sorted(b.poll())
+    assert done == sorted(slots)
+    for c, n, s in zip(cases, steps, slots):
+        assert b.info(s)["steps_done"] == n
+        _same((b.populations(s), b.beads(s)), _alone(fpd, c, n))
+    b.close()
+
+
+def test_staggered_admission_and_slot_reuse(fpd):
+    cases = _cases(1)
+    b = fpd.Batch(1, max_slots=3, pool_bytes=64 << 20, max_beads=128)
+    s0 = b.add(cases[0], 50)
+    assert b.run(7) == 7
+    s1 = b.add(cases[1], 30)                 # joins at global step 7 (odd)
+    assert b.run(10) == 10
+    s2 = b.add(cases[3], 25)                 # joins at global step 17
+    while b.run(1000):
+        pass
+    assert sorted(b.poll()) == sorted([s0, s1, s2])
+    for c, n, s in [(cases[0], 50, s0), (cases[1], 30, s1), (cases[3], 25, s2)]:
+        _same((b.populations(s), b.beads(s)), _alone(fpd, c, n))
+    # free a slot and reuse it (and its pool room) for another instance
+    b.remove(s1)
+    s3 = b.add(cases[2], 12)
+    assert s3 == s1
+    while b.run(1000):
+        pass
+    _same((b.populations(s3), b.beads(s3)), _alone(fpd, cases[2], 12))
+    b.close()
+
+
+def test_admission_limits(fpd):
+    cfg = wl.couette_only(64, 64, precision=1)
+    pool = 9 * 64 * 64 * 4 * 2 + 4096          # room for two such lattices
+    b = fpd.Batch(1, max_slots=4, pool_bytes=pool, max_beads=8)
+    b.add(cfg, 5)
+    b.add(cfg, 5)
+    with pytest.raises(fpd.FpdError) as e:
+        b.add(cfg, 5)
+    assert e.value.code == fpd.FPD_EBUSY
+    rng = np.random.default_rng(3)
+    big = wl.random_fiber(rng, 32, 16, n_beads=9, a=1.5, xi=0.5, precision=1)
+    with pytest.raises(fpd.FpdError):          # 9 beads > room for 8
+        b.add(big, 5)
+    with pytest.raises(fpd.FpdError) as e:     # precision mismatch
+        b.add(wl.couette_only(16, 16, precision=0), 5)
+    assert e.value.code == fpd.FPD_EINVAL
+    st = b.stats()
+    assert st["running"] == 2 and st["pool_used"] > 0
+    b.close()
+
+
+def test_batched_sweep_instances_run_and_conserve_mass(fpd):
+    inst = wl.batched_sweep(n=24, seed=11)
+    b = fpd.Batch(1, max_slots=32, pool_bytes=1 << 30, max_beads=1024)
+    slots = [b.add(c, 200) for c in inst]
+    while b.run(64):
+        pass
+    for c, s in zip(inst, slots):
+        f = b.populations(s)
+        assert np.all(np.isfinite(f))
+        m = f.sum()
+        assert abs(m - c["nx"] * c["ny"]) / (c["nx"] * c["ny"]) < 1e-5
+        R = b.beads(s)[0]
+        assert np.all(np.isfinite(R))
+    b.close()
