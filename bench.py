@@ -50,7 +50,7 @@ def measured_peaks() -> dict:
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for name in ("fpd_lattice.cu", "fpd_device.cuh", "fpd_kernels.h"):
+    for name in ("fpd_lattice.cu", "fpd_device.cuh"):
         with open(os.path.join(ROOT, "paper_2212_14153_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -118,7 +118,7 @@ class ClockSampler:
 # ------------------------------------------------------------------ GPU arm
 def run_gpu(args, rank: int, world: int):
     import torch
-    from paper_2212_14153_gb300 import build, fpd, workloads
+    from paper_2212_14153_gb300 import build, fpd, replicas, workloads
 
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
@@ -164,11 +164,9 @@ def run_gpu(args, rank: int, world: int):
     sim.set_profiling(False)
     diag = sim.diag()
     sim.close()
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    mlups = cells * args.steps * world / (ms * 1e-3) / 1e6
+    # whole job: every rank's cell updates over the slowest rank's time
+    mlups = replicas.job_rate(cells * args.steps, ms * 1e-3) / 1e6
+    ms = replicas.max_over_ranks(ms)
 
     # ---- end to end through the public API with host buffers
     e2e_steps = max(1, min(args.steps, args.e2e_steps))
@@ -183,11 +181,7 @@ def run_gpu(args, rank: int, world: int):
     ux, uy, rho = sim.fields()
     sim.close()
     e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_mlups = cells * e2e_steps * world / e2e_s / 1e6
+    e2e_mlups = replicas.job_rate(cells * e2e_steps, e2e_s) / 1e6
     h2d_total = 200 + 8 * 2 * cfg["n_fibers"] * 2 + 8 * 2 * nb  # params, centres/angles, bead table
     d2h_step = 8 * 7 * nb                                        # R, V, F, S every step
     d2h_total = d2h_step * e2e_steps + 3 * 8 * cells             # + final u_x, u_y, rho

@@ -4,6 +4,7 @@
 
 #include <cmath>
 #include <cstdint>
+#include <cstdlib>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -200,6 +201,9 @@ void free_all(fpd_sim *s) {
     cudaFree(s->masks[0]);
     cudaFree(s->scratch);
     cudaFree(s->inst_d);
+    for (int p = 0; p < 2; ++p)
+        if (s->graph[p]) cudaGraphExecDestroy(s->graph[p]);
+    if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
     for (auto e : s->ev_pool) cudaEventDestroy(e);
     for (auto &r : s->recs) {
         cudaEventDestroy(r.a);
@@ -246,6 +250,75 @@ void harvest(fpd_sim *s) {
 // current bead table: the one that drove the last collision (step 0: the
 // initial table)
 int cur_tab(const fpd_sim *s) { return s->nstep == 0 ? 0 : (int)((s->nstep - 1) & 1); }
+
+}  // namespace
+
+namespace {
+
+// Enqueue one time step (bead phase for t >= 1, then the sweep) on `st`.
+// Consecutive launches are programmatic dependents unless profiled.
+int enqueue_step(fpd_sim *s, cudaStream_t st, int64_t t, bool profiled) {
+    const fpd::Inst &I = s->inst;
+    const int parity = (int)(t & 1);
+    cudaError_t e;
+    if (I.nb > 0 && t >= 1) {
+        cudaEvent_t a = nullptr, b = nullptr;
+        if (profiled) {
+            a = take_event(s);
+            b = take_event(s);
+            cudaEventRecord(a, st);
+        }
+        e = fpd::launch_beads(s->precision, s->inst_d, nullptr, I.nb, s->pool, s->tab[0], s->tab[1],
+                              s->masks[parity], parity, 1, s->counters, profiled ? 0 : 1, st);
+        if (e != cudaSuccess) return cuda_fail(s, e, "bead kernel launch");
+        if (profiled) {
+            cudaEventRecord(b, st);
+            s->recs.push_back({a, b, 1});
+        }
+    }
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (profiled) {
+        a = take_event(s);
+        b = take_event(s);
+        cudaEventRecord(a, st);
+    }
+    const int after_beads = (I.nb > 0 && t >= 1 && !profiled) ? 1 : 0;
+    e = fpd::launch_lattice(s->precision, s->inst_d, I, s->pool, s->tab[parity], s->masks[parity],
+                            s->masks[parity ^ 1], parity, after_beads, st);
+    if (e != cudaSuccess) return cuda_fail(s, e, "lattice kernel launch");
+    if (profiled) {
+        cudaEventRecord(b, st);
+        s->recs.push_back({a, b, 0});
+        if (s->recs.size() > 4096) harvest(s);
+    }
+    return FPD_OK;
+}
+
+// Capture kGraphSteps consecutive steps starting at parity p (t >= 1) on a
+// private stream and instantiate them; the graph replays on any stream.
+int capture_chunk(fpd_sim *s, int p) {
+    cudaError_t e;
+    if (!s->cap_stream && (e = cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+        return cuda_fail(s, e, "capture stream");
+    if ((e = cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+        return cuda_fail(s, e, "begin capture");
+    int rc = FPD_OK;
+    for (int i = 0; i < fpd::kGraphSteps && rc == FPD_OK; ++i) rc = enqueue_step(s, s->cap_stream, 2 + p + i, false);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(s->cap_stream, &g);
+    if (rc != FPD_OK) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(s, e, "end capture");
+    e = cudaGraphInstantiate(&s->graph[p], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        s->graph[p] = nullptr;
+        return cuda_fail(s, e, "graph instantiate");
+    }
+    return FPD_OK;
+}
 
 }  // namespace
 
@@ -322,6 +395,10 @@ int fpd_create(const fpd_params *p, void *stream, fpd_sim **out) {
     s->precision = p->precision;
     s->elem = elem_size(p->precision);
     s->stream = (cudaStream_t)stream;
+    {
+        const char *ng = std::getenv("FPD_NO_GRAPHS");
+        s->use_graphs = !(ng && ng[0] == '1');
+    }
     const fpd::Inst &I = s->inst;
     const int nb = I.nb;
     cudaError_t e;
@@ -384,42 +461,26 @@ int fpd_create(const fpd_params *p, void *stream, fpd_sim **out) {
 int fpd_step(fpd_sim *s, int64_t n_steps) {
     if (!s) return fail(nullptr, FPD_EINVAL, "fpd_step: NULL handle");
     if (n_steps < 0) return fail(s, FPD_EINVAL, "n_steps must be >= 0");
-    const fpd::Inst &I = s->inst;
-    for (int64_t t = 0; t < n_steps; ++t) {
-        const int parity = (int)(s->nstep & 1);
-        const int tnew = (int)(s->nstep & 1);
-        cudaError_t e;
-        if (I.nb > 0 && s->nstep >= 1) {
-            cudaEvent_t a = nullptr, b = nullptr;
-            if (s->profiling) {
-                a = take_event(s);
-                b = take_event(s);
-                cudaEventRecord(a, s->stream);
+    while (n_steps > 0) {
+        // whole chunks of the step loop replay a captured graph (one launch
+        // instead of two per step); the first step, remainders and profiled
+        // steps are launched directly
+        if (s->use_graphs && !s->profiling && s->nstep >= 1 && n_steps >= fpd::kGraphSteps) {
+            const int p = (int)(s->nstep & 1);
+            if (!s->graph[p]) {
+                int rc = capture_chunk(s, p);
+                if (rc != FPD_OK) return rc;
             }
-            e = fpd::launch_beads(s->precision, s->inst_d, nullptr, I.nb, s->pool, s->tab[0], s->tab[1],
-                                  s->masks[tnew], parity, 1, s->counters, s->profiling ? 0 : 1, s->stream);
-            if (e != cudaSuccess) return cuda_fail(s, e, "bead kernel launch");
-            if (s->profiling) {
-                cudaEventRecord(b, s->stream);
-                s->recs.push_back({a, b, 1});
-            }
+            cudaError_t e = cudaGraphLaunch(s->graph[p], s->stream);
+            if (e != cudaSuccess) return cuda_fail(s, e, "graph launch");
+            s->nstep += fpd::kGraphSteps;
+            n_steps -= fpd::kGraphSteps;
+            continue;
         }
-        cudaEvent_t a = nullptr, b = nullptr;
-        if (s->profiling) {
-            a = take_event(s);
-            b = take_event(s);
-            cudaEventRecord(a, s->stream);
-        }
-        const int after_beads = (I.nb > 0 && s->nstep >= 1 && !s->profiling) ? 1 : 0;
-        e = fpd::launch_lattice(s->precision, s->inst_d, I, s->pool, s->tab[tnew], s->masks[tnew],
-                                s->masks[tnew ^ 1], parity, after_beads, s->stream);
-        if (e != cudaSuccess) return cuda_fail(s, e, "lattice kernel launch");
-        if (s->profiling) {
-            cudaEventRecord(b, s->stream);
-            s->recs.push_back({a, b, 0});
-            if (s->recs.size() > 4096) harvest(s);
-        }
+        int rc = enqueue_step(s, s->stream, s->nstep, s->profiling);
+        if (rc != FPD_OK) return rc;
         s->nstep++;
+        --n_steps;
     }
     return FPD_OK;
 }

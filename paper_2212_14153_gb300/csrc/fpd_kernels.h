@@ -11,6 +11,7 @@ constexpr int kTileX = 32;       // lattice tile: 32 x 8 cells, one thread each
 constexpr int kTileY = 8;
 constexpr int kMaxBeads = 256;   // beads per instance (shared-memory tables)
 constexpr int kBeadThreads = 256;
+constexpr int kGraphSteps = 32;  // time steps per captured graph chunk
 
 // One fused collide-stream-bounce-back sweep of a single instance (Sec. 2.3
 // item (2) with the item-(1) overlay of Eqs. 1, 2, 4 evaluated in hot tiles).

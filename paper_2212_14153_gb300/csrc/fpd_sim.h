@@ -35,6 +35,10 @@ struct fpd_sim {
     std::vector<Rec> recs;
     double ms[2] = {0, 0};
     double launches[2] = {0, 0};
+    // captured step chunks, one per starting parity (see fpd_step)
+    bool use_graphs = true;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
 };
 
 namespace fpd {

@@ -272,3 +272,23 @@ def test_full_size_two_fiber_lattice_f64_and_f32():
         print(f"full size precision {precision}: rel L2 u {eu:.3e}, R {eR:.3e}")
         assert eu < tol_u and eR < tol_R
         g.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_graph_chunks_equal_direct_steps(precision):
+    # one fpd_step(n) call replays captured 32-step graphs; n calls of
+    # fpd_step(1) launch every kernel directly: the results must be identical
+    rng = np.random.default_rng(77)
+    cfg = wl.random_fiber(rng, 70, 37, n_beads=6, a=2.0, xi=1.0, n_fibers=2, precision=precision)
+    a = gpu_sim(cfg)
+    b = gpu_sim(cfg)
+    a.step(101)
+    for _ in range(101):
+        b.step(1)
+    assert np.array_equal(a.populations(), b.populations())
+    for x, y in zip(a.beads(), b.beads()):
+        assert np.array_equal(x, y)
+    a.step(64)           # chunks starting at an odd step
+    for _ in range(64):
+        b.step(1)
+    assert np.array_equal(a.populations(), b.populations())

@@ -1,0 +1,139 @@
+"""Precision study: each storage precision against the FP64 oracle and the
+FP64 GPU path (itself pinned to the oracle at 1e-12).
+
+Stated per result: velocity relative L2, bead-position relative L2 and
+largest |dR| (lattice units), and the tumbling half-period of a stiff fiber.
+Run with -s to see the table.  Bounds are the design's error budget:
+FP32 storage of f - w with FP32 math, FP16 storage of (f - w) 2^s with FP32
+math; bead integration and reductions in FP64 throughout.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2212_14153_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+THREADS = min(16, os.cpu_count() or 1)
+NAMES = {0: "f64", 1: "f32", 2: "f16-store"}
+
+
+@pytest.fixture(scope="module")
+def fpd():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2212_14153_gb300 import build, fpd as binding
+    build.build()
+    return binding
+
+
+def rel(a, b):
+    return float(np.sqrt(np.sum((a - b) ** 2) / np.sum(b ** 2)))
+
+
+def errors(sim, ref_u, ref_R):
+    ux, uy, _ = sim.fields()
+    R = sim.beads()[0]
+    return dict(u=rel(np.stack([ux, uy]), ref_u), R=rel(R, ref_R), dRmax=float(np.abs(R - ref_R).max()))
+
+
+def test_two_fiber_lattice_against_oracle(fpd):
+    # 4096 x 1024, two 20-bead fibers: every precision vs the oracle, 40 steps
+    base = wl.two_fiber_large()
+    steps = 40
+    o = oracle.Sim(dict(base, threads=THREADS))
+    o.step(steps)
+    oux, ouy, _ = o.fields()
+    ref_u, ref_R = np.stack([oux, ouy]), o.beads()[0]
+    bounds = {0: (1e-12, 1e-13), 1: (1e-5, 1e-9), 2: (5e-3, 1e-5)}
+    for p in (0, 1, 2):
+        s = fpd.Simulation(dict(base, precision=p))
+        s.step(steps)
+        e = errors(s, ref_u, ref_R)
+        s.close()
+        print(f"two-fiber 4096x1024, {steps} steps, {NAMES[p]} vs oracle: {e}")
+        assert e["u"] < bounds[p][0] and e["R"] < bounds[p][1]
+
+
+def test_two_fiber_lattice_long_against_fp64_gpu(fpd):
+    base = wl.two_fiber_large()
+    steps = 2000
+    ref = fpd.Simulation(dict(base, precision=0))
+    ref.step(steps)
+    ux, uy, _ = ref.fields()
+    ref_u, ref_R = np.stack([ux, uy]), ref.beads()[0]
+    ref.close()
+    for p, bu in ((1, 1e-4), (2, 3e-2)):
+        s = fpd.Simulation(dict(base, precision=p))
+        s.step(steps)
+        e = errors(s, ref_u, ref_R)
+        s.close()
+        print(f"two-fiber 4096x1024, {steps} steps, {NAMES[p]} vs f64 GPU: {e}")
+        assert e["u"] < bu
+
+
+def test_single_fiber_long_run_drift(fpd):
+    # 1024 x 256, 20-bead fairly flexible fiber, Re = 10: FP32 and FP16
+    # storage against the FP64 GPU path along a long run
+    base = wl.single_fiber_medium()
+    checkpoints = [10_000, 50_000, 100_000, 200_000]
+    sims = {p: fpd.Simulation(dict(base, precision=p)) for p in (0, 1, 2)}
+    done = 0
+    for c in checkpoints:
+        for s in sims.values():
+            s.step(c - done)
+        done = c
+        ux, uy, _ = sims[0].fields()
+        ref_u, ref_R = np.stack([ux, uy]), sims[0].beads()[0]
+        for p in (1, 2):
+            e = errors(sims[p], ref_u, ref_R)
+            print(f"single-fiber 1024x256, {c} steps, {NAMES[p]} vs f64 GPU: {e}")
+            if p == 1:
+                assert e["u"] < 2e-3 and e["dRmax"] < 0.05
+            else:
+                assert e["u"] < 1e-1 and np.isfinite(e["dRmax"])
+    for s in sims.values():
+        s.close()
+
+
+def _half_period(run_steps, get_R, N):
+    """Steps for the end-to-end vector to turn from +90 to -90 degrees."""
+    prev = math.pi / 2
+    unw = prev
+    t, ts, ths = 0, [0.0], [prev]
+    while unw > -math.pi / 2 - 0.05:
+        run_steps(100)
+        t += 100
+        R = get_R()
+        d = R[N - 1] - R[0]
+        th = math.atan2(d[1], d[0])
+        dd = th - prev
+        dd -= math.pi * round(dd / math.pi)
+        unw += dd
+        prev = th
+        ts.append(t)
+        ths.append(unw)
+        assert t < 200_000
+    i = int(np.argmax(np.array(ths) <= -math.pi / 2))
+    return ts[i - 1] + (-math.pi / 2 - ths[i - 1]) / (ths[i] - ths[i - 1]) * (ts[i] - ts[i - 1])
+
+
+def test_tumbling_period_per_precision(fpd):
+    # stiff fiber (K = 3.3), C = 0.2, Re = 1 (Re_ps = 0.25): the configuration
+    # of the oracle's Jeffery-orbit pin
+    N, a, U, Lx = 6, 2.0, 0.05, 80
+    H = int(round(N * 2 * a / 0.2))
+    cfg = dict(wl.couette_only(Lx, H, u=U), nu_f=-1.0, re=1.0, visc_ratio=50.0, xi=0.5, a=a, n_beads=N,
+               n_fibers=1, stiffness_K=3.3, centres=[[Lx / 2, H / 2]], theta0=[math.pi / 2])
+    o = oracle.Sim(dict(cfg, threads=THREADS))
+    T_ref = _half_period(o.step, lambda: o.beads()[0], N)
+    for p, tol in ((0, 1e-6), (1, 1e-3), (2, 2e-2)):
+        s = fpd.Simulation(dict(cfg, precision=p))
+        T = _half_period(s.step, lambda: s.beads()[0], N)
+        s.close()
+        print(f"tumbling half-period: oracle {T_ref:.2f} steps, {NAMES[p]} {T:.2f} (rel {abs(T / T_ref - 1):.2e})")
+        assert abs(T / T_ref - 1) < tol
