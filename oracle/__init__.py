@@ -62,7 +62,8 @@ class OrcParams(ctypes.Structure):
         ("gy", ctypes.c_double), ("collision", ctypes.c_int32),
         ("s_e", ctypes.c_double), ("s_eps", ctypes.c_double),
         ("s_q", ctypes.c_double), ("init_couette", ctypes.c_int32),
-        ("threads", ctypes.c_int32),
+        ("threads", ctypes.c_int32), ("sandwich_zl", ctypes.c_double),
+        ("sandwich_zr", ctypes.c_double),
     ]
 
 
@@ -121,7 +122,7 @@ DEFAULTS = dict(
     nx=16, ny=16, u_bottom=0.0, u_top=0.0, nu_f=-1.0, re=1.0, visc_ratio=50.0,
     xi=1.0, a=2.0, n_beads=0, n_fibers=0, k_s=-1.0, k_b=0.0, stiffness_K=0.0,
     k_ev=-1.0, phi_cut=8.0, gx=0.0, gy=0.0, collision=0, s_e=1.64, s_eps=1.54,
-    s_q=1.9, init_couette=1, threads=1,
+    s_q=1.9, init_couette=1, threads=1, sandwich_zl=0.0, sandwich_zr=0.0,
 )
 
 

@@ -82,6 +82,8 @@ typedef struct {
     double s_e, s_eps, s_q;/* constant rates for collision == 1               */
     int32_t init_couette;  /* 1: equilibrium at the linear wall profile       */
     int32_t threads;       /* OpenMP threads for the lattice loops (<=0: 1)   */
+    double sandwich_zl;    /* > 0: static solid layers of Eq. 14 below zl ... */
+    double sandwich_zr;    /* ... and above zr (interface width xi)           */
 } orc_params;
 
 typedef struct {
@@ -466,6 +468,16 @@ static void overlay(orc_sim *s) {
         }
     }
     free(ci); free(cj); free(ph);
+    /* Sec. 3.1 sandwich benchmark: static solid layers, Eq. 14, in the
+     * wall-normal coordinate y (the paper's z), added to the bead profiles */
+    if (s->p.sandwich_zl > 0.0) {
+        for (int j = 0; j < ny; ++j) {
+            double y = j + 0.5, ph;
+            if (y <= 0.5 * ny) ph = 0.5 * (tanh((s->p.sandwich_zl - y) / s->p.xi) + 1.0);
+            else ph = 0.5 * (tanh((y - s->p.sandwich_zr) / s->p.xi) + 1.0);
+            for (int i = 0; i < nx; ++i) Phi[(size_t)j * nx + i] += ph;
+        }
+    }
     /* Eq. 1 for the kinematic viscosity (rho_0 = 1) */
     for (size_t c = 0; c < ncell; ++c) s->nu[c] = s->nu_f * (1.0 + (s->p.visc_ratio - 1.0) * Phi[c]);
     free(Phi);

@@ -7,6 +7,7 @@ channel flow, conservation laws, finite differences of the bead-spring energy
 is Eq. 12), and invariants of Eqs. 4-5.  No test here needs a GPU.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -324,3 +325,57 @@ def test_derived_parameters_follow_definitions():
     assert math.isclose(d["gamma_dot"], gd, rel_tol=1e-15)
     assert math.isclose(d["nu_f"], gd * lc * lc / 1.0, rel_tol=1e-15)           # Re = gd lc^2 / nu
     assert math.isclose(2 * d["k_b"] / (d["nu_f"] * gd * lc * lc), 3.3, rel_tol=1e-14)  # Eq. 18
+
+
+# ------------------------------------------------------------ sandwich Couette (Sec. 3.1)
+def _sandwich_profile(H, r_eta, xi_rel, nu=0.2, U=0.01, steps=None):
+    cfg = wl.couette_only(4, H, u=0.0, nu=nu, init_couette=0)
+    cfg.update(u_bottom=0.0, u_top=U, visc_ratio=r_eta, xi=xi_rel * H, sandwich_zl=H / 3,
+               sandwich_zr=2 * H / 3, threads=min(8, os.cpu_count() or 1))
+    s = oracle.Sim(cfg)
+    s.step(steps or int(30 * (H / 3) ** 2 / nu) + 2000)
+    return s.fields()[0][:, 0], cfg
+
+
+def _closed_form(H, r_eta, xi, nu, U):
+    # steady variable-viscosity Couette flow: constant shear stress, so
+    # u(y) = U * int_0^y dy'/nu(y') / int_0^H dy'/nu(y') with nu from Eqs. 1, 14
+    from scipy.integrate import quad
+
+    def phi(y):
+        if y <= H / 2:
+            return 0.5 * (math.tanh((H / 3 - y) / xi) + 1)
+        return 0.5 * (math.tanh((y - 2 * H / 3) / xi) + 1)
+
+    inv = lambda y: 1.0 / (nu * (1 + (r_eta - 1) * phi(y)))
+    pts = [H / 3, 2 * H / 3]
+    total = quad(inv, 0, H, limit=400, points=pts)[0]
+    y = np.arange(H) + 0.5
+    return np.array([U * quad(inv, 0, v, limit=400, points=[p for p in pts if p < v])[0] / total for v in y])
+
+
+def test_sandwich_couette_second_order_to_closed_form():
+    errs = []
+    for H in (30, 60):
+        u, cfg = _sandwich_profile(H, 50.0, 0.02)
+        errs.append(np.abs(u - _closed_form(H, 50.0, cfg["xi"], 0.2, 0.01)).max() / 0.01)
+    assert errs[1] < 3e-3
+    assert 3.0 < errs[0] / errs[1] < 4.8        # O(dx^2) at fixed xi / H
+
+
+def test_sandwich_couette_approaches_eq13_as_interface_thins():
+    # Eq. 13: v = 0 below H/3, linear across the fluid layer, V0 above 2H/3.
+    # At r_eta = 50 the solids keep O(1/r_eta) of the drop; thinner
+    # interfaces (smaller r_xi = xi / H) fit Eq. 13 better (Sec. 3.1).  A
+    # larger r_eta alone does not help at a fixed, coarse resolution: the
+    # tanh tail times r_eta moves the effective interface ~ (xi/2) ln r_eta
+    # into the fluid, which the closed form above accounts for exactly.
+    H = 60
+    y = np.arange(H) + 0.5
+    eq13 = np.clip(0.01 * (y / (H / 3) - 1), 0.0, 0.01)
+    dev = []
+    for r_xi in (0.04, 0.02, 0.01):
+        u, _ = _sandwich_profile(H, 50.0, r_xi)
+        dev.append(np.abs(u - eq13).max() / 0.01)
+    assert dev[2] < 0.05
+    assert dev[0] > dev[1] > dev[2]
