@@ -115,6 +115,22 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def l2_note(state_bytes: int) -> str:
+    mib = state_bytes / 2 ** 20
+    if state_bytes > L2_BYTES:
+        return f"state {mib:.0f} MiB > 129 MiB L2: every step streams from HBM, no flush needed"
+    return f"state {mib:.0f} MiB fits in the 129 MiB L2: L2-resident, not an HBM measurement"
+
+
+def pick_variant(args, cfg):
+    """Sweep launch shape: fixed by --variant, or timed by the autotuner."""
+    if args.variant != "auto":
+        return int(args.variant), None
+    from paper_2212_14153_gb300 import autotune
+    ms = autotune.time_variants(cfg, steps=128, warmup=32)
+    return int(min(range(len(ms)), key=lambda i: ms[i])), [round(m, 5) for m in ms]
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_gpu(args, rank: int, world: int):
     import torch
@@ -133,6 +149,7 @@ def run_gpu(args, rank: int, world: int):
     cfg = workloads.two_fiber_large(seed=3 + rank, precision=args.precision)
     cells = cfg["nx"] * cfg["ny"]
     stream = torch.cuda.Stream()
+    variant, variant_ms = pick_variant(args, cfg)
 
     def barrier():
         if world > 1:
@@ -141,6 +158,7 @@ def run_gpu(args, rank: int, world: int):
     # ---- device-resident throughput (value): consecutive launches overlap
     # (programmatic dependent launch), so no per-kernel events in this region
     sim = fpd.Simulation(cfg, stream=stream.cuda_stream)
+    sim.set_tuning(variant)
     sim.step(args.warmup)
     sim.sync()
     barrier()
@@ -174,6 +192,7 @@ def run_gpu(args, rank: int, world: int):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     sim = fpd.Simulation(cfg, stream=stream.cuda_stream)
+    sim.set_tuning(variant)
     nb = sim.nb
     for _ in range(e2e_steps):
         sim.step(1)
@@ -210,7 +229,7 @@ def run_gpu(args, rank: int, world: int):
                 "workload": cfg["name"], "nx": cfg["nx"], "ny": cfg["ny"], "fibers": cfg["n_fibers"],
                 "beads_per_fiber": cfg["n_beads"], "storage": {0: "f64", 1: "f32", 2: "f16x2^s"}[args.precision],
                 "bytes_per_cell_update": bpc, "per_gpu": "one independent instance",
-                "l2": f"state {bpc // 2 * cells / 2**20:.0f} MiB > 129 MiB L2, no flush",
+                "l2": l2_note(bpc // 2 * cells), "sweep_variant": variant, "variant_ms_per_step": variant_ms,
                 "parallelism": f"replicas x{world}",
             },
             "roofline": {
@@ -302,8 +321,24 @@ def run_sweep(args, rank: int, world: int):
     pool = sum(serve.state_bytes(c, args.precision) + 4096 for c in inst)
     nbeads = sum(c["n_beads"] * c["n_fibers"] for c in inst)
     b = fpd.Batch(args.precision, len(inst), pool, nbeads, stream=stream.cuda_stream)
+    T = 64  # steps per variant for the launch-shape autotuning below
+    nvar = 2
     for c in inst:
-        b.add(c, W + S)
+        b.add(c, nvar * (T + 8) + W + S)
+    variant_ms = []
+    for v in range(nvar):
+        b.set_tuning(v)
+        b.run(8)
+        b.sync()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        b.run(T)
+        a1.record(stream)
+        a1.synchronize()
+        variant_ms.append(a0.elapsed_time(a1) / T)
+    variant = int(min(range(nvar), key=lambda i: variant_ms[i])) if args.variant == "auto" else int(args.variant)
+    b.set_tuning(variant)
     b.run(W)
     b.sync()
     torch.cuda.synchronize()
@@ -325,6 +360,7 @@ def run_sweep(args, rank: int, world: int):
     t_plain = 0.0
     for c in inst:
         sim = fpd.Simulation(c, stream=stream.cuda_stream)
+        sim.set_tuning(variant)
         sim.step(W)
         sim.sync()
         ev0.record(stream)
@@ -341,7 +377,8 @@ def run_sweep(args, rank: int, world: int):
         "higher_is_better": True, "dtype": {0: "f64", 1: "f32", 2: "f32"}[args.precision], "data": "synthetic",
         "config": {"workload": "batched_sweep", "instances": len(inst), "cells": sum(cells), "beads": nbeads,
                    "H": [min(c["ny"] for c in inst), max(c["ny"] for c in inst)],
-                   "accuracy": "each instance bit-identical to its alone run"},
+                   "accuracy": "each instance bit-identical to its alone run",
+                   "sweep_variant": variant, "variant_ms_per_step": [round(m, 4) for m in variant_ms]},
         "batched_s": t_batch, "plain_s": t_plain,
     }
     print(json.dumps(line), flush=True)
@@ -404,6 +441,7 @@ def main():
     ap.add_argument("--cap-bytes", type=int, default=150 << 30)
     ap.add_argument("--max-slots", type=int, default=512)
     ap.add_argument("--chunk", type=int, default=500)
+    ap.add_argument("--variant", default="auto", choices=["auto", "0", "1"])
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

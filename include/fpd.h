@@ -92,6 +92,11 @@ typedef struct {
     const double *centre_xy;/* n_fibers x 2: fiber centres (ignored if bead_xy) */
     const double *theta0;   /* n_fibers: fiber angles in radians               */
     const double *bead_xy;  /* optional (n_fibers*n_beads) x 2 explicit R_i^0  */
+    double sandwich_zl;     /* > 0: static solid layers of the Couette benchmark
+                               (Sec. 3.1, Eq. 14): phi(y) = (tanh((zl - y)/xi)
+                               + 1)/2 for y <= H/2, (tanh((y - zr)/xi) + 1)/2
+                               above, added to the bead profiles in Eq. 1   */
+    double sandwich_zr;
 } fpd_params;
 
 typedef struct fpd_sim fpd_sim;
@@ -168,6 +173,15 @@ int fpd_diag(fpd_sim *s, double out[4]);
  * and must not overlap.  Returns FPD_ENAN like fpd_diag.  Synchronises. */
 int fpd_diag_noalloc(fpd_sim *s, double out[4]);
 
+/* Kernel tuning (no effect on results): variant 0 runs the lattice sweep
+ * with one cell per thread (32 x 8 threads per 32 x 8 tile), variant 1 with
+ * two cells per thread along y (32 x 4 threads).  Chosen per workload by an
+ * autotuner that times both; both give bit-identical results.
+ * fpd_set_tuning synchronises and drops captured step graphs; FPD_EINVAL
+ * for an unknown variant.  fpd_get_tuning: current variant and count. */
+int fpd_set_tuning(fpd_sim *s, int32_t variant);
+int fpd_get_tuning(const fpd_sim *s, int32_t *variant, int32_t *n_variants);
+
 /* Derived parameters: out[0] nu_f, [1] k_s, [2] k_b, [3] k_ev, [4] l_0,
  * [5] support radius a + phi_cut xi, [6] gamma_dot, [7] stored bytes per
  * cell update (2 x 9 x storage size). */
@@ -212,6 +226,9 @@ int fpd_batch_add(fpd_batch *b, const fpd_params *p, int64_t n_steps, int32_t *s
  * the count).  Instances that reach their count become finished.  Enqueues
  * the work asynchronously (the call may synchronise after admissions). */
 int fpd_batch_run(fpd_batch *b, int64_t max_steps, int64_t *steps_done);
+
+/* Lattice sweep variant of the batch (as fpd_set_tuning). */
+int fpd_batch_set_tuning(fpd_batch *b, int32_t variant);
 
 /* Block until the batch's work has finished. */
 int fpd_batch_sync(fpd_batch *b);

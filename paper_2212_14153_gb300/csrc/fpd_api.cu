@@ -168,6 +168,17 @@ int derive(fpd_sim *s, const fpd_params &p) {
     I.f_inv_xi = (float)I.inv_xi;
     I.f_rcut = (float)I.rcut;
     I.f_rcut2 = (float)I.rcut2;
+    if (p.sandwich_zl > 0.0) {
+        if (!(p.xi > 0.0)) return fail(nullptr, FPD_EINVAL, "sandwich layers need xi > 0");
+        if (!(p.sandwich_zr > p.sandwich_zl)) return fail(nullptr, FPD_EINVAL, "sandwich_zr must exceed sandwich_zl");
+        I.sandwich = 1;
+        I.sw_zl = p.sandwich_zl;
+        I.sw_zr = p.sandwich_zr;
+        I.half_h = 0.5 * p.ny;
+        I.f_sw_zl = (float)p.sandwich_zl;
+        I.f_sw_zr = (float)p.sandwich_zr;
+        I.f_half_h = (float)I.half_h;
+    }
     I.ks_l02 = s->k_s / (l0 * l0);
     I.f_ks_l02 = (float)I.ks_l02;
     I.f_kb = (float)s->k_b;
@@ -284,7 +295,7 @@ int enqueue_step(fpd_sim *s, cudaStream_t st, int64_t t, bool profiled) {
     }
     const int after_beads = (I.nb > 0 && t >= 1 && !profiled) ? 1 : 0;
     e = fpd::launch_lattice(s->precision, s->inst_d, I, s->pool, s->tab[parity], s->masks[parity],
-                            s->masks[parity ^ 1], parity, after_beads, st);
+                            s->masks[parity ^ 1], parity, after_beads, s->variant, st);
     if (e != cudaSuccess) return cuda_fail(s, e, "lattice kernel launch");
     if (profiled) {
         cudaEventRecord(b, st);
@@ -482,6 +493,30 @@ int fpd_step(fpd_sim *s, int64_t n_steps) {
         s->nstep++;
         --n_steps;
     }
+    return FPD_OK;
+}
+
+int fpd_set_tuning(fpd_sim *s, int32_t variant) {
+    if (!s) return fail(nullptr, FPD_EINVAL, "fpd_set_tuning: NULL handle");
+    if (variant < 0 || variant >= fpd::kLatticeVariants)
+        return fail(s, FPD_EINVAL, "tuning variant must be in [0, %d)", fpd::kLatticeVariants);
+    if (variant != s->variant) {
+        cudaError_t e = cudaStreamSynchronize(s->stream);
+        if (e != cudaSuccess) return cuda_fail(s, e, "fpd_set_tuning");
+        for (int p = 0; p < 2; ++p)
+            if (s->graph[p]) {
+                cudaGraphExecDestroy(s->graph[p]);
+                s->graph[p] = nullptr;
+            }
+        s->variant = variant;
+    }
+    return FPD_OK;
+}
+
+int fpd_get_tuning(const fpd_sim *s, int32_t *variant, int32_t *n_variants) {
+    if (!s) return FPD_EINVAL;
+    if (variant) *variant = s->variant;
+    if (n_variants) *n_variants = fpd::kLatticeVariants;
     return FPD_OK;
 }
 

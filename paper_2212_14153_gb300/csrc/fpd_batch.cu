@@ -110,6 +110,7 @@ struct fpd_batch {
     int64_t gstep = 0;
     double cell_updates = 0.0;
     bool dirty = true;
+    int variant = 0;  // lattice sweep variant
     double *scratch = nullptr;
     size_t scratch_bytes = 0;
     std::string err;
@@ -162,10 +163,19 @@ int rebuild(fpd_batch *b) {
     cudaError_t e;
     std::vector<int2> tiles;
     const int gp = (int)(b->gstep & 1);
+    // words per tile mask: enough for the largest resident instance
+    int W = 1;
+    for (auto &sl : b->slots)
+        if (sl.state == kActive) W = std::max(W, (sl.inst.nb + 31) / 32);
+    if (W != b->mask_words) {
+        b->mask_words = W;
+        b->tiles_cap = 0;  // reallocate the masks below
+    }
     for (int s = 0; s < b->max_slots; ++s) {
         Slot &sl = b->slots[s];
         if (sl.state != kActive) continue;
         fpd::Inst &I = sl.inst;
+        I.mask_words = W;
         I.tile_base = (int)tiles.size();
         for (int by = 0; by < I.nty; ++by)
             for (int bx = 0; bx < I.ntx; ++bx) tiles.push_back(make_int2(s, (by << 16) | bx));
@@ -173,12 +183,12 @@ int rebuild(fpd_batch *b) {
         b->insts_h[s] = I;
     }
     b->ntiles = (int)tiles.size();
-    if (b->ntiles > b->tiles_cap) {
+    if (b->ntiles > b->tiles_cap || !b->masks) {
         cudaFree(b->tiles_d);
         cudaFree(b->masks);
         b->tiles_d = nullptr;
         b->masks = nullptr;
-        const int cap = std::max(b->ntiles, 2 * b->tiles_cap);
+        const int cap = std::max(std::max(b->ntiles, 1), 2 * b->tiles_cap);
         if ((e = cudaMalloc(&b->tiles_d, cap * sizeof(int2))) != cudaSuccess) return bcuda(b, e, "cudaMalloc tiles");
         if ((e = cudaMalloc(&b->masks, 2 * (size_t)cap * b->mask_words * sizeof(unsigned))) != cudaSuccess)
             return bcuda(b, e, "cudaMalloc masks");
@@ -246,7 +256,7 @@ int fpd_batch_create(int32_t precision, int32_t max_slots, int64_t pool_bytes, i
     b->elem = precision == 0 ? 8 : (precision == 1 ? 4 : 2);
     b->max_slots = max_slots;
     b->max_beads = max_beads;
-    b->mask_words = (fpd::kMaxBeads + 31) / 32;
+    b->mask_words = 1;
     b->stream = (cudaStream_t)stream;
     b->slots.assign(max_slots, Slot());
     b->insts_h.assign(max_slots, fpd::Inst{});
@@ -295,7 +305,6 @@ int fpd_batch_add(fpd_batch *b, const fpd_params *p, int64_t n_steps, int32_t *s
     int rc = fpd::derive_params(&tmp, *p);
     if (rc != FPD_OK) return bfail(b, rc, "%s", fpd::create_error());
     fpd::Inst I = tmp.inst;
-    I.mask_words = b->mask_words;
     int s = -1;
     for (int i = 0; i < b->max_slots; ++i)
         if (b->slots[i].state == kFree) {
@@ -391,7 +400,7 @@ int fpd_batch_run(fpd_batch *b, int64_t max_steps, int64_t *steps_done) {
             if (e != cudaSuccess) return bcuda(b, e, "batched bead phase");
         }
         e = fpd::launch_lattice_batch(b->precision, b->insts_d, b->tiles_d, b->ntiles, b->pool, b->tab[0], b->tab[1],
-                                      mw, mc, gp, nbl > 0 ? 1 : 0, b->stream);
+                                      mw, mc, gp, nbl > 0 ? 1 : 0, b->variant, b->stream);
         if (e != cudaSuccess) return bcuda(b, e, "batched lattice sweep");
         b->gstep++;
         if (any_first) {
@@ -410,6 +419,14 @@ int fpd_batch_run(fpd_batch *b, int64_t max_steps, int64_t *steps_done) {
             }
         }
     if (steps_done) *steps_done = chunk;
+    return FPD_OK;
+}
+
+int fpd_batch_set_tuning(fpd_batch *b, int32_t variant) {
+    if (!b) return FPD_EINVAL;
+    if (variant < 0 || variant >= fpd::kLatticeVariants)
+        return bfail(b, FPD_EINVAL, "tuning variant must be in [0, %d)", fpd::kLatticeVariants);
+    b->variant = variant;
     return FPD_OK;
 }
 

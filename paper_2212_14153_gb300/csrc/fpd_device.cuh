@@ -51,7 +51,20 @@ struct Inst {
     // bead-force constants: k_s / l0^2, k_b, k_ev, l0, 1 / nx
     double ks_l02;
     float f_ks_l02, f_kb, f_kev, f_l0, f_inv_nx;
+    // static solid layers of the sandwich Couette benchmark (Eq. 14)
+    int32_t sandwich, pad2_;
+    double sw_zl, sw_zr, half_h;
+    float f_sw_zl, f_sw_zr, f_half_h;
 };
+
+// phi(y) of the sandwich layers (Eq. 14) at height y
+__device__ __forceinline__ double sandwich_phi_f64(const Inst &I, double y) {
+    return y <= I.half_h ? 0.5 * (tanh((I.sw_zl - y) / I.xi) + 1.0) : 0.5 * (tanh((y - I.sw_zr) / I.xi) + 1.0);
+}
+__device__ __forceinline__ float sandwich_phi_f32(const Inst &I, float y) {
+    return y <= I.f_half_h ? 0.5f * (tanhf((I.f_sw_zl - y) * I.f_inv_xi) + 1.0f)
+                           : 0.5f * (tanhf((y - I.f_sw_zr) * I.f_inv_xi) + 1.0f);
+}
 
 template <class R> __device__ __forceinline__ R bb_term(const Inst &I, int wall, int k);
 template <> __device__ __forceinline__ double bb_term<double>(const Inst &I, int wall, int k) {

@@ -20,9 +20,12 @@ constexpr int kGraphSteps = 32;  // time steps per captured graph chunk
 // after_beads = 1 when the previous launch on the stream is the bead phase
 // of the same step: the sweep is then launched as a programmatic dependent
 // of it and loads its populations before waiting for it.
+// variant: 0 = one cell per thread (32 x 8 threads), 1 = two cells per
+// thread along y (32 x 4 threads); same tiles, same results.
+constexpr int kLatticeVariants = 2;
 cudaError_t launch_lattice(int precision, const Inst *inst_d, const Inst &inst_h, void *pool, BeadTab tab,
                            const unsigned *mask_read, unsigned *mask_clear, int parity, int after_beads,
-                           cudaStream_t st);
+                           int variant, cudaStream_t st);
 
 // Bead phase (items (3) then (1)): one CTA per bead of any instance
 // (blist[i] = (instance slot, global bead index); NULL = instance 0, bead i;
@@ -42,7 +45,7 @@ cudaError_t launch_beads(int precision, const Inst *inst_d, const int2 *blist, i
 // (slot, by << 16 | bx)); each instance at its own parity.
 cudaError_t launch_lattice_batch(int precision, const Inst *insts, const int2 *tiles, int ntiles, void *pool,
                                  BeadTab tab0, BeadTab tab1, const unsigned *mask_read, unsigned *mask_clear,
-                                 int gparity, int after_beads, cudaStream_t st);
+                                 int gparity, int after_beads, int variant, cudaStream_t st);
 
 cudaError_t launch_init(int precision, const Inst *inst_d, const Inst &inst_h, void *pool, int couette,
                         cudaStream_t st);

@@ -26,112 +26,141 @@ template <> struct Real<double> { using type = double; };
 
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 
-// One cell of the sweep: tile (bx, by) of instance I, at the instance's
-// step parity; the CTA's thread (threadIdx.x, threadIdx.y) owns one cell.
-template <class S>
-__device__ __forceinline__ void lattice_cell(const Inst &I, S *__restrict__ pool, const BeadTab &tab,
-                                             const unsigned *__restrict__ mask_read, unsigned *__restrict__ mask_clear,
-                                             const int bx, const int by, const int parity, const int early_load) {
-    using R = typename Real<S>::type;
-    constexpr bool kF64 = std::is_same<R, double>::value;
-    const int x = bx * kTileX + threadIdx.x, y = by * kTileY + threadIdx.y;
-    const int tile = I.tile_base + by * I.ntx + bx;
-    const int W = I.mask_words;
-    const bool valid = x < I.nx && y < I.ny;
-    S *A = pool + I.pop_off;
-    const Cell C = make_cell(I, x, valid ? y : 0);
-    R g[9];
-    // populations come from the previous sweep; when the bead phase runs
-    // between the two sweeps they may be loaded before waiting on it
-    if (early_load && valid) load_pops<S, R>(A, I, C, parity, g);
-    pdl_wait();
-    pdl_trigger();
-    if (threadIdx.x == 0 && threadIdx.y == 0)  // the other parity's mask, for the next bead phase
-        for (int w = 0; w < W; ++w) mask_clear[tile * W + w] = 0u;
-    if (!valid) return;
-    if (!early_load) load_pops<S, R>(A, I, C, parity, g);
-    const unsigned *m = mask_read + tile * W;
-    unsigned any = 0u;
-    for (int w = 0; w < W; ++w) any |= m[w];
-    R s_nu, s_e, s_eps, s_q, Fx, Fy;
-    if constexpr (kF64) {
+// Relaxation rates and force density of one cell (Eqs. 1, 2, 4) from the
+// beads marked in its tile's mask (m, W words; any = OR of the words).
+template <class R>
+__device__ __forceinline__ void cell_overlay(const Inst &I, const BeadTab &tab, const unsigned *__restrict__ m,
+                                             const int W, const unsigned any, const int x, const int y, R &Fx,
+                                             R &Fy, R &s_nu, R &s_e, R &s_eps, R &s_q) {
+    if constexpr (std::is_same<R, double>::value) {
         Fx = I.gx;
         Fy = I.gy;
-        if (any == 0u) {
+        if (any == 0u && !I.sandwich) {
             s_nu = I.fluid_rates_d[0];
             s_e = I.fluid_rates_d[1];
             s_eps = I.fluid_rates_d[2];
             s_q = I.fluid_rates_d[3];
-        } else {
-            double Phi = 0.0;
-            const double xc = x + 0.5, yc = y + 0.5;
-            for (int w = 0; w < W; ++w) {
-                unsigned bits = m[w];
-                while (bits) {
-                    const int q = I.bead_off + 32 * w + __ffs(bits) - 1;
-                    bits &= bits - 1u;
-                    const double ph = phi_f64(I, xc, yc, tab.Rx[q], tab.Ry[q]);
-                    if (ph != 0.0) {
-                        Phi += ph;
-                        Fx += ph * tab.Gx[q];
-                        Fy += ph * tab.Gy[q];
-                    }
+            return;
+        }
+        const double xc = x + 0.5, yc = y + 0.5;
+        double Phi = I.sandwich ? sandwich_phi_f64(I, yc) : 0.0;
+        for (int w = 0; w < W; ++w) {
+            unsigned bits = m[w];
+            while (bits) {
+                const int q = I.bead_off + 32 * w + __ffs(bits) - 1;
+                bits &= bits - 1u;
+                const double ph = phi_f64(I, xc, yc, tab.Rx[q], tab.Ry[q]);
+                if (ph != 0.0) {
+                    Phi += ph;
+                    Fx += ph * tab.Gx[q];
+                    Fy += ph * tab.Gy[q];
                 }
             }
-            const double nu = I.nu_f * (1.0 + (I.visc_ratio - 1.0) * Phi);
-            rates<double>(I.collision, nu, I.s_e, I.s_eps, I.s_q, s_nu, s_e, s_eps, s_q);
         }
+        const double nu = I.nu_f * (1.0 + (I.visc_ratio - 1.0) * Phi);
+        rates<double>(I.collision, nu, I.s_e, I.s_eps, I.s_q, s_nu, s_e, s_eps, s_q);
     } else {
         Fx = I.f_gx;
         Fy = I.f_gy;
-        if (any == 0u) {
+        if (any == 0u && !I.sandwich) {
             s_nu = I.fluid_rates_f[0];
             s_e = I.fluid_rates_f[1];
             s_eps = I.fluid_rates_f[2];
             s_q = I.fluid_rates_f[3];
-        } else {
-            float Phi = 0.f;
-            const float hnx = 0.5f * I.nx, fnx = (float)I.nx;
-            const float xc = (float)x + 0.5f, yc = (float)y + 0.5f;
-            for (int w = 0; w < W; ++w) {
-                unsigned bits = m[w];
-                while (bits) {
-                    const int q = I.bead_off + 32 * w + __ffs(bits) - 1;
-                    bits &= bits - 1u;
-                    // (x_c - R_x) with R_x = hi + lo; the periodic shift is
-                    // applied to the cell centre first so that xc - hi is exact
-                    const float bx = tab.xh[q];
-                    float xcl = xc;
-                    const float d0 = xcl - bx;
-                    xcl = (d0 > hnx) ? xcl - fnx : ((d0 < -hnx) ? xcl + fnx : xcl);
-                    const float dx = (xcl - bx) - tab.xl[q];
-                    const float dy = (yc - tab.yh[q]) - tab.yl[q];
-                    const float ph = phi_f32(dx, dy, I.f_a, I.f_inv_xi, I.f_rcut2);
-                    Phi += ph;
-                    Fx += ph * tab.gxf[q];
-                    Fy += ph * tab.gyf[q];
-                }
-            }
-            const float nu = I.f_nu_f * (1.0f + I.f_visc_m1 * Phi);
-            rates<float>(I.collision, nu, I.f_s_e, I.f_s_eps, I.f_s_q, s_nu, s_e, s_eps, s_q);
+            return;
         }
+        const float hnx = 0.5f * I.nx, fnx = (float)I.nx;
+        const float xc = (float)x + 0.5f, yc = (float)y + 0.5f;
+        float Phi = I.sandwich ? sandwich_phi_f32(I, yc) : 0.f;
+        for (int w = 0; w < W; ++w) {
+            unsigned bits = m[w];
+            while (bits) {
+                const int q = I.bead_off + 32 * w + __ffs(bits) - 1;
+                bits &= bits - 1u;
+                // (x_c - R_x) with R_x = hi + lo; the periodic shift is
+                // applied to the cell centre first so that xc - hi is exact
+                const float bx = tab.xh[q];
+                float xcl = xc;
+                const float d0 = xcl - bx;
+                xcl = (d0 > hnx) ? xcl - fnx : ((d0 < -hnx) ? xcl + fnx : xcl);
+                const float dx = (xcl - bx) - tab.xl[q];
+                const float dy = (yc - tab.yh[q]) - tab.yl[q];
+                const float ph = phi_f32(dx, dy, I.f_a, I.f_inv_xi, I.f_rcut2);
+                Phi += ph;
+                Fx += ph * tab.gxf[q];
+                Fy += ph * tab.gyf[q];
+            }
+        }
+        const float nu = I.f_nu_f * (1.0f + I.f_visc_m1 * Phi);
+        rates<float>(I.collision, nu, I.f_s_e, I.f_s_eps, I.f_s_q, s_nu, s_e, s_eps, s_q);
     }
-    collide<R>(g, Fx, Fy, s_nu, s_e, s_eps, s_q);
-    store_pops<S, R>(A, I, C, parity, g);
 }
 
-template <class S>
-__global__ void __launch_bounds__(kTileX *kTileY)
+// One tile of the sweep: tile (bx, by) of instance I at the instance's step
+// parity.  The CTA has kTileX x (kTileY / CY) threads; thread (tx, ty) owns
+// the CY cells (x, y0 + ty + k kTileY / CY), k < CY, of its column.
+template <class S, int CY>
+__device__ __forceinline__ void lattice_tile(const Inst &I, S *__restrict__ pool, const BeadTab &tab,
+                                             const unsigned *__restrict__ mask_read, unsigned *__restrict__ mask_clear,
+                                             const int bx, const int by, const int parity, const int early_load) {
+    using R = typename Real<S>::type;
+    constexpr int RY = kTileY / CY;
+    const int x = bx * kTileX + threadIdx.x;
+    const int tile = I.tile_base + by * I.ntx + bx;
+    const int W = I.mask_words;
+    S *A = pool + I.pop_off;
+    int y[CY];
+    bool valid[CY];
+    Cell C[CY];
+    R g[CY][9];
+#pragma unroll
+    for (int k = 0; k < CY; ++k) {
+        y[k] = by * kTileY + threadIdx.y + k * RY;
+        valid[k] = x < I.nx && y[k] < I.ny;
+        C[k] = make_cell(I, x, valid[k] ? y[k] : 0);
+    }
+    // populations come from the previous sweep; when the bead phase runs
+    // between the two sweeps they may be loaded before waiting on it
+    if (early_load) {
+#pragma unroll
+        for (int k = 0; k < CY; ++k)
+            if (valid[k]) load_pops<S, R>(A, I, C[k], parity, g[k]);
+    }
+    pdl_wait();
+    pdl_trigger();
+    if (threadIdx.x == 0 && threadIdx.y == 0)  // the other parity's mask, for the next bead phase
+        for (int w = 0; w < W; ++w) mask_clear[tile * W + w] = 0u;
+    if (!valid[0]) return;  // cells further down the column are invalid too
+    if (!early_load) {
+#pragma unroll
+        for (int k = 0; k < CY; ++k)
+            if (valid[k]) load_pops<S, R>(A, I, C[k], parity, g[k]);
+    }
+    const unsigned *m = mask_read + tile * W;
+    unsigned any = 0u;
+    for (int w = 0; w < W; ++w) any |= m[w];
+#pragma unroll
+    for (int k = 0; k < CY; ++k) {
+        if (!valid[k]) continue;
+        R Fx, Fy, s_nu, s_e, s_eps, s_q;
+        cell_overlay<R>(I, tab, m, W, any, x, y[k], Fx, Fy, s_nu, s_e, s_eps, s_q);
+        collide<R>(g[k], Fx, Fy, s_nu, s_e, s_eps, s_q);
+        store_pops<S, R>(A, I, C[k], parity, g[k]);
+    }
+}
+
+template <class S, int CY>
+__global__ void __launch_bounds__(kTileX *kTileY / CY)
     k_lattice(const Inst I, S *__restrict__ pool, const BeadTab tab, const unsigned *__restrict__ mask_read,
               unsigned *__restrict__ mask_clear, const int parity, const int early_load) {
-    lattice_cell<S>(I, pool, tab, mask_read, mask_clear, blockIdx.x, blockIdx.y, parity, early_load);
+    lattice_tile<S, CY>(I, pool, tab, mask_read, mask_clear, blockIdx.x, blockIdx.y, parity, early_load);
 }
 
 // Batched sweep over a packed tile list: tiles[t] = (instance slot,
 // by << 16 | bx).  Each instance reads table and layout of its own parity
 // (global parity ^ par_xor); the record is copied to shared memory per CTA.
-template <class S>
-__global__ void __launch_bounds__(kTileX *kTileY)
+template <class S, int CY>
+__global__ void __launch_bounds__(kTileX *kTileY / CY)
     k_lattice_batch(const Inst *__restrict__ insts, const int2 *__restrict__ tiles, S *__restrict__ pool,
                     const BeadTab tab0, const BeadTab tab1, const unsigned *__restrict__ mask_read,
                     unsigned *__restrict__ mask_clear, const int gparity, const int early_load) {
@@ -141,12 +170,12 @@ __global__ void __launch_bounds__(kTileX *kTileY)
         const unsigned *src = (const unsigned *)(insts + t.x);
         unsigned *dst = (unsigned *)&sI;
         const int tid = threadIdx.y * kTileX + threadIdx.x;
-        for (int wd = tid; wd < (int)(sizeof(Inst) / 4); wd += kTileX * kTileY) dst[wd] = src[wd];
+        for (int wd = tid; wd < (int)(sizeof(Inst) / 4); wd += kTileX * kTileY / CY) dst[wd] = src[wd];
     }
     __syncthreads();
     const int parity = gparity ^ sI.par_xor;
-    lattice_cell<S>(sI, pool, parity ? tab1 : tab0, mask_read, mask_clear, t.y & 0xffff, t.y >> 16, parity,
-                    early_load);
+    lattice_tile<S, CY>(sI, pool, parity ? tab1 : tab0, mask_read, mask_clear, t.y & 0xffff, t.y >> 16, parity,
+                        early_load);
 }
 
 // Equilibrium start: f_k = f_k^eq(rho = 1, u = (u_wall(y), 0)) with the
@@ -305,57 +334,76 @@ __global__ void __launch_bounds__(kDiagThreads)
 }  // namespace
 
 // ---------------------------------------------------------------- launchers
-template <class S>
+template <class S, int CY>
 static cudaError_t lattice_t(const Inst &I, void *pool, BeadTab tab, const unsigned *mask_read,
                              unsigned *mask_clear, int parity, int after_beads, cudaStream_t st) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(I.ntx, I.nty);
-    cfg.blockDim = dim3(kTileX, kTileY);
+    cfg.blockDim = dim3(kTileX, kTileY / CY);
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = after_beads ? 1 : 0;
-    return cudaLaunchKernelEx(&cfg, k_lattice<S>, I, (S *)pool, tab, mask_read, mask_clear, parity, after_beads);
+    return cudaLaunchKernelEx(&cfg, k_lattice<S, CY>, I, (S *)pool, tab, mask_read, mask_clear, parity,
+                              after_beads);
+}
+
+template <class S>
+static cudaError_t lattice_v(int variant, const Inst &I, void *pool, BeadTab tab, const unsigned *mask_read,
+                             unsigned *mask_clear, int parity, int after_beads, cudaStream_t st) {
+    if (variant == 1) return lattice_t<S, 2>(I, pool, tab, mask_read, mask_clear, parity, after_beads, st);
+    return lattice_t<S, 1>(I, pool, tab, mask_read, mask_clear, parity, after_beads, st);
 }
 
 cudaError_t launch_lattice(int precision, const Inst *, const Inst &inst_h, void *pool, BeadTab tab,
                            const unsigned *mask_read, unsigned *mask_clear, int parity, int after_beads,
-                           cudaStream_t st) {
+                           int variant, cudaStream_t st) {
     switch (precision) {
-        case 0: return lattice_t<double>(inst_h, pool, tab, mask_read, mask_clear, parity, after_beads, st);
-        case 1: return lattice_t<float>(inst_h, pool, tab, mask_read, mask_clear, parity, after_beads, st);
-        case 2: return lattice_t<__half>(inst_h, pool, tab, mask_read, mask_clear, parity, after_beads, st);
+        case 0: return lattice_v<double>(variant, inst_h, pool, tab, mask_read, mask_clear, parity, after_beads, st);
+        case 1: return lattice_v<float>(variant, inst_h, pool, tab, mask_read, mask_clear, parity, after_beads, st);
+        case 2: return lattice_v<__half>(variant, inst_h, pool, tab, mask_read, mask_clear, parity, after_beads, st);
     }
     return cudaErrorInvalidValue;
 }
 
-template <class S>
+template <class S, int CY>
 static cudaError_t lattice_batch_t(const Inst *insts, const int2 *tiles, int ntiles, void *pool, BeadTab tab0,
                                    BeadTab tab1, const unsigned *mask_read, unsigned *mask_clear, int gparity,
                                    int after_beads, cudaStream_t st) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(ntiles);
-    cfg.blockDim = dim3(kTileX, kTileY);
+    cfg.blockDim = dim3(kTileX, kTileY / CY);
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = after_beads ? 1 : 0;
-    return cudaLaunchKernelEx(&cfg, k_lattice_batch<S>, insts, tiles, (S *)pool, tab0, tab1, mask_read, mask_clear,
-                              gparity, after_beads);
+    return cudaLaunchKernelEx(&cfg, k_lattice_batch<S, CY>, insts, tiles, (S *)pool, tab0, tab1, mask_read,
+                              mask_clear, gparity, after_beads);
+}
+
+template <class S>
+static cudaError_t lattice_batch_v(int variant, const Inst *insts, const int2 *tiles, int ntiles, void *pool,
+                                   BeadTab tab0, BeadTab tab1, const unsigned *mask_read, unsigned *mask_clear,
+                                   int gparity, int after_beads, cudaStream_t st) {
+    if (variant == 1)
+        return lattice_batch_t<S, 2>(insts, tiles, ntiles, pool, tab0, tab1, mask_read, mask_clear, gparity,
+                                     after_beads, st);
+    return lattice_batch_t<S, 1>(insts, tiles, ntiles, pool, tab0, tab1, mask_read, mask_clear, gparity,
+                                 after_beads, st);
 }
 
 cudaError_t launch_lattice_batch(int precision, const Inst *insts, const int2 *tiles, int ntiles, void *pool,
                                  BeadTab tab0, BeadTab tab1, const unsigned *mask_read, unsigned *mask_clear,
-                                 int gparity, int after_beads, cudaStream_t st) {
+                                 int gparity, int after_beads, int variant, cudaStream_t st) {
     if (ntiles <= 0) return cudaSuccess;
     switch (precision) {
-        case 0: return lattice_batch_t<double>(insts, tiles, ntiles, pool, tab0, tab1, mask_read, mask_clear, gparity, after_beads, st);
-        case 1: return lattice_batch_t<float>(insts, tiles, ntiles, pool, tab0, tab1, mask_read, mask_clear, gparity, after_beads, st);
-        case 2: return lattice_batch_t<__half>(insts, tiles, ntiles, pool, tab0, tab1, mask_read, mask_clear, gparity, after_beads, st);
+        case 0: return lattice_batch_v<double>(variant, insts, tiles, ntiles, pool, tab0, tab1, mask_read, mask_clear, gparity, after_beads, st);
+        case 1: return lattice_batch_v<float>(variant, insts, tiles, ntiles, pool, tab0, tab1, mask_read, mask_clear, gparity, after_beads, st);
+        case 2: return lattice_batch_v<__half>(variant, insts, tiles, ntiles, pool, tab0, tab1, mask_read, mask_clear, gparity, after_beads, st);
     }
     return cudaErrorInvalidValue;
 }

@@ -37,6 +37,7 @@ struct fpd_sim {
     double launches[2] = {0, 0};
     // captured step chunks, one per starting parity (see fpd_step)
     bool use_graphs = true;
+    int variant = 0;  // lattice sweep variant (see launch_lattice)
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
 };

@@ -39,6 +39,7 @@ class fpd_params(ctypes.Structure):
         ("init_couette", ctypes.c_int32),
         ("s_e", ctypes.c_double), ("s_eps", ctypes.c_double), ("s_q", ctypes.c_double),
         ("centre_xy", _DP), ("theta0", _DP), ("bead_xy", _DP),
+        ("sandwich_zl", ctypes.c_double), ("sandwich_zr", ctypes.c_double),
     ]
 
 
@@ -65,6 +66,10 @@ SIGNATURES = {
     "fpd_diag": (ctypes.c_int, [ctypes.c_void_p, _DP]),
     "fpd_diag_noalloc": (ctypes.c_int, [ctypes.c_void_p, _DP]),
     "fpd_derived": (ctypes.c_int, [ctypes.c_void_p, _DP]),
+    "fpd_set_tuning": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "fpd_get_tuning": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32),
+                                      ctypes.POINTER(ctypes.c_int32)]),
+    "fpd_batch_set_tuning": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "fpd_set_profiling": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "fpd_kernel_times": (ctypes.c_int, [ctypes.c_void_p, _DP]),
     "fpd_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
@@ -168,6 +173,20 @@ def fpd_diag_noalloc(h, out) -> None:
     _check(load_library().fpd_diag_noalloc(h, _ptr(out)), h)
 
 
+def fpd_set_tuning(h, variant: int) -> None:
+    _check(load_library().fpd_set_tuning(h, int(variant)), h)
+
+
+def fpd_get_tuning(h) -> tuple[int, int]:
+    v, n = ctypes.c_int32(0), ctypes.c_int32(0)
+    _check(load_library().fpd_get_tuning(h, ctypes.byref(v), ctypes.byref(n)), h)
+    return v.value, n.value
+
+
+def fpd_batch_set_tuning(b, variant: int) -> None:
+    _bcheck(load_library().fpd_batch_set_tuning(b, int(variant)), b)
+
+
 def fpd_derived(h, out) -> None:
     _check(load_library().fpd_derived(h, _ptr(out)), h)
 
@@ -200,7 +219,8 @@ def params_from_config(cfg: dict) -> tuple[fpd_params, list]:
                   n_fibers="n_fibers", k_s="k_s", k_b="k_b", stiffness_K="stiffness_K",
                   k_ev="k_ev", phi_cut="phi_cut", gx="body_force_x", gy="body_force_y",
                   precision="precision", collision="collision", init_couette="init_couette",
-                  s_e="s_e", s_eps="s_eps", s_q="s_q")
+                  s_e="s_e", s_eps="s_eps", s_q="s_q", sandwich_zl="sandwich_zl",
+                  sandwich_zr="sandwich_zr")
     for k, field in simple.items():
         if k in cfg:
             setattr(p, field, cfg[k])
@@ -282,6 +302,12 @@ class Simulation:
         fpd_derived(self.h, out)
         keys = ["nu_f", "k_s", "k_b", "k_ev", "l0", "rcut", "gamma_dot", "bytes_per_cell"]
         return dict(zip(keys, out.tolist()))
+
+    def set_tuning(self, variant: int):
+        fpd_set_tuning(self.h, variant)
+
+    def tuning(self) -> tuple[int, int]:
+        return fpd_get_tuning(self.h)
 
     def set_profiling(self, on: bool):
         fpd_set_profiling(self.h, on)
@@ -434,3 +460,6 @@ class Batch:
 
     def stats(self) -> dict:
         return fpd_batch_stats(self.h)
+
+    def set_tuning(self, variant: int):
+        fpd_batch_set_tuning(self.h, variant)

@@ -292,3 +292,36 @@ def test_graph_chunks_equal_direct_steps(precision):
     for _ in range(64):
         b.step(1)
     assert np.array_equal(a.populations(), b.populations())
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-13), (1, 1e-5), (2, 1e-2)])
+def test_sweep_variants_agree(precision, tol):
+    # the autotuner's launch shapes (1 or 2 cells per thread) compute the
+    # same arithmetic; the compiler may contract multiply-adds differently
+    # in the two instantiations, so they agree to rounding, not bit for bit
+    rng = np.random.default_rng(78)
+    cfg = wl.random_fiber(rng, 75, 45, n_beads=6, a=2.0, xi=1.0, n_fibers=2, precision=precision)
+    a = gpu_sim(cfg)
+    b = gpu_sim(cfg)
+    b.set_tuning(1)
+    assert b.tuning() == (1, 2)
+    a.step(77)
+    b.step(77)
+    w = oracle.feq(1.0, 0.0, 0.0)[:, None, None]
+    e = rel_l2(b.populations() - w, a.populations() - w)
+    print(f"variant 1 vs 0, precision {precision}: rel L2 of f - w {e:.2e}")
+    assert e < tol
+    assert rel_l2(b.beads()[0], a.beads()[0]) < tol * 1e-3
+
+
+def test_sandwich_couette_parity():
+    # Sec. 3.1 benchmark: static solid layers (Eq. 14) between walls at 0
+    # and V0; FP64 path against the oracle, FP32 against the FP64 path
+    H = 45
+    cfg = wl.couette_only(12, H, u=0.0, nu=0.2, init_couette=0)
+    cfg.update(u_bottom=0.0, u_top=0.01, visc_ratio=50.0, xi=0.9, sandwich_zl=H / 3, sandwich_zr=2 * H / 3)
+    g, o = run_both(cfg, 3000)
+    compare_f64(g, o)
+    g32 = gpu_sim(dict(cfg, precision=1))
+    g32.step(3000)
+    assert rel_l2(g32.fields()[0], g.fields()[0]) < 1e-4
