@@ -1,0 +1,69 @@
+"""Host analysis of tumbling (Sec. 4): orientation tracking, periods, the
+Jeffery fit of Eq. 19 and the shape-regime classifier, on analytic and
+synthetic histories (no GPU)."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2212_14153_gb300 import tumbling as tb
+
+
+@pytest.mark.parametrize("r_e", [0.1, 0.132, 0.25])
+def test_analytic_jeffery_orbit_satisfies_eq19_and_period(r_e):
+    g = 5e-4
+    T = tb.jeffery_half_period(r_e, g)
+    t = np.linspace(0, 3.2 * T, 40001)
+    th = tb.jeffery_angle(t, math.pi / 2, r_e, g)
+    # the closed form obeys Eq. 19 pointwise
+    om = np.gradient(th, t)
+    A = (1 - r_e ** 2) / (1 + r_e ** 2)
+    pred = 0.5 * g * (A * np.cos(2 * th) - 1)
+    assert np.abs(om - pred)[5:-5].max() < 1e-5 * g   # finite-difference derivative
+    # every 180-degree turn takes pi (r + 1/r) / gamma_dot
+    hp = tb.half_periods(t, th)
+    assert len(hp) >= 2
+    assert np.allclose(hp, T, rtol=1e-6)
+    # the least-squares fit recovers r_e
+    r_fit, resid = tb.jeffery_fit(t, th, g)
+    assert abs(r_fit / r_e - 1) < 1e-4 and resid < 1e-5
+
+
+def test_track_unwraps_head_tail_symmetric_angles():
+    tr = tb.Track()
+    true = np.linspace(1.5, -6.0, 200)          # clockwise through several turns
+    for i, a in enumerate(true):
+        wrapped = math.atan2(math.sin(a), math.cos(a))
+        if i % 3 == 0:
+            wrapped = math.atan2(math.sin(a + math.pi), math.cos(a + math.pi))  # reversed end-to-end
+        tr.add(i, wrapped, 1.0)
+    _, th, _ = tr.arrays()
+    assert np.allclose(th - th[0], true - true[0], atol=1e-12)
+
+
+def test_orientation_and_end_to_end():
+    R = np.array([[0.0, 0.0], [4.0, 0.0], [8.0, 4.0]])
+    assert math.isclose(tb.orientation(R, 3), math.atan2(4, 8))
+    assert math.isclose(tb.end_to_end_ratio(R, 3, 4.0), math.hypot(8, 4) / 8.0)
+
+
+def _history(theta, e2e):
+    t = np.arange(len(theta), dtype=float)
+    return t, np.asarray(theta, float), np.asarray(e2e, float)
+
+
+def test_classifier_regimes():
+    g = 1e-3
+    t = np.linspace(0, 3 * tb.jeffery_half_period(0.15, g), 3000)
+    th = tb.jeffery_angle(t, 1.0, 0.15, g)
+    assert tb.classify(t, th, np.full_like(t, 0.995), g) == "jeffery"
+    # bends during each turn and straightens again
+    e2e = 0.99 - 0.1 * np.sin(th) ** 8
+    assert tb.classify(t, th, e2e, g) == "s-turn"
+    # folds during the first turn and stays folded
+    e2e = np.where(t > t[-1] * 0.2, 0.6, 0.99)
+    assert tb.classify(t, th, e2e, g) == "s-coiled"
+    # stops turning
+    th_stuck = 0.35 + 0.3 * np.exp(-t / (t[-1] * 0.1))
+    assert tb.classify(t, th_stuck, np.full_like(t, 0.99), g) == "jeffery-stuck"
+    assert tb.classify(t, th_stuck, np.full_like(t, 0.8), g) == "s-stuck"
