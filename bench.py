@@ -322,7 +322,7 @@ def run_sweep(args, rank: int, world: int):
     nbeads = sum(c["n_beads"] * c["n_fibers"] for c in inst)
     b = fpd.Batch(args.precision, len(inst), pool, nbeads, stream=stream.cuda_stream)
     T = 64  # steps per variant for the launch-shape autotuning below
-    nvar = 2
+    nvar = fpd.fpd_sweep_variants()
     for c in inst:
         b.add(c, nvar * (T + 8) + W + S)
     variant_ms = []
@@ -441,7 +441,7 @@ def main():
     ap.add_argument("--cap-bytes", type=int, default=150 << 30)
     ap.add_argument("--max-slots", type=int, default=512)
     ap.add_argument("--chunk", type=int, default=500)
-    ap.add_argument("--variant", default="auto", choices=["auto", "0", "1"])
+    ap.add_argument("--variant", default="auto", choices=["auto", "0", "1", "2"])
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

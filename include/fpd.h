@@ -173,14 +173,22 @@ int fpd_diag(fpd_sim *s, double out[4]);
  * and must not overlap.  Returns FPD_ENAN like fpd_diag.  Synchronises. */
 int fpd_diag_noalloc(fpd_sim *s, double out[4]);
 
-/* Kernel tuning (no effect on results): variant 0 runs the lattice sweep
- * with one cell per thread (32 x 8 threads per 32 x 8 tile), variant 1 with
- * two cells per thread along y (32 x 4 threads).  Chosen per workload by an
- * autotuner that times both; both give bit-identical results.
- * fpd_set_tuning synchronises and drops captured step graphs; FPD_EINVAL
- * for an unknown variant.  fpd_get_tuning: current variant and count. */
+/* Kernel tuning (same arithmetic, same results up to rounding: the
+ * compiler may contract multiply-adds differently in each variant):
+ * variant 0 runs the lattice sweep with one cell per thread (32 x 8 threads
+ * per 32 x 8 tile), variant 1 with two cells per thread along y (32 x 4
+ * threads), variant 2 with 2 (FP64) or 4 (FP32, FP16 storage) consecutive
+ * cells per thread along x, each plane moved with one 16-byte (8-byte for
+ * FP16) access; variant 2 needs nx to be a multiple of that width, and an
+ * instance whose nx is not runs variant 0 instead.  Chosen per workload by
+ * an autotuner that times them.  fpd_set_tuning synchronises and drops
+ * captured step graphs; FPD_EINVAL for an unknown variant.  fpd_get_tuning:
+ * current variant and count. */
 int fpd_set_tuning(fpd_sim *s, int32_t variant);
 int fpd_get_tuning(const fpd_sim *s, int32_t *variant, int32_t *n_variants);
+/* Number of sweep variants (host only: needs no device or handle).  The
+ * paper has no counterpart: launch shapes are an implementation choice. */
+int32_t fpd_sweep_variants(void);
 
 /* Derived parameters: out[0] nu_f, [1] k_s, [2] k_b, [3] k_ev, [4] l_0,
  * [5] support radius a + phi_cut xi, [6] gamma_dot, [7] stored bytes per
@@ -227,7 +235,9 @@ int fpd_batch_add(fpd_batch *b, const fpd_params *p, int64_t n_steps, int32_t *s
  * the work asynchronously (the call may synchronise after admissions). */
 int fpd_batch_run(fpd_batch *b, int64_t max_steps, int64_t *steps_done);
 
-/* Lattice sweep variant of the batch (as fpd_set_tuning). */
+/* Lattice sweep variant of the batch (as fpd_set_tuning; under variant 2
+ * an instance whose nx is not a multiple of the vector width runs its tiles
+ * with that many cells per thread along y instead). */
 int fpd_batch_set_tuning(fpd_batch *b, int32_t variant);
 
 /* Block until the batch's work has finished. */

@@ -4,8 +4,9 @@ Each sweep variant (see fpd_set_tuning) is timed with CUDA events on a
 scratch instance of the same workload (same parameters, so the same hot
 tiles), after warm-up, and the fastest is returned and cached per GPU,
 precision and lattice size in a JSON file ($FPD_TUNING_CACHE, default
-~/.cache/fpd_gb300/tuning.json).  Variants give bit-identical results, so
-the choice only affects speed.
+~/.cache/fpd_gb300/tuning.json).  Variants compute the same arithmetic
+(they differ only in how the compiler contracts multiply-adds, i.e. at the
+rounding level), so the choice only affects speed.
 """
 from __future__ import annotations
 

@@ -513,6 +513,8 @@ int fpd_set_tuning(fpd_sim *s, int32_t variant) {
     return FPD_OK;
 }
 
+int32_t fpd_sweep_variants(void) { return fpd::kLatticeVariants; }
+
 int fpd_get_tuning(const fpd_sim *s, int32_t *variant, int32_t *n_variants) {
     if (!s) return FPD_EINVAL;
     if (variant) *variant = s->variant;

@@ -21,8 +21,11 @@ constexpr int kGraphSteps = 32;  // time steps per captured graph chunk
 // of the same step: the sweep is then launched as a programmatic dependent
 // of it and loads its populations before waiting for it.
 // variant: 0 = one cell per thread (32 x 8 threads), 1 = two cells per
-// thread along y (32 x 4 threads); same tiles, same results.
-constexpr int kLatticeVariants = 2;
+// thread along y (32 x 4 threads), 2 = lattice_vec_width(precision) cells per
+// thread along x with vector loads and stores ((32 / width) x 8 threads;
+// needs nx % width == 0, otherwise variant 0 runs); same tiles, same results.
+constexpr int kLatticeVariants = 3;
+inline int lattice_vec_width(int precision) { return precision == 0 ? 2 : 4; }
 cudaError_t launch_lattice(int precision, const Inst *inst_d, const Inst &inst_h, void *pool, BeadTab tab,
                            const unsigned *mask_read, unsigned *mask_clear, int parity, int after_beads,
                            int variant, cudaStream_t st);
@@ -42,7 +45,9 @@ cudaError_t launch_beads(int precision, const Inst *inst_d, const int2 *blist, i
                          int advance, unsigned *counters, int pdl, cudaStream_t st);
 
 // Batched sweep over a packed tile list of many instances (tiles[t] =
-// (slot, by << 16 | bx)); each instance at its own parity.
+// (slot, by << 16 | bx)); each instance at its own parity.  Under variant 2
+// the tiles of an instance whose nx is not a multiple of the vector width
+// run with that many cells per thread along y on the same threads.
 cudaError_t launch_lattice_batch(int precision, const Inst *insts, const int2 *tiles, int ntiles, void *pool,
                                  BeadTab tab0, BeadTab tab1, const unsigned *mask_read, unsigned *mask_clear,
                                  int gparity, int after_beads, int variant, cudaStream_t st);

@@ -97,15 +97,16 @@ __device__ __forceinline__ void cell_overlay(const Inst &I, const BeadTab &tab, 
 }
 
 // One tile of the sweep: tile (bx, by) of instance I at the instance's step
-// parity.  The CTA has kTileX x (kTileY / CY) threads; thread (tx, ty) owns
-// the CY cells (x, y0 + ty + k kTileY / CY), k < CY, of its column.
+// parity, on kTileX x (kTileY / CY) threads; thread (tx, ty) owns the CY
+// cells (x, y0 + ty + k kTileY / CY), k < CY, of its column.
 template <class S, int CY>
 __device__ __forceinline__ void lattice_tile(const Inst &I, S *__restrict__ pool, const BeadTab &tab,
                                              const unsigned *__restrict__ mask_read, unsigned *__restrict__ mask_clear,
-                                             const int bx, const int by, const int parity, const int early_load) {
+                                             const int bx, const int by, const int parity, const int early_load,
+                                             const int tx, const int ty) {
     using R = typename Real<S>::type;
     constexpr int RY = kTileY / CY;
-    const int x = bx * kTileX + threadIdx.x;
+    const int x = bx * kTileX + tx;
     const int tile = I.tile_base + by * I.ntx + bx;
     const int W = I.mask_words;
     S *A = pool + I.pop_off;
@@ -115,7 +116,7 @@ __device__ __forceinline__ void lattice_tile(const Inst &I, S *__restrict__ pool
     R g[CY][9];
 #pragma unroll
     for (int k = 0; k < CY; ++k) {
-        y[k] = by * kTileY + threadIdx.y + k * RY;
+        y[k] = by * kTileY + ty + k * RY;
         valid[k] = x < I.nx && y[k] < I.ny;
         C[k] = make_cell(I, x, valid[k] ? y[k] : 0);
     }
@@ -128,7 +129,7 @@ __device__ __forceinline__ void lattice_tile(const Inst &I, S *__restrict__ pool
     }
     pdl_wait();
     pdl_trigger();
-    if (threadIdx.x == 0 && threadIdx.y == 0)  // the other parity's mask, for the next bead phase
+    if (tx == 0 && ty == 0)  // the other parity's mask, for the next bead phase
         for (int w = 0; w < W; ++w) mask_clear[tile * W + w] = 0u;
     if (!valid[0]) return;  // cells further down the column are invalid too
     if (!early_load) {
@@ -153,7 +154,8 @@ template <class S, int CY>
 __global__ void __launch_bounds__(kTileX *kTileY / CY)
     k_lattice(const Inst I, S *__restrict__ pool, const BeadTab tab, const unsigned *__restrict__ mask_read,
               unsigned *__restrict__ mask_clear, const int parity, const int early_load) {
-    lattice_tile<S, CY>(I, pool, tab, mask_read, mask_clear, blockIdx.x, blockIdx.y, parity, early_load);
+    lattice_tile<S, CY>(I, pool, tab, mask_read, mask_clear, blockIdx.x, blockIdx.y, parity, early_load,
+                        threadIdx.x, threadIdx.y);
 }
 
 // Batched sweep over a packed tile list: tiles[t] = (instance slot,
@@ -175,7 +177,310 @@ __global__ void __launch_bounds__(kTileX *kTileY / CY)
     __syncthreads();
     const int parity = gparity ^ sI.par_xor;
     lattice_tile<S, CY>(sI, pool, parity ? tab1 : tab0, mask_read, mask_clear, t.y & 0xffff, t.y >> 16, parity,
-                        early_load);
+                        early_load, threadIdx.x, threadIdx.y);
+}
+
+// ------------------------------------------------ vectorised sweep (variant 2)
+// Each thread owns NV consecutive cells of one tile row and moves each of its
+// nine planes with one 16-byte access (8 bytes for FP16 storage).  A tile row
+// of 32 cells is a segment of G = 32 / NV lanes of one warp.  Even steps are
+// purely local.  On odd steps a direction with c_kx = +1 needs the element
+// one to the left of the thread's vector and one of its results lands one to
+// the right (mirrored for c_kx = -1): the missing element comes from the
+// neighbouring lane by a shuffle; at the segment ends (tile edges, the
+// periodic wrap, the last cell of a row) the edge lane reads or writes that
+// single element with a scalar access, and leaves out of its vector store
+// the element its neighbour tile writes.  Requires nx % NV == 0.
+
+template <class S, int NV> struct VecIO;
+template <> struct VecIO<float, 4> {
+    static __device__ __forceinline__ void ld(const float *p, float, float v[4]) {
+        const float4 t = *reinterpret_cast<const float4 *>(p);
+        v[0] = t.x, v[1] = t.y, v[2] = t.z, v[3] = t.w;
+    }
+    static __device__ __forceinline__ void st(float *p, const float v[4], float) {
+        *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+    // elements 1..3 (the first is written by the tile to the left)
+    static __device__ __forceinline__ void st_tail(float *p, const float v[4], float) {
+        p[1] = v[1];
+        *reinterpret_cast<float2 *>(p + 2) = make_float2(v[2], v[3]);
+    }
+    // elements 0..2 (the last is written by the tile to the right)
+    static __device__ __forceinline__ void st_head(float *p, const float v[4], float) {
+        *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
+        p[2] = v[2];
+    }
+};
+template <> struct VecIO<double, 2> {
+    static __device__ __forceinline__ void ld(const double *p, float, double v[2]) {
+        const double2 t = *reinterpret_cast<const double2 *>(p);
+        v[0] = t.x, v[1] = t.y;
+    }
+    static __device__ __forceinline__ void st(double *p, const double v[2], float) {
+        *reinterpret_cast<double2 *>(p) = make_double2(v[0], v[1]);
+    }
+    static __device__ __forceinline__ void st_tail(double *p, const double v[2], float) { p[1] = v[1]; }
+    static __device__ __forceinline__ void st_head(double *p, const double v[2], float) { p[0] = v[0]; }
+};
+template <> struct VecIO<__half, 4> {
+    // same rounding as the scalar path: exact widening, then one multiply;
+    // one multiply, then round-to-nearest narrowing
+    static __device__ __forceinline__ void ld(const __half *p, float inv_scale, float v[4]) {
+        const uint2 t = *reinterpret_cast<const uint2 *>(p);
+        const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&t.x));
+        const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&t.y));
+        v[0] = a.x * inv_scale, v[1] = a.y * inv_scale, v[2] = b.x * inv_scale, v[3] = b.y * inv_scale;
+    }
+    static __device__ __forceinline__ __half2 pack(float a, float b, float scale) {
+        return __floats2half2_rn(a * scale, b * scale);
+    }
+    static __device__ __forceinline__ void st(__half *p, const float v[4], float scale) {
+        const __half2 a = pack(v[0], v[1], scale), b = pack(v[2], v[3], scale);
+        uint2 t;
+        t.x = *reinterpret_cast<const unsigned *>(&a);
+        t.y = *reinterpret_cast<const unsigned *>(&b);
+        *reinterpret_cast<uint2 *>(p) = t;
+    }
+    static __device__ __forceinline__ void st_tail(__half *p, const float v[4], float scale) {
+        p[1] = __float2half_rn(v[1] * scale);
+        *reinterpret_cast<__half2 *>(p + 2) = pack(v[2], v[3], scale);
+    }
+    static __device__ __forceinline__ void st_head(__half *p, const float v[4], float scale) {
+        *reinterpret_cast<__half2 *>(p) = pack(v[0], v[1], scale);
+        p[2] = __float2half_rn(v[2] * scale);
+    }
+};
+
+template <class S> struct VecWidth { static constexpr int value = 16 / (int)sizeof(S); };
+template <> struct VecWidth<__half> { static constexpr int value = 4; };
+
+// The NV cells x0 .. x0 + NV - 1 of row y owned by one thread.
+struct VCell {
+    int x0, xm, xp;  // first cell, the cell left of it, the cell right of the last (periodic)
+    int r0, rm, rp;  // element offsets of rows y, y - 1, y + 1
+    bool bot, top, valid;
+    bool left, right;  // first lane of its segment / last lane holding cells of its row segment
+};
+template <int NV>
+__device__ __forceinline__ VCell make_vcell(const Inst &I, int x0, int y, int lane_in_seg) {
+    constexpr int G = kTileX / NV;
+    VCell c;
+    c.valid = x0 < I.nx && y < I.ny;
+    const int yy = c.valid ? y : 0;
+    c.x0 = x0;
+    c.xm = (x0 == 0) ? I.nx - 1 : x0 - 1;
+    c.xp = (x0 + NV >= I.nx) ? 0 : x0 + NV;
+    c.r0 = yy * I.pitch;
+    c.rm = c.r0 - I.pitch;
+    c.rp = c.r0 + I.pitch;
+    c.bot = (yy == 0);
+    c.top = (yy == I.ny - 1);
+    c.left = lane_in_seg == 0;
+    c.right = lane_in_seg == G - 1 || x0 + NV == I.nx;
+    return c;
+}
+
+// Gather of direction k into g[j][k] for the thread's NV cells (see load_one
+// for the scalar form of both parities).  Every lane executes the shuffles.
+template <int k, class S, int NV, class R>
+__device__ __forceinline__ void vload_one(const S *__restrict__ A, const Inst &I, const VCell &C, int parity,
+                                          R g[NV][9]) {
+    constexpr int cx = Q<k>::cx, cy = Q<k>::cy, o = Q<k>::opp;
+    constexpr int G = kTileX / NV;
+    R v[NV];
+    if (parity == 0) {
+        if (C.valid) VecIO<S, NV>::ld(A + (k * I.plane32 + C.r0 + C.x0), I.inv_scale[k], v);
+#pragma unroll
+        for (int j = 0; j < NV; ++j) g[j][k] = C.valid ? v[j] : (R)0;
+        return;
+    }
+    const bool wall = (cy > 0 && C.bot) || (cy < 0 && C.top);
+    const int row = wall ? C.r0 : (cy > 0 ? C.rm : (cy < 0 ? C.rp : C.r0));
+    // scale[k] == scale[opp k]: one factor serves both planes
+    if (C.valid) VecIO<S, NV>::ld(A + ((wall ? k : o) * I.plane32 + row + C.x0), I.inv_scale[k], v);
+    else {
+#pragma unroll
+        for (int j = 0; j < NV; ++j) v[j] = (R)0;
+    }
+    R nb = (R)0;
+    if constexpr (cx > 0) nb = __shfl_up_sync(0xffffffffu, v[NV - 1], 1, G);
+    if constexpr (cx < 0) nb = __shfl_down_sync(0xffffffffu, v[0], 1, G);
+    if (wall) {
+        const R b = bb_term<R>(I, cy > 0 ? 0 : 1, k);
+#pragma unroll
+        for (int j = 0; j < NV; ++j) g[j][k] = v[j] + b;
+        return;
+    }
+    if constexpr (cx == 0) {
+#pragma unroll
+        for (int j = 0; j < NV; ++j) g[j][k] = v[j];
+    } else if constexpr (cx > 0) {
+        if (C.left && C.valid) nb = (R)Store<S>::ld(A + (o * I.plane32 + row + C.xm), I.inv_scale[o]);
+        g[0][k] = nb;
+#pragma unroll
+        for (int j = 1; j < NV; ++j) g[j][k] = v[j - 1];
+    } else {
+        if (C.right && C.valid) nb = (R)Store<S>::ld(A + (o * I.plane32 + row + C.xp), I.inv_scale[o]);
+#pragma unroll
+        for (int j = 0; j < NV - 1; ++j) g[j][k] = v[j + 1];
+        g[NV - 1][k] = nb;
+    }
+}
+
+// Scatter of direction k (see store_one for the scalar form).
+template <int k, class S, int NV, class R>
+__device__ __forceinline__ void vstore_one(S *__restrict__ A, const Inst &I, const VCell &C, int parity,
+                                           const R g[NV][9]) {
+    constexpr int cx = Q<k>::cx, cy = Q<k>::cy, o = Q<k>::opp;
+    constexpr int G = kTileX / NV;
+    R v[NV];
+    if (parity == 0) {
+        if (!C.valid) return;
+#pragma unroll
+        for (int j = 0; j < NV; ++j) v[j] = g[j][k];
+        VecIO<S, NV>::st(A + (o * I.plane32 + C.r0 + C.x0), v, I.scale[o]);
+        return;
+    }
+    // the results shifted by c_kx within the vector, the neighbour's in the gap
+    if constexpr (cx > 0) {
+        v[0] = __shfl_up_sync(0xffffffffu, g[NV - 1][k], 1, G);
+#pragma unroll
+        for (int j = 1; j < NV; ++j) v[j] = g[j - 1][k];
+    } else if constexpr (cx < 0) {
+        v[NV - 1] = __shfl_down_sync(0xffffffffu, g[0][k], 1, G);
+#pragma unroll
+        for (int j = 0; j < NV - 1; ++j) v[j] = g[j + 1][k];
+    }
+    if (!C.valid) return;
+    const bool wall = (cy > 0 && C.top) || (cy < 0 && C.bot);
+    if (wall) {
+        const R b = bb_term<R>(I, cy > 0 ? 1 : 0, k);
+#pragma unroll
+        for (int j = 0; j < NV; ++j) v[j] = g[j][k] - b;
+        VecIO<S, NV>::st(A + (o * I.plane32 + C.r0 + C.x0), v, I.scale[o]);
+        return;
+    }
+    const int row = cy > 0 ? C.rp : (cy < 0 ? C.rm : C.r0);
+    S *p = A + (k * I.plane32 + row + C.x0);
+    if constexpr (cx == 0) {
+#pragma unroll
+        for (int j = 0; j < NV; ++j) v[j] = g[j][k];
+        VecIO<S, NV>::st(p, v, I.scale[k]);
+    } else if constexpr (cx > 0) {
+        if (C.left) VecIO<S, NV>::st_tail(p, v, I.scale[k]);
+        else VecIO<S, NV>::st(p, v, I.scale[k]);
+        if (C.right) Store<S>::st(A + (k * I.plane32 + row + C.xp), g[NV - 1][k], I.scale[k]);
+    } else {
+        if (C.right) VecIO<S, NV>::st_head(p, v, I.scale[k]);
+        else VecIO<S, NV>::st(p, v, I.scale[k]);
+        if (C.left) Store<S>::st(A + (k * I.plane32 + row + C.xm), g[0][k], I.scale[k]);
+    }
+}
+
+template <class S, int NV, class R>
+__device__ __forceinline__ void vload_pops(const S *__restrict__ A, const Inst &I, const VCell &C, int parity,
+                                           R g[NV][9]) {
+    vload_one<0, S, NV>(A, I, C, parity, g);
+    vload_one<1, S, NV>(A, I, C, parity, g);
+    vload_one<2, S, NV>(A, I, C, parity, g);
+    vload_one<3, S, NV>(A, I, C, parity, g);
+    vload_one<4, S, NV>(A, I, C, parity, g);
+    vload_one<5, S, NV>(A, I, C, parity, g);
+    vload_one<6, S, NV>(A, I, C, parity, g);
+    vload_one<7, S, NV>(A, I, C, parity, g);
+    vload_one<8, S, NV>(A, I, C, parity, g);
+}
+
+template <class S, int NV, class R>
+__device__ __forceinline__ void vstore_pops(S *__restrict__ A, const Inst &I, const VCell &C, int parity,
+                                            const R g[NV][9]) {
+    vstore_one<0, S, NV>(A, I, C, parity, g);
+    vstore_one<1, S, NV>(A, I, C, parity, g);
+    vstore_one<2, S, NV>(A, I, C, parity, g);
+    vstore_one<3, S, NV>(A, I, C, parity, g);
+    vstore_one<4, S, NV>(A, I, C, parity, g);
+    vstore_one<5, S, NV>(A, I, C, parity, g);
+    vstore_one<6, S, NV>(A, I, C, parity, g);
+    vstore_one<7, S, NV>(A, I, C, parity, g);
+    vstore_one<8, S, NV>(A, I, C, parity, g);
+}
+
+// One tile with (32 / NV) x 8 threads; thread (tx, ty) owns cells
+// x0 = bx 32 + tx NV .. x0 + NV - 1 of row by 8 + ty.  No lane returns
+// before the scatter: the shuffles need the whole warp.
+template <class S>
+__device__ __forceinline__ void lattice_tile_vec(const Inst &I, S *__restrict__ pool, const BeadTab &tab,
+                                                 const unsigned *__restrict__ mask_read,
+                                                 unsigned *__restrict__ mask_clear, const int bx, const int by,
+                                                 const int parity, const int early_load) {
+    using R = typename Real<S>::type;
+    constexpr int NV = VecWidth<S>::value;
+    const int x0 = bx * kTileX + threadIdx.x * NV;
+    const int y = by * kTileY + threadIdx.y;
+    const int tile = I.tile_base + by * I.ntx + bx;
+    const int W = I.mask_words;
+    S *A = pool + I.pop_off;
+    const VCell C = make_vcell<NV>(I, x0, y, threadIdx.x);
+    R g[NV][9];
+    if (early_load) vload_pops<S, NV>(A, I, C, parity, g);
+    pdl_wait();
+    pdl_trigger();
+    if (threadIdx.x == 0 && threadIdx.y == 0)
+        for (int w = 0; w < W; ++w) mask_clear[tile * W + w] = 0u;
+    if (!early_load) vload_pops<S, NV>(A, I, C, parity, g);
+    if (C.valid) {
+        const unsigned *m = mask_read + tile * W;
+        unsigned any = 0u;
+        for (int w = 0; w < W; ++w) any |= m[w];
+#pragma unroll
+        for (int j = 0; j < NV; ++j) {
+            R Fx, Fy, s_nu, s_e, s_eps, s_q;
+            cell_overlay<R>(I, tab, m, W, any, x0 + j, y, Fx, Fy, s_nu, s_e, s_eps, s_q);
+            collide<R>(g[j], Fx, Fy, s_nu, s_e, s_eps, s_q);
+        }
+    }
+    vstore_pops<S, NV>(A, I, C, parity, g);
+}
+
+template <class S>
+__global__ void __launch_bounds__(kTileX / VecWidth<S>::value * kTileY)
+    k_lattice_vec(const Inst I, S *__restrict__ pool, const BeadTab tab, const unsigned *__restrict__ mask_read,
+                  unsigned *__restrict__ mask_clear, const int parity, const int early_load) {
+    lattice_tile_vec<S>(I, pool, tab, mask_read, mask_clear, blockIdx.x, blockIdx.y, parity, early_load);
+}
+
+// The column form needs more registers than the vector form: cap them at
+// 128 (8 CTAs of 64 threads) for FP32 / FP16 storage; FP64 (128 threads)
+// keeps 3 CTAs per SM without spilling
+template <class S> struct BatchVecMinBlocks { static constexpr int value = sizeof(S) == 8 ? 3 : 8; };
+template <class S>
+__global__ void __launch_bounds__(kTileX / VecWidth<S>::value * kTileY, BatchVecMinBlocks<S>::value)
+    k_lattice_batch_vec(const Inst *__restrict__ insts, const int2 *__restrict__ tiles, S *__restrict__ pool,
+                        const BeadTab tab0, const BeadTab tab1, const unsigned *__restrict__ mask_read,
+                        unsigned *__restrict__ mask_clear, const int gparity, const int early_load) {
+    constexpr int NT = kTileX / VecWidth<S>::value * kTileY;
+    __shared__ Inst sI;
+    const int2 t = tiles[blockIdx.x];
+    {
+        const unsigned *src = (const unsigned *)(insts + t.x);
+        unsigned *dst = (unsigned *)&sI;
+        const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+        for (int wd = tid; wd < (int)(sizeof(Inst) / 4); wd += NT) dst[wd] = src[wd];
+    }
+    __syncthreads();
+    const int parity = gparity ^ sI.par_xor;
+    // an instance whose width is not a multiple of NV runs the column form
+    // on the same threads: NV cells per thread along y
+    constexpr int NV = VecWidth<S>::value;
+    if (sI.nx % NV == 0) {
+        lattice_tile_vec<S>(sI, pool, parity ? tab1 : tab0, mask_read, mask_clear, t.y & 0xffff, t.y >> 16,
+                            parity, early_load);
+    } else {
+        const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+        lattice_tile<S, NV>(sI, pool, parity ? tab1 : tab0, mask_read, mask_clear, t.y & 0xffff, t.y >> 16,
+                            parity, early_load, tid % kTileX, tid / kTileX);
+    }
 }
 
 // Equilibrium start: f_k = f_k^eq(rho = 1, u = (u_wall(y), 0)) with the
@@ -351,8 +656,26 @@ static cudaError_t lattice_t(const Inst &I, void *pool, BeadTab tab, const unsig
 }
 
 template <class S>
+static cudaError_t lattice_vec_t(const Inst &I, void *pool, BeadTab tab, const unsigned *mask_read,
+                                 unsigned *mask_clear, int parity, int after_beads, cudaStream_t st) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(I.ntx, I.nty);
+    cfg.blockDim = dim3(kTileX / VecWidth<S>::value, kTileY);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = after_beads ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k_lattice_vec<S>, I, (S *)pool, tab, mask_read, mask_clear, parity,
+                              after_beads);
+}
+
+template <class S>
 static cudaError_t lattice_v(int variant, const Inst &I, void *pool, BeadTab tab, const unsigned *mask_read,
                              unsigned *mask_clear, int parity, int after_beads, cudaStream_t st) {
+    if (variant == 2 && I.nx % VecWidth<S>::value == 0)
+        return lattice_vec_t<S>(I, pool, tab, mask_read, mask_clear, parity, after_beads, st);
     if (variant == 1) return lattice_t<S, 2>(I, pool, tab, mask_read, mask_clear, parity, after_beads, st);
     return lattice_t<S, 1>(I, pool, tab, mask_read, mask_clear, parity, after_beads, st);
 }
@@ -386,9 +709,29 @@ static cudaError_t lattice_batch_t(const Inst *insts, const int2 *tiles, int nti
 }
 
 template <class S>
+static cudaError_t lattice_batch_vec_t(const Inst *insts, const int2 *tiles, int ntiles, void *pool, BeadTab tab0,
+                                       BeadTab tab1, const unsigned *mask_read, unsigned *mask_clear, int gparity,
+                                       int after_beads, cudaStream_t st) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(ntiles);
+    cfg.blockDim = dim3(kTileX / VecWidth<S>::value, kTileY);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = after_beads ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k_lattice_batch_vec<S>, insts, tiles, (S *)pool, tab0, tab1, mask_read,
+                              mask_clear, gparity, after_beads);
+}
+
+template <class S>
 static cudaError_t lattice_batch_v(int variant, const Inst *insts, const int2 *tiles, int ntiles, void *pool,
                                    BeadTab tab0, BeadTab tab1, const unsigned *mask_read, unsigned *mask_clear,
                                    int gparity, int after_beads, cudaStream_t st) {
+    if (variant == 2)
+        return lattice_batch_vec_t<S>(insts, tiles, ntiles, pool, tab0, tab1, mask_read, mask_clear, gparity,
+                                      after_beads, st);
     if (variant == 1)
         return lattice_batch_t<S, 2>(insts, tiles, ntiles, pool, tab0, tab1, mask_read, mask_clear, gparity,
                                      after_beads, st);

@@ -67,6 +67,7 @@ SIGNATURES = {
     "fpd_diag_noalloc": (ctypes.c_int, [ctypes.c_void_p, _DP]),
     "fpd_derived": (ctypes.c_int, [ctypes.c_void_p, _DP]),
     "fpd_set_tuning": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "fpd_sweep_variants": (ctypes.c_int32, []),
     "fpd_get_tuning": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32),
                                       ctypes.POINTER(ctypes.c_int32)]),
     "fpd_batch_set_tuning": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
@@ -175,6 +176,10 @@ def fpd_diag_noalloc(h, out) -> None:
 
 def fpd_set_tuning(h, variant: int) -> None:
     _check(load_library().fpd_set_tuning(h, int(variant)), h)
+
+
+def fpd_sweep_variants() -> int:
+    return int(load_library().fpd_sweep_variants())
 
 
 def fpd_get_tuning(h) -> tuple[int, int]:

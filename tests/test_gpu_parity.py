@@ -294,24 +294,82 @@ def test_graph_chunks_equal_direct_steps(precision):
     assert np.array_equal(a.populations(), b.populations())
 
 
+@pytest.mark.parametrize("variant", [1, 2])
 @pytest.mark.parametrize("precision,tol", [(0, 1e-13), (1, 1e-5), (2, 1e-2)])
-def test_sweep_variants_agree(precision, tol):
-    # the autotuner's launch shapes (1 or 2 cells per thread) compute the
-    # same arithmetic; the compiler may contract multiply-adds differently
-    # in the two instantiations, so they agree to rounding, not bit for bit
+def test_sweep_variants_agree(precision, tol, variant):
+    # the autotuner's launch shapes (1 or 2 cells per thread along y, or a
+    # vector of cells along x) compute the same arithmetic; the compiler may
+    # contract multiply-adds differently in each instantiation, so they
+    # agree to rounding, not bit for bit.  nx = 76: a multiple of the vector
+    # width whose last tile is 12 cells wide; ny = 45: ragged rows too
     rng = np.random.default_rng(78)
-    cfg = wl.random_fiber(rng, 75, 45, n_beads=6, a=2.0, xi=1.0, n_fibers=2, precision=precision)
+    cfg = wl.random_fiber(rng, 76, 45, n_beads=6, a=2.0, xi=1.0, n_fibers=2, precision=precision)
     a = gpu_sim(cfg)
     b = gpu_sim(cfg)
-    b.set_tuning(1)
-    assert b.tuning() == (1, 2)
+    b.set_tuning(variant)
+    assert b.tuning() == (variant, 3)
     a.step(77)
     b.step(77)
     w = oracle.feq(1.0, 0.0, 0.0)[:, None, None]
     e = rel_l2(b.populations() - w, a.populations() - w)
-    print(f"variant 1 vs 0, precision {precision}: rel L2 of f - w {e:.2e}")
+    print(f"variant {variant} vs 0, precision {precision}: rel L2 of f - w {e:.2e}")
     assert e < tol
     assert rel_l2(b.beads()[0], a.beads()[0]) < tol * 1e-3
+
+
+@pytest.mark.parametrize("seed,nx,ny,N,NF,a,xi,coll", [
+    (21, 76, 37, 5, 1, 2.0, 1.0, 0),    # last tile 12 cells wide, ragged rows
+    (22, 96, 48, 6, 2, 2.0, 0.5, 1),    # two fibers, Lallemand-Luo rates
+    (23, 36, 17, 4, 1, 2.0, 1.0, 2),    # support wider than half the lattice, BGK
+    (24, 34, 23, 3, 1, 2.5, 1.0, 0),    # FP64 vector width 2: 34 = 32 + 2
+])
+def test_vector_sweep_fp64_parity(seed, nx, ny, N, NF, a, xi, coll):
+    rng = np.random.default_rng(seed)
+    cfg = wl.random_fiber(rng, nx, ny, n_beads=N, a=a, xi=xi, n_fibers=NF, collision=coll,
+                          gx=float(rng.uniform(-1e-6, 1e-6)))
+    g = gpu_sim(cfg)
+    g.set_tuning(2)
+    o = orc_sim(cfg)
+    g.step(301)
+    o.step(301)
+    compare_f64(g, o)
+
+
+def test_vector_sweep_tiny_lattices():
+    # one vector per row (the lane is both segment ends, the periodic wrap
+    # lands in its own vector), single rows, rows of two vectors
+    for nx, ny in [(2, 5), (4, 1), (4, 9), (8, 3), (12, 2)]:
+        cfg = wl.couette_only(nx, ny, u=0.01, nu=0.15, init_couette=1)
+        cfg["gx"] = 1e-6
+        cfg["gy"] = -3e-7
+        g = gpu_sim(cfg)
+        g.set_tuning(2)
+        o = orc_sim(cfg)
+        g.step(57)
+        o.step(57)
+        compare_f64(g, o)
+        if nx % 4 == 0:
+            for p in (1, 2):
+                a = gpu_sim(dict(cfg, precision=p))
+                b = gpu_sim(dict(cfg, precision=p))
+                b.set_tuning(2)
+                a.step(57)
+                b.step(57)
+                assert np.abs(a.populations() - b.populations()).max() < (1e-7 if p == 1 else 1e-5)
+
+
+def test_vector_variant_falls_back_when_width_does_not_divide_nx():
+    # nx = 75: variant 2 runs the one-cell-per-thread sweep, bit for bit
+    rng = np.random.default_rng(31)
+    cfg = wl.random_fiber(rng, 75, 40, n_beads=5, a=2.0, xi=1.0, precision=1)
+    a = gpu_sim(cfg)
+    b = gpu_sim(cfg)
+    b.set_tuning(2)
+    a.step(45)
+    b.step(45)
+    assert np.array_equal(a.populations(), b.populations())
+    for x, y in zip(a.beads(), b.beads()):
+        assert np.array_equal(x, y)
 
 
 def test_sandwich_couette_parity():
