@@ -125,6 +125,136 @@ def classify(t: np.ndarray, theta: np.ndarray, e2e: np.ndarray, gamma_dot: float
     return "s-turn"
 
 
+def critical_fit(x: np.ndarray, T: np.ndarray, beta: float = 0.5) -> tuple[float, float, float]:
+    """Fit of the divergence law of Secs. 4.2-4.3, gamma_dot T = A (x_cr - x)^-beta
+    (x = Re_ps or the confinement C), for a given exponent beta.  With beta
+    fixed, T^(-1/beta) = c (x_cr - x) is a straight line in x, fitted by least
+    squares.  Returns (x_cr, T0, rms relative residual of T), T0 being the
+    law extrapolated to x = 0 (the paper's normalisation)."""
+    x = np.asarray(x, dtype=float)
+    T = np.asarray(T, dtype=float)
+    y = T ** (-1.0 / beta)
+    slope, icpt = np.polyfit(x, y, 1)
+    c = -slope
+    x_cr = icpt / c
+    T0 = icpt ** (-beta)
+    pred = (c * (x_cr - x)) ** (-beta)
+    return float(x_cr), float(T0), float(np.sqrt(np.mean((pred / T - 1.0) ** 2)))
+
+
+def critical_fit_beta(x: np.ndarray, T: np.ndarray, betas=None) -> tuple[float, float, float, float]:
+    """As critical_fit with the exponent also fitted (scanned over `betas`,
+    default 0.05 .. 2 in steps of 0.01): returns (x_cr, T0, beta, rms)."""
+    betas = np.arange(0.05, 2.0001, 0.01) if betas is None else betas
+    best = None
+    for b in betas:
+        with np.errstate(invalid="ignore", divide="ignore"):
+            x_cr, T0, rms = critical_fit(x, T, float(b))
+        if np.isfinite(rms) and x_cr > np.max(x) and (best is None or rms < best[3]):
+            best = (x_cr, T0, float(b), rms)
+    if best is None:
+        raise ValueError("no exponent gives a critical point beyond the data")
+    return best
+
+
+def tumbling_case(K: float, C: float, Re_ps: float, N: int = 10, a: float = 2.0, U: float = 0.02,
+               theta0: float = math.pi / 2, r_eta: float = 100.0, r_xi: float = 0.125,
+               lx_over_d: float = 25.0) -> tuple[dict, float]:
+    """Configuration of the Sec. 4 tumbling runs: one fiber of N beads of
+    diameter d = 2a (l_c = N d, r_c = 1/N) centred between walls at -U and
+    +U, H = l_c / C, L_x = lx_over_d d, Re = 4 Re_ps (Eq. 18), xi = r_xi d.
+    Returns (config, shear rate 2U/H)."""
+    d = 2.0 * a
+    lc = d * N
+    H = int(round(lc / C))
+    Lx = int(round(lx_over_d * d))
+    cfg = dict(nx=Lx, ny=H, u_bottom=-U, u_top=U, nu_f=-1.0, re=4.0 * Re_ps, visc_ratio=r_eta,
+               xi=r_xi * d, a=a, n_beads=N, n_fibers=1, stiffness_K=K, k_s=-1.0, k_b=0.0, k_ev=-1.0,
+               phi_cut=8.0, gx=0.0, gy=0.0, collision=0, s_e=1.64, s_eps=1.54, s_q=1.9,
+               init_couette=1, centres=[[Lx / 2.0, H / 2.0]], theta0=[theta0])
+    return cfg, 2.0 * U / H
+
+
+@dataclass
+class PeriodResult:
+    T: float             # steps per steady 180-degree turn (inf if none)
+    stuck_deg: float     # orientation (degrees, in (-90, 90]) of a stuck fiber, else nan
+    track: Track
+
+
+def _crossing(t, th, level):
+    """First time the unwrapped angle falls to `level` (linear interpolation)."""
+    k = int(np.argmax(th <= level))
+    if th[k] > level:
+        return None
+    if k == 0:
+        return float(t[0])
+    return float(t[k - 1] + (level - th[k - 1]) / (th[k] - th[k - 1]) * (t[k] - t[k - 1]))
+
+
+def measure_periods(configs: list[dict], max_steps: int, sample_every: int = 200, precision: int = 1,
+                    stuck_window: int | None = None, stuck_deg: float = 1.0,
+                    stream=None) -> list[PeriodResult]:
+    """Tumbling period T of every configuration (Sec. 4.2: the time of a
+    180-degree rotation), measured on the batched engine.
+
+    The first half turn after placement carries the start-up transient, so T
+    is taken between the first two crossings of the fiber's orientation
+    through theta0 - pi/2 and theta0 - 3 pi/2 (for theta0 = pi/2: from
+    horizontal to horizontal).  An instance leaves the batch as soon as its
+    period is measured, or when over the last `stuck_window` steps (default
+    max_steps / 5) it has turned by less than `stuck_deg` degrees (stuck,
+    Secs. 4.2-4.3), or at max_steps (T = inf)."""
+    from . import fpd
+    W = stuck_window or max(sample_every, max_steps // 5)
+    cells = sum(int(c["nx"]) * int(c["ny"]) for c in configs)
+    es = {0: 8, 1: 4, 2: 2}[precision]
+    pool = 9 * es * (cells + 64 * sum(int(c["ny"]) for c in configs)) + 4096 * len(configs)
+    nbeads = sum(int(c["n_beads"]) * int(c["n_fibers"]) for c in configs)
+    b = fpd.Batch(precision, len(configs), pool, nbeads, stream)
+    slots = [b.add(dict(c, precision=precision), max_steps) for c in configs]
+    tracks = [Track() for _ in configs]
+    th0 = [float(c["theta0"][0]) for c in configs]
+    res: list[PeriodResult | None] = [None] * len(configs)
+    live = set(range(len(configs)))
+
+    def sample(t):
+        for i in list(live):
+            c = configs[i]
+            R = b.beads(slots[i])[0]
+            tracks[i].add(t, orientation(R, c["n_beads"]),
+                          end_to_end_ratio(R, c["n_beads"], 2.0 * c["a"]))
+
+    sample(0)
+    done = 0
+    while live and done < max_steps:
+        d = b.run(min(sample_every, max_steps - done))
+        if d == 0:
+            break
+        done += d
+        sample(done)
+        for i in list(live):
+            t, th, _ = tracks[i].arrays()
+            # orientation is taken modulo pi; align the first sample with theta0
+            th = th + math.pi * round((th0[i] - th[0]) / math.pi)
+            t1 = _crossing(t, th, th0[i] - math.pi / 2)
+            t2 = _crossing(t, th, th0[i] - 1.5 * math.pi) if t1 is not None else None
+            if t2 is not None:
+                res[i] = PeriodResult(t2 - t1, float("nan"), tracks[i])
+            elif t[-1] >= W:
+                j = int(np.searchsorted(t, t[-1] - W))
+                if abs(th[-1] - th[j]) < math.radians(stuck_deg):
+                    ang = math.degrees(th[-1]) % 180.0
+                    res[i] = PeriodResult(float("inf"), ang - 180.0 if ang > 90.0 else ang, tracks[i])
+            if res[i] is not None:
+                live.discard(i)
+                b.remove(slots[i])
+    for i in live:
+        res[i] = PeriodResult(float("inf"), float("nan"), tracks[i])
+    b.close()
+    return res
+
+
 def run_tracks(configs: list[dict], steps: int, sample_every: int, precision: int = 1,
                stream=None) -> list[Track]:
     """Advance every configuration together on the batched engine for

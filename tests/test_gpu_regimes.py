@@ -11,7 +11,6 @@ import numpy as np
 import pytest
 
 from paper_2212_14153_gb300 import tumbling as tb
-from paper_2212_14153_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
 
@@ -25,14 +24,8 @@ def _built():
     build.build()
 
 
-def fiber_case(K, C, Re_ps, N=10, a=2.0, U=0.02, theta0=math.radians(80.0), r_eta=100.0):
-    lc = 2 * a * N
-    H = int(round(lc / C))
-    Lx = int(25 * 2 * a)                     # L_x / d = 25 (Sec. 4.3)
-    cfg = wl.couette_only(Lx, H, u=U)
-    cfg.update(nu_f=-1.0, re=4.0 * Re_ps, visc_ratio=r_eta, xi=0.125 * 2 * a, a=a, n_beads=N, n_fibers=1,
-               stiffness_K=K, centres=[[Lx / 2, H / 2]], theta0=[theta0])
-    return cfg, 2 * U / H
+def fiber_case(K, C, Re_ps, theta0=math.radians(80.0)):
+    return tb.tumbling_case(K, C, Re_ps, N=10, a=2.0, U=0.02, theta0=theta0, r_eta=100.0)
 
 
 def test_fig7_stiffness_regimes():

@@ -67,3 +67,38 @@ def test_classifier_regimes():
     th_stuck = 0.35 + 0.3 * np.exp(-t / (t[-1] * 0.1))
     assert tb.classify(t, th_stuck, np.full_like(t, 0.99), g) == "jeffery-stuck"
     assert tb.classify(t, th_stuck, np.full_like(t, 0.8), g) == "s-stuck"
+
+
+@pytest.mark.parametrize("x_cr,beta,T0", [(2.2, 0.5, 30.6), (0.7, 0.5, 29.5), (5.6, 0.3, 11.9), (0.8, 0.6, 7.3)])
+def test_critical_fit_recovers_the_divergence_law(x_cr, beta, T0):
+    # gamma_dot T = T0 (1 - x / x_cr)^-beta, sampled below x_cr (the four
+    # laws reported in Secs. 4.2-4.3)
+    x = np.linspace(0.1, 0.9, 7) * x_cr
+    T = T0 * (1 - x / x_cr) ** (-beta)
+    xc, t0, rms = tb.critical_fit(x, T, beta)
+    assert abs(xc / x_cr - 1) < 1e-10 and abs(t0 / T0 - 1) < 1e-10 and rms < 1e-10
+    xc, t0, b, rms = tb.critical_fit_beta(x, T)
+    assert abs(b - beta) < 1e-9 and abs(xc / x_cr - 1) < 1e-6
+    # the wrong exponent leaves a residual and moves the critical point
+    xc2, _, rms2 = tb.critical_fit(x, T, beta + 0.3)
+    assert rms2 > 1e-3 and abs(xc2 - x_cr) > 1e-3
+
+
+def test_critical_fit_with_noise_and_without_divergence():
+    rng = np.random.default_rng(3)
+    x = np.linspace(0.25, 2.0, 8)
+    T = 16.0 * (1 - x / 2.4) ** -0.5 * (1 + 0.01 * rng.standard_normal(x.size))
+    xc, t0, rms = tb.critical_fit(x, T, 0.5)
+    assert abs(xc - 2.4) < 0.05 and abs(t0 - 16.0) < 0.5 and rms < 0.03
+    # a period that does not grow has no critical point beyond the data
+    with pytest.raises(ValueError):
+        tb.critical_fit_beta(x, 20.0 - x)
+
+
+def test_tumbling_case_geometry():
+    cfg, g = tb.tumbling_case(3.3, 0.2, 1.5, N=10, a=2.0, U=0.02)
+    d = 4.0
+    assert cfg["ny"] == 200 and cfg["nx"] == 100            # H = l_c / C, L_x = 25 d
+    assert cfg["re"] == 6.0 and cfg["xi"] == 0.125 * d      # Re = 4 Re_ps, xi = r_xi d
+    assert g == 2 * 0.02 / 200
+    assert cfg["centres"] == [[50.0, 100.0]]
