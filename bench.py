@@ -56,14 +56,15 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(workload: str, precision: int):
-    """DRAM bytes per launch of the lattice kernel from the committed ncu
-    summary, if it was taken on the current kernel source; else None."""
+def ncu_traffic(workload: str, precision: int, variant: int):
+    """DRAM bytes per launch of the lattice kernel (the given sweep variant)
+    from the committed ncu summary, if it was taken on the current kernel
+    source; else None."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
-        e = d[f"{workload}:{precision}"]
+        e = d[f"{workload}:{precision}:v{variant}"]
         if e.get("kernel_hash") != kernel_source_hash():
             return None
         return float(e["dram_bytes_per_launch_full"])
@@ -210,7 +211,7 @@ def run_gpu(args, rank: int, world: int):
         bpc = 18 * STORE_BYTES[args.precision]
         lat_ms = kt["lattice_ms"] / max(kt["lattice_launches"], 1)
         achieved = bpc * cells / (lat_ms * 1e-3) / 1e9
-        traffic = ncu_traffic(cfg["name"], args.precision)
+        traffic = ncu_traffic(cfg["name"], args.precision, variant)
         gpu_launches = kt["lattice_launches"] + kt["bead_launches"]  # per timed region
         line = {
             "metric": "MLUPS (million lattice-cell updates per second) of the FPD-MRT step",

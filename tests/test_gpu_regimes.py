@@ -10,6 +10,7 @@ import math
 import numpy as np
 import pytest
 
+from paper_2212_14153_gb300 import studies
 from paper_2212_14153_gb300 import tumbling as tb
 
 pytestmark = pytest.mark.gpu
@@ -66,3 +67,19 @@ def test_rigid_period_grows_with_reynolds():
         periods.append(T)
         print(f"Re_ps = {r}: gamma_dot T_180 = {T * g:.2f}, Jeffery fit r_e = {r_fit:.3f} (rms {resid:.3f})")
     assert periods[0] < periods[1] < periods[2]
+
+
+def test_rigid_critical_reynolds_and_stuck_angle():
+    # Fig. 5b / Fig. 6b, r_c = 0.1, C = 0.2: the period diverges as
+    # (Re_cr - Re_ps)^-1/2 with Re_cr ~ 2.2, and at Re_ps = 6 the fiber
+    # sticks at ~20.4 degrees.  Loose pins: the paper's resolution is unstated
+    out = studies.sweep("rigid-re", values=[0.25, 1.0, 1.5, 1.75, 2.0, 6.0])
+    rows = out["rows"]
+    for r in rows:
+        print(f"Re_ps = {r['x']}: gamma_dot T = {r['gT']:.2f}, stuck at {r['stuck_deg']:.2f} deg")
+    fit = out["fit_paper_beta"]
+    print("fit (beta = 1/2):", fit, "free beta:", out.get("fit_free_beta"))
+    T = [r["gT"] for r in rows[:5]]
+    assert all(np.isfinite(T)) and np.all(np.diff(T) > 0)
+    assert 1.9 < fit["x_cr"] < 2.5 and fit["rms"] < 0.03
+    assert not np.isfinite(rows[5]["gT"]) and 15.0 < rows[5]["stuck_deg"] < 25.0
