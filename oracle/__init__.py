@@ -17,6 +17,11 @@ Parity status per function (what pins each, all in ``tests/test_oracle*.py``):
   spreading / reduction (Eqs. 4-5)        -- sum of f = sum of F_i, uniform
                                              velocity gives V_i = U exactly
   coupled step                            -- Jeffery period of a stiff fiber
+  sandwich layers (Eq. 14)                -- steady variable-viscosity
+                                             Couette closed form, 2nd order
+  periodic y, driven bead, eps_v          -- Hasimoto's drag of a periodic
+                                             array of discs; eps_v -> 0 for a
+                                             uniformly translating fluid
 """
 from __future__ import annotations
 
@@ -63,7 +68,8 @@ class OrcParams(ctypes.Structure):
         ("s_e", ctypes.c_double), ("s_eps", ctypes.c_double),
         ("s_q", ctypes.c_double), ("init_couette", ctypes.c_int32),
         ("threads", ctypes.c_int32), ("sandwich_zl", ctypes.c_double),
-        ("sandwich_zr", ctypes.c_double),
+        ("sandwich_zr", ctypes.c_double), ("periodic_y", ctypes.c_int32),
+        ("bead_fx", ctypes.c_double), ("bead_fy", ctypes.c_double),
     ]
 
 
@@ -104,6 +110,7 @@ def _load():
                 "orc_bead_energy": (ctypes.c_double, [P, ctypes.c_double, ctypes.c_double,
                                                       ctypes.c_double, _DP]),
                 "orc_phi": (ctypes.c_double, [ctypes.c_double] * 8),
+                "orc_internal_flow": (None, [ctypes.c_void_p, _DP]),
             }
             for name, (res, args) in sigs.items():
                 fn = getattr(lib, name)
@@ -123,6 +130,7 @@ DEFAULTS = dict(
     xi=1.0, a=2.0, n_beads=0, n_fibers=0, k_s=-1.0, k_b=0.0, stiffness_K=0.0,
     k_ev=-1.0, phi_cut=8.0, gx=0.0, gy=0.0, collision=0, s_e=1.64, s_eps=1.54,
     s_q=1.9, init_couette=1, threads=1, sandwich_zl=0.0, sandwich_zr=0.0,
+    periodic_y=0, bead_fx=0.0, bead_fy=0.0,
 )
 
 
@@ -193,16 +201,16 @@ def collide_bgk(f, Fx, Fy, tau) -> np.ndarray:
     return out
 
 
-def bead_forces(R, n_beads, n_fibers, a, k_s, k_b, k_ev, nx=10**6) -> np.ndarray:
-    p = make_params(nx=nx, n_beads=n_beads, n_fibers=n_fibers, a=a)
+def bead_forces(R, n_beads, n_fibers, a, k_s, k_b, k_ev, nx=10**6, **extra) -> np.ndarray:
+    p = make_params(nx=nx, n_beads=n_beads, n_fibers=n_fibers, a=a, **extra)
     R = np.ascontiguousarray(R, dtype=np.float64).reshape(-1)
     F = np.zeros_like(R)
     _load().orc_bead_forces(ctypes.byref(p), k_s, k_b, k_ev, _ptr(R), _ptr(F))
     return F.reshape(-1, 2)
 
 
-def bead_energy(R, n_beads, n_fibers, a, k_s, k_b, k_ev, nx=10**6) -> float:
-    p = make_params(nx=nx, n_beads=n_beads, n_fibers=n_fibers, a=a)
+def bead_energy(R, n_beads, n_fibers, a, k_s, k_b, k_ev, nx=10**6, **extra) -> float:
+    p = make_params(nx=nx, n_beads=n_beads, n_fibers=n_fibers, a=a, **extra)
     R = np.ascontiguousarray(R, dtype=np.float64).reshape(-1)
     return _load().orc_bead_energy(ctypes.byref(p), k_s, k_b, k_ev, _ptr(R))
 
@@ -280,6 +288,12 @@ class Sim:
         out = np.zeros(3)
         self._lib.orc_totals(self._h, _ptr(out))
         return out
+
+    def internal_flow(self) -> np.ndarray:
+        """eps_v of every bead (Sec. 3.2): sum phi (v - V)^2 / sum phi."""
+        out = np.zeros(max(self.nb, 1))
+        self._lib.orc_internal_flow(self._h, _ptr(out))
+        return out[:self.nb]
 
     def derived(self) -> dict:
         out = np.zeros(7)

@@ -30,6 +30,11 @@
  *          2000) and Guo's forcing (PRE 65, 046308, 2002) are used.
  *   Sec. 4.1 Couette cell: walls at z = 0 and z = H moving at -V0 and +V0,
  *          periodic in x; here the wall-normal axis is called y.
+ *   Sec. 3.1 sandwich Couette: static solid layers phi(y) of Eq. 14.
+ *   Sec. 3.2 driven particle: a box periodic in x and y, a constant force F_0
+ *          on the particle, and eps_v = int phi (v - V_0)^2 / int phi.  The
+ *          uniform counter-force -F_0 / (nx ny) on the fluid that keeps the
+ *          periodic box from accelerating is the caller's body force (gx, gy).
  * Readings where the paper is silent (the same list is kept with the design
  * notes): half-way moving-wall bounce-back with rho_w = 1; hard phi cutoff at
  * |r - R_i| >= a + phi_cut*xi; minimum-image distance in x; the half-force
@@ -84,6 +89,8 @@ typedef struct {
     int32_t threads;       /* OpenMP threads for the lattice loops (<=0: 1)   */
     double sandwich_zl;    /* > 0: static solid layers of Eq. 14 below zl ... */
     double sandwich_zr;    /* ... and above zr (interface width xi)           */
+    int32_t periodic_y;    /* 1: periodic in y too, no walls (Sec. 3.2)       */
+    double bead_fx, bead_fy; /* constant external force on every bead (F_0) */
 } orc_params;
 
 typedef struct {
@@ -352,6 +359,7 @@ static void forces_impl(const orc_params *p, double k_s, double k_b, double k_ev
                 if (same && (b2 - b1) < 2) continue;
                 double dx = min_image(R[2 * b1] - R[2 * b2], (double)p->nx);
                 double dy = R[2 * b1 + 1] - R[2 * b2 + 1];
+                if (p->periodic_y) dy = min_image(dy, (double)p->ny);
                 double r = sqrt(dx * dx + dy * dy);
                 if (r < l0 && r > 0.0) {
                     double mag = k_ev * (l0 - r) / r;
@@ -360,6 +368,11 @@ static void forces_impl(const orc_params *p, double k_s, double k_b, double k_ev
                 }
             }
         }
+    }
+    /* constant external force F_0 on every bead (driven particle, Sec. 3.2) */
+    for (int b = 0; b < nb; ++b) {
+        F[2 * b] += p->bead_fx;
+        F[2 * b + 1] += p->bead_fy;
     }
 }
 
@@ -387,9 +400,12 @@ static double energy_impl(const orc_params *p, double k_s, double k_b, double k_
             if (same && (b2 - b1) < 2) continue;
             double dx = min_image(R[2 * b1] - R[2 * b2], (double)p->nx);
             double dy = R[2 * b1 + 1] - R[2 * b2 + 1];
+            if (p->periodic_y) dy = min_image(dy, (double)p->ny);
             double r = sqrt(dx * dx + dy * dy);
             if (r < l0) U += 0.5 * k_ev * (l0 - r) * (l0 - r);
         }
+    /* potential of the constant external force: -F_0 . R */
+    for (int b = 0; b < nb; ++b) U -= p->bead_fx * R[2 * b] + p->bead_fy * R[2 * b + 1];
     return U;
 }
 
@@ -403,14 +419,25 @@ double orc_bead_energy(const orc_params *p, double k_s, double k_b, double k_ev,
     return energy_impl(p, k_s, k_b, k_ev, R);
 }
 
-/* Eq. 2 with the hard support cutoff, for a cell centre (xc, yc). */
-double orc_phi(double a, double xi, double rcut, double nx, double xc, double yc, double Rx, double Ry) {
-    double dx = min_image(xc - Rx, nx);
-    double dy = yc - Ry;
+/* Eq. 2 with the hard support cutoff, at separation (dx, dy) from R_i. */
+static double phi_of(double dx, double dy, double a, double xi, double rcut) {
     double r2 = dx * dx + dy * dy;
     if (r2 >= rcut * rcut) return 0.0;
     double r = sqrt(r2);
     return 0.5 * (tanh((a - r) / xi) + 1.0);
+}
+
+/* Eq. 2 for a cell centre (xc, yc), minimum image in x. */
+double orc_phi(double a, double xi, double rcut, double nx, double xc, double yc, double Rx, double Ry) {
+    return phi_of(min_image(xc - Rx, nx), yc - Ry, a, xi, rcut);
+}
+
+/* Eq. 2 for the simulation's geometry: minimum image in x, and in y too
+ * when the lattice is periodic in y. */
+static double phi_at(const orc_sim *s, double xc, double yc, double Rx, double Ry) {
+    double dy = yc - Ry;
+    if (s->p.periodic_y) dy = min_image(dy, (double)s->p.ny);
+    return phi_of(min_image(xc - Rx, (double)s->p.nx), dy, s->p.a, s->p.xi, s->rcut);
 }
 
 /* ------------------------------------------------------------------ */
@@ -420,7 +447,7 @@ double orc_phi(double a, double xi, double rcut, double nx, double xc, double yc
 /* List every cell whose centre lies within the cutoff of a bead at (Rx, Ry),
  * each cell once (minimum image in x, clipped at the walls in y), with its
  * phi.  Returns the count; the arrays hold at most support_capacity(s). */
-static int support_capacity(const orc_sim *s) {
+static int support_capacity(const orc_sim *s) {  /* cells of the bead's box */
     int w = 2 * ((int)ceil(s->rcut) + 2) + 1;
     int wx = w < s->p.nx ? w : s->p.nx, wy = w < s->p.ny ? w : s->p.ny;
     return wx * wy;
@@ -429,15 +456,20 @@ static int support_capacity(const orc_sim *s) {
 static int support_cells(const orc_sim *s, double Rx, double Ry, int *ci, int *cj, double *phi) {
     const int nx = s->p.nx, ny = s->p.ny;
     int j0 = (int)floor(Ry - s->rcut - 0.5) - 1, j1 = (int)ceil(Ry + s->rcut - 0.5) + 1;
-    if (j0 < 0) j0 = 0;
-    if (j1 > ny - 1) j1 = ny - 1;
+    if (s->p.periodic_y) {
+        if (j1 - j0 + 1 >= ny) { j0 = 0; j1 = ny - 1; }
+    } else {
+        if (j0 < 0) j0 = 0;
+        if (j1 > ny - 1) j1 = ny - 1;
+    }
     int i0 = (int)floor(Rx - s->rcut - 0.5) - 1, i1 = (int)ceil(Rx + s->rcut - 0.5) + 1;
     if (i1 - i0 + 1 >= nx) { i0 = 0; i1 = nx - 1; }
     int n = 0;
-    for (int j = j0; j <= j1; ++j)
+    for (int jj = j0; jj <= j1; ++jj)
         for (int ii = i0; ii <= i1; ++ii) {
             int i = ((ii % nx) + nx) % nx;
-            double ph = orc_phi(s->p.a, s->p.xi, s->rcut, (double)nx, i + 0.5, j + 0.5, Rx, Ry);
+            int j = ((jj % ny) + ny) % ny;
+            double ph = phi_at(s, i + 0.5, j + 0.5, Rx, Ry);
             if (ph == 0.0) continue;
             ci[n] = i; cj[n] = j; phi[n] = ph; ++n;
         }
@@ -545,9 +577,10 @@ static void collide_all(orc_sim *s) {
     }
 }
 
-/* Pull streaming, periodic in x; a population that would come from beyond a
- * wall is the reflected one of the same cell with the moving-wall term
- * -6 w_k rho_w (c_k . u_w), rho_w = 1, k the direction into the wall. */
+/* Pull streaming, periodic in x (and in y when periodic_y); a population
+ * that would come from beyond a wall is the reflected one of the same cell
+ * with the moving-wall term -6 w_k rho_w (c_k . u_w), rho_w = 1, k the
+ * direction into the wall. */
 static void stream_all(orc_sim *s) {
     const int nx = s->p.nx, ny = s->p.ny;
 #pragma omp parallel for schedule(static)
@@ -556,6 +589,7 @@ static void stream_all(orc_sim *s) {
             for (int k = 0; k < 9; ++k) {
                 int sj = j - CY[k];
                 int si = ((i - CX[k]) % nx + nx) % nx;
+                if (s->p.periodic_y) sj = (sj % ny + ny) % ny;
                 double v;
                 if (sj >= 0 && sj < ny) {
                     v = s->ftmp[IDX(k, sj, si, nx, ny)];
@@ -691,6 +725,29 @@ void orc_totals(const orc_sim *s, double *out3) {
                 m += v; px += v * CX[k]; py += v * CY[k];
             }
     out3[0] = m; out3[1] = px; out3[2] = py;
+}
+
+/* Strength of the residual flow inside each bead (Sec. 3.2):
+ *   eps_v = sum_x phi_i (v - V_i)^2 / sum_x phi_i
+ * with v the fluid velocity of orc_fields, phi_i and the sums over the
+ * bead's support at its current R_i, and V_i its latest velocity. */
+void orc_internal_flow(const orc_sim *s, double *eps) {
+    int cap = support_capacity(s);
+    int *ci = (int *)malloc(cap * sizeof(int)), *cj = (int *)malloc(cap * sizeof(int));
+    double *ph = (double *)malloc(cap * sizeof(double));
+    for (int b = 0; b < s->nb; ++b) {
+        int n = support_cells(s, s->R[2 * b], s->R[2 * b + 1], ci, cj, ph);
+        double num = 0.0, den = 0.0;
+        for (int q = 0; q < n; ++q) {
+            double ux, uy;
+            velocity_at(s, ci[q], cj[q], &ux, &uy, NULL);
+            double dx = ux - s->V[2 * b], dy = uy - s->V[2 * b + 1];
+            num += ph[q] * (dx * dx + dy * dy);
+            den += ph[q];
+        }
+        eps[b] = num / den;
+    }
+    free(ci); free(cj); free(ph);
 }
 
 /* nu_f, k_s, k_b, k_ev, l0, rcut, gamma_dot */

@@ -379,3 +379,113 @@ def test_sandwich_couette_approaches_eq13_as_interface_thins():
         dev.append(np.abs(u - eq13).max() / 0.01)
     assert dev[2] < 0.05
     assert dev[0] > dev[1] > dev[2]
+
+
+# ------------------------------------------------------------ periodic box, driven bead (Sec. 3.2)
+def test_external_force_is_gradient_and_periodic_excluded_volume():
+    # F_0 on every bead is -grad(-F_0 . R); across the periodic y edge the
+    # excluded volume uses the minimum image (energy and force alike)
+    rng = np.random.default_rng(9)
+    a, ks, kb, kev, ny = 2.0, 3.0, 0.7, 2.5, 30
+    R = np.array([[10.0, 1.0], [13.0, 1.5], [16.0, 2.0], [12.0, 28.8], [15.5, 29.5]]) + rng.normal(0, 0.1, (5, 2))
+    extra = dict(ny=ny, periodic_y=1, bead_fx=2e-3, bead_fy=-1e-3)
+    F = oracle.bead_forces(R, 5, 1, a, ks, kb, kev, **extra)
+    h = 1e-6
+    for b in range(5):
+        for d in range(2):
+            Rp = R.copy(); Rp[b, d] += h
+            Rm = R.copy(); Rm[b, d] -= h
+            fd = -(oracle.bead_energy(Rp, 5, 1, a, ks, kb, kev, **extra)
+                   - oracle.bead_energy(Rm, 5, 1, a, ks, kb, kev, **extra)) / (2 * h)
+            assert abs(F[b, d] - fd) <= 1e-7 * np.abs(F).max()
+    # beads 1 and 4 overlap only through the y edge; without periodicity they do not
+    F_walls = oracle.bead_forces(R, 5, 1, a, ks, kb, kev, ny=ny, bead_fx=2e-3, bead_fy=-1e-3)
+    assert np.abs(F - F_walls).max() > 1e-3
+    # the internal forces still sum to zero: the total is N F_0
+    assert np.allclose(F.sum(axis=0), [5 * 2e-3, -5 * 1e-3], rtol=0, atol=1e-14)
+
+
+def _shear_wave_rate(L, coll, nu=0.1):
+    k = 2 * math.pi / L
+    s = oracle.Sim(dict(nx=4, ny=L, nu_f=nu, periodic_y=1, init_couette=0, collision=coll,
+                        threads=min(4, os.cpu_count() or 1)))
+    y = np.arange(L) + 0.5
+    fy = np.stack([oracle.feq(1.0, ux, 0.0) for ux in 1e-3 * np.sin(k * y)], axis=1)
+    s.set_populations(np.repeat(fy[:, :, None], 4, axis=2).copy())
+
+    def amp():
+        return 2.0 / L * float(np.sum(s.fields()[0][:, 0] * np.sin(k * y)))
+    s.step(200)
+    a1 = amp()
+    s.step(2000)
+    return math.log(a1 / amp()) / 2000 / (nu * k * k)
+
+
+@pytest.mark.parametrize("coll", [0, 1, 2])
+def test_periodic_shear_wave_decays_at_nu_k2(coll):
+    # u_x = U sin(k y) across the periodic y direction decays as exp(-nu k^2 t);
+    # the lattice rate converges to nu k^2 at second order in k
+    e32, e64 = _shear_wave_rate(32, coll) - 1, _shear_wave_rate(64, coll) - 1
+    assert abs(e64) < 2e-3
+    assert 3.5 < e32 / e64 < 4.5
+
+
+def _driven(L, a, xi, r_eta, centre, F0=2e-5, nu=1.0 / 6.0, **kw):
+    return oracle.Sim(dict(nx=L, ny=L, nu_f=nu, n_beads=1, n_fibers=1, a=a, xi=xi, visc_ratio=r_eta,
+                           periodic_y=1, init_couette=0, bead_fx=F0, gx=-F0 / (L * L), centres=[centre],
+                           theta0=[0.0], threads=min(8, os.cpu_count() or 1), **kw))
+
+
+def test_driven_bead_periodic_translation_invariance_and_momentum_balance():
+    # the same bead shifted by whole cells across both periodic edges moves
+    # identically; the counter body force keeps the total momentum at zero
+    a = _driven(40, 2.0, 0.5, 100.0, [20.3, 20.6])
+    b = _driven(40, 2.0, 0.5, 100.0, [20.3 + 17, 20.6 + 19 - 40])  # y = -0.4: across the edge
+    a.step(300)
+    b.step(300)
+    Ra, Va, Fa, Sa = a.beads()
+    Rb, Vb, Fb, Sb = b.beads()
+    # equal up to the rounding of the shifted coordinates (a wrong wrap
+    # would differ at O(1))
+    assert abs(Vb[0] - Va[0]).max() <= 1e-10 * abs(Va[0]).max()
+    assert abs(Sb[0] - Sa[0]) <= 1e-12 * Sa[0]
+    assert abs(b.internal_flow()[0] / a.internal_flow()[0] - 1) < 1e-9
+    assert Va[0, 0] > 0 and np.allclose(Fa[0], [2e-5, 0.0], rtol=0, atol=1e-20)
+    # the momentum F_0 t put into the bead returns to the fluid exactly (up to
+    # rounding of the population sums)
+    assert np.abs(a.totals()[1:]).max() < 1e-9 * 2e-5 * 300
+
+
+def _hasimoto(a, L):
+    # drag of a periodic square array of discs in Stokes flow, area fraction c
+    c = math.pi * a * a / (L * L)
+    return 4 * math.pi / (-0.5 * math.log(c) - 0.738 + c - 0.887 * c * c + 2.039 * c ** 3)
+
+
+def test_driven_bead_drag_approaches_hasimoto():
+    # steady F_0 / (eta V_0) of the FPD disc (a = 2, H = 10 d) against the
+    # rigid-disc array: the smooth viscous rim makes the disc hydrodynamically
+    # larger than a, by less as the interface thins (r_xi = xi / d)
+    ratios = []
+    for xi in (0.5, 0.25):
+        s = _driven(40, 2.0, xi, 100.0, [20.0, 20.0])
+        s.step(int(3 * 40 * 40 / (1.0 / 6.0)))
+        V = s.beads()[1][0, 0]
+        ratios.append(2e-5 / (V / 6.0) / _hasimoto(2.0, 40))
+    assert 1.0 < ratios[1] < ratios[0] < 1.35
+
+
+def test_internal_flow_vanishes_for_uniform_translation_and_falls_with_viscosity_ratio():
+    # a uniformly moving box carries the bead rigidly: eps_v = 0 exactly
+    s = oracle.Sim(dict(nx=24, ny=24, nu_f=0.1, n_beads=1, n_fibers=1, a=2.0, xi=0.5, periodic_y=1,
+                        init_couette=1, u_bottom=0.01, u_top=0.01, centres=[[12.0, 12.0]], theta0=[0.0]))
+    s.step(20)
+    assert np.allclose(s.beads()[1][0], [0.01, 0.0], rtol=0, atol=1e-15)
+    assert s.internal_flow()[0] < 1e-28
+    # Fig. 3d: the residual internal flow of a driven particle falls with r_eta
+    ev = []
+    for r_eta in (1.0, 10.0, 100.0):
+        d = _driven(40, 2.0, 0.25, r_eta, [20.0, 20.0])
+        d.step(6000)
+        ev.append(d.internal_flow()[0] / d.beads()[1][0, 0] ** 2)
+    assert ev[0] > 3 * ev[1] > 9 * ev[2] > 0
