@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define FPD_ABI_VERSION 1
+#define FPD_ABI_VERSION 2
 
 typedef enum {
     FPD_OK = 0,
@@ -97,6 +97,11 @@ typedef struct {
                                + 1)/2 for y <= H/2, (tanh((y - zr)/xi) + 1)/2
                                above, added to the bead profiles in Eq. 1   */
     double sandwich_zr;
+    int32_t periodic_y;     /* 1: periodic in y as well, no walls (the driven
+                               particle of Sec. 3.2); wall speeds then only
+                               shape the init_couette start                   */
+    double bead_force_x;    /* constant external force F_0 added to the force */
+    double bead_force_y;    /* of every bead (Sec. 3.2), spread by Eq. 4       */
 } fpd_params;
 
 typedef struct fpd_sim fpd_sim;
@@ -172,6 +177,14 @@ int fpd_diag(fpd_sim *s, double out[4]);
  * (other streams, handles or threads on the same device) race on the array
  * and must not overlap.  Returns FPD_ENAN like fpd_diag.  Synchronises. */
 int fpd_diag_noalloc(fpd_sim *s, double out[4]);
+
+/* Residual flow inside each bead (Sec. 3.2): eps[i] = sum_x phi_i (v - V_i)^2
+ * / sum_x phi_i over the bead's support at its current position, v the
+ * velocity of fpd_read_fields and V_i the bead's latest velocity.  eps:
+ * caller-owned host array of n_beads * n_fibers doubles.  Evaluated in FP64
+ * from the stored populations whatever the storage precision.  FPD_EINVAL
+ * for a NULL pointer; synchronises. */
+int fpd_internal_flow(fpd_sim *s, double *eps);
 
 /* Kernel tuning (same arithmetic, same results up to rounding: the
  * compiler may contract multiply-adds differently in each variant):
@@ -256,6 +269,8 @@ int fpd_batch_slot_info(fpd_batch *b, int32_t slot, int64_t out[6]);
 int fpd_batch_read_fields(fpd_batch *b, int32_t slot, double *ux, double *uy, double *rho);
 int fpd_batch_read_beads(fpd_batch *b, int32_t slot, double *pos, double *vel, double *force, double *support);
 int fpd_batch_read_populations(fpd_batch *b, int32_t slot, double *f);
+/* As fpd_internal_flow for one slot (running or finished).  Synchronises. */
+int fpd_batch_internal_flow(fpd_batch *b, int32_t slot, double *eps);
 
 /* Release a slot and its pool and bead room. */
 int fpd_batch_remove(fpd_batch *b, int32_t slot);

@@ -55,6 +55,11 @@ int derive(fpd_sim *s, const fpd_params &p) {
         return fail(nullptr, FPD_EINVAL, "at most %d beads per simulation (got %d)", fpd::kMaxBeads, nb);
     if (!is_fin(p.u_bottom) || !is_fin(p.u_top) || !is_fin(p.body_force_x) || !is_fin(p.body_force_y))
         return fail(nullptr, FPD_EINVAL, "wall speeds and body force must be finite");
+    if (!is_fin(p.bead_force_x) || !is_fin(p.bead_force_y))
+        return fail(nullptr, FPD_EINVAL, "bead_force must be finite");
+    if (p.periodic_y != 0 && p.periodic_y != 1) return fail(nullptr, FPD_EINVAL, "periodic_y must be 0 or 1");
+    if (p.periodic_y && p.sandwich_zl > 0.0)
+        return fail(nullptr, FPD_EINVAL, "the sandwich layers need walls (periodic_y = 0)");
     const double l0 = 2.0 * p.bead_radius;
     const double gd = (p.u_top - p.u_bottom) / (double)p.ny;
     const double lc = p.n_beads * l0;
@@ -179,6 +184,12 @@ int derive(fpd_sim *s, const fpd_params &p) {
         I.f_sw_zr = (float)p.sandwich_zr;
         I.f_half_h = (float)I.half_h;
     }
+    I.periodic_y = p.periodic_y;
+    I.f_inv_ny = (float)(1.0 / p.ny);
+    I.ext_fx = p.bead_force_x;
+    I.ext_fy = p.bead_force_y;
+    I.f_ext_fx = (float)p.bead_force_x;
+    I.f_ext_fy = (float)p.bead_force_y;
     I.ks_l02 = s->k_s / (l0 * l0);
     I.f_ks_l02 = (float)I.ks_l02;
     I.f_kb = (float)s->k_b;
@@ -204,6 +215,14 @@ int derive(fpd_sim *s, const fpd_params &p) {
     return FPD_OK;
 }
 
+void drop_graphs(fpd_sim *s) {
+    for (int p = 0; p < fpd::kMaskBufs; ++p)
+        if (s->graph[p]) {
+            cudaGraphExecDestroy(s->graph[p]);
+            s->graph[p] = nullptr;
+        }
+}
+
 void free_all(fpd_sim *s) {
     if (!s) return;
     cudaFree(s->pool);
@@ -212,8 +231,9 @@ void free_all(fpd_sim *s) {
     cudaFree(s->masks[0]);
     cudaFree(s->scratch);
     cudaFree(s->inst_d);
-    for (int p = 0; p < 2; ++p)
-        if (s->graph[p]) cudaGraphExecDestroy(s->graph[p]);
+    if (s->host_stage) cudaFreeHost(s->host_stage);
+    s->host_stage = nullptr;
+    drop_graphs(s);
     if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
     for (auto e : s->ev_pool) cudaEventDestroy(e);
     for (auto &r : s->recs) {
@@ -280,7 +300,7 @@ int enqueue_step(fpd_sim *s, cudaStream_t st, int64_t t, bool profiled) {
             cudaEventRecord(a, st);
         }
         e = fpd::launch_beads(s->precision, s->inst_d, nullptr, I.nb, s->pool, s->tab[0], s->tab[1],
-                              s->masks[parity], parity, 1, s->counters, profiled ? 0 : 1, st);
+                              s->masks[t % fpd::kMaskBufs], parity, 1, s->counters, profiled ? 0 : 1, st);
         if (e != cudaSuccess) return cuda_fail(s, e, "bead kernel launch");
         if (profiled) {
             cudaEventRecord(b, st);
@@ -294,8 +314,13 @@ int enqueue_step(fpd_sim *s, cudaStream_t st, int64_t t, bool profiled) {
         cudaEventRecord(a, st);
     }
     const int after_beads = (I.nb > 0 && t >= 1 && !profiled) ? 1 : 0;
-    e = fpd::launch_lattice(s->precision, s->inst_d, I, s->pool, s->tab[parity], s->masks[parity],
-                            s->masks[parity ^ 1], parity, after_beads, s->variant, st);
+    constexpr int M = fpd::kMaskBufs;
+    // from step 1 on, the previous bead phase (or the initial marks) is in
+    // the previous buffer
+    const fpd::SweepMasks mk{s->masks[t % M], s->masks[(t + M - 1) % M], s->masks[(t + 1) % M],
+                             (t >= 1 && s->early_cold) ? 1 : 0};
+    e = fpd::launch_lattice(s->precision, s->inst_d, I, s->pool, s->tab[parity], mk, parity, after_beads,
+                            s->variant, st);
     if (e != cudaSuccess) return cuda_fail(s, e, "lattice kernel launch");
     if (profiled) {
         cudaEventRecord(b, st);
@@ -305,8 +330,9 @@ int enqueue_step(fpd_sim *s, cudaStream_t st, int64_t t, bool profiled) {
     return FPD_OK;
 }
 
-// Capture kGraphSteps consecutive steps starting at parity p (t >= 1) on a
-// private stream and instantiate them; the graph replays on any stream.
+// Capture kGraphSteps consecutive steps whose first step t (>= 1) has
+// t % kMaskBufs == p on a private stream and instantiate them; the graph
+// replays on any stream.
 int capture_chunk(fpd_sim *s, int p) {
     cudaError_t e;
     if (!s->cap_stream && (e = cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
@@ -314,7 +340,8 @@ int capture_chunk(fpd_sim *s, int p) {
     if ((e = cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
         return cuda_fail(s, e, "begin capture");
     int rc = FPD_OK;
-    for (int i = 0; i < fpd::kGraphSteps && rc == FPD_OK; ++i) rc = enqueue_step(s, s->cap_stream, 2 + p + i, false);
+    for (int i = 0; i < fpd::kGraphSteps && rc == FPD_OK; ++i)
+        rc = enqueue_step(s, s->cap_stream, fpd::kMaskBufs + p + i, false);
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(s->cap_stream, &g);
     if (rc != FPD_OK) {
@@ -409,6 +436,8 @@ int fpd_create(const fpd_params *p, void *stream, fpd_sim **out) {
     {
         const char *ng = std::getenv("FPD_NO_GRAPHS");
         s->use_graphs = !(ng && ng[0] == '1');
+        const char *ne = std::getenv("FPD_NO_EARLY_COLD");
+        s->early_cold = !(ne && ne[0] == '1');
     }
     const fpd::Inst &I = s->inst;
     const int nb = I.nb;
@@ -438,11 +467,12 @@ int fpd_create(const fpd_params *p, void *stream, fpd_sim **out) {
                                  b + 5 * nbm, b + 6 * nbm, b + 7 * nbm, b + 8 * nbm, f,
                                  f + nbm,     f + 2 * nbm, f + 3 * nbm, f + 4 * nbm, f + 5 * nbm};
     }
-    // tile masks for both step parities, zeroed
+    // tile masks, one buffer per step of the rotation, zeroed
     const size_t mask_words = (size_t)I.ntx * I.nty * I.mask_words;
-    FPD_TRY(cudaMalloc(&s->masks[0], 2 * mask_words * sizeof(unsigned)), "cudaMalloc tile masks");
-    s->masks[1] = s->masks[0] + mask_words;
-    FPD_TRY(cudaMemsetAsync(s->masks[0], 0, 2 * mask_words * sizeof(unsigned), s->stream), "cudaMemset masks");
+    FPD_TRY(cudaMalloc(&s->masks[0], fpd::kMaskBufs * mask_words * sizeof(unsigned)), "cudaMalloc tile masks");
+    for (int m = 1; m < fpd::kMaskBufs; ++m) s->masks[m] = s->masks[0] + m * mask_words;
+    FPD_TRY(cudaMemsetAsync(s->masks[0], 0, fpd::kMaskBufs * mask_words * sizeof(unsigned), s->stream),
+            "cudaMemset masks");
     FPD_TRY(cudaMalloc(&s->counters, sizeof(unsigned)), "cudaMalloc counters");
     FPD_TRY(cudaMemsetAsync(s->counters, 0, sizeof(unsigned), s->stream), "cudaMemset counters");
     FPD_TRY(cudaMalloc(&s->inst_d, sizeof(fpd::Inst)), "cudaMalloc instance");
@@ -477,7 +507,7 @@ int fpd_step(fpd_sim *s, int64_t n_steps) {
         // instead of two per step); the first step, remainders and profiled
         // steps are launched directly
         if (s->use_graphs && !s->profiling && s->nstep >= 1 && n_steps >= fpd::kGraphSteps) {
-            const int p = (int)(s->nstep & 1);
+            const int p = (int)(s->nstep % fpd::kMaskBufs);
             if (!s->graph[p]) {
                 int rc = capture_chunk(s, p);
                 if (rc != FPD_OK) return rc;
@@ -503,11 +533,7 @@ int fpd_set_tuning(fpd_sim *s, int32_t variant) {
     if (variant != s->variant) {
         cudaError_t e = cudaStreamSynchronize(s->stream);
         if (e != cudaSuccess) return cuda_fail(s, e, "fpd_set_tuning");
-        for (int p = 0; p < 2; ++p)
-            if (s->graph[p]) {
-                cudaGraphExecDestroy(s->graph[p]);
-                s->graph[p] = nullptr;
-            }
+        drop_graphs(s);
         s->variant = variant;
     }
     return FPD_OK;
@@ -536,7 +562,8 @@ int fpd_read_fields(fpd_sim *s, double *ux, double *uy, double *rho) {
     int rc = ensure_scratch(s, 3 * n * sizeof(double));
     if (rc) return rc;
     const int ct = cur_tab(s);
-    cudaError_t e = fpd::launch_fields(s->precision, s->inst_d, I, s->pool, s->tab[ct], s->masks[ct],
+    const int cm = s->nstep == 0 ? 0 : (int)((s->nstep - 1) % fpd::kMaskBufs);
+    cudaError_t e = fpd::launch_fields(s->precision, s->inst_d, I, s->pool, s->tab[ct], s->masks[cm],
                                        (int)(s->nstep & 1), s->scratch, s->scratch + n, s->scratch + 2 * n,
                                        s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "fields kernel");
@@ -549,33 +576,56 @@ int fpd_read_fields(fpd_sim *s, double *ux, double *uy, double *rho) {
     return fpd_sync(s);
 }
 
+int fpd_internal_flow(fpd_sim *s, double *eps) {
+    if (!s) return fail(nullptr, FPD_EINVAL, "fpd_internal_flow: NULL handle");
+    if (!eps) return fail(s, FPD_EINVAL, "fpd_internal_flow: NULL output");
+    const fpd::Inst &I = s->inst;
+    if (I.nb == 0) return fpd_sync(s);
+    int rc = ensure_scratch(s, 2 * (size_t)I.nb * sizeof(double));
+    if (rc) return rc;
+    cudaError_t e = fpd::launch_internal_flow(s->precision, I, s->pool, s->tab[cur_tab(s)], (int)(s->nstep & 1),
+                                              s->scratch, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "internal-flow kernel");
+    std::vector<double> h(2 * (size_t)I.nb);
+    e = cudaMemcpyAsync(h.data(), s->scratch, h.size() * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "copy internal flow");
+    if ((rc = fpd_sync(s))) return rc;
+    for (int q = 0; q < I.nb; ++q) eps[q] = h[2 * q] / h[2 * q + 1];
+    return FPD_OK;
+}
+
 int fpd_read_beads(fpd_sim *s, double *pos, double *vel, double *force, double *support) {
     if (!s) return fail(nullptr, FPD_EINVAL, "fpd_read_beads: NULL handle");
     const int nb = s->inst.nb;
+    if (nb == 0) return fpd_sync(s);
+    // R, V, F, S of a table are seven consecutive arrays of nb doubles: one
+    // copy into pinned staging memory, ordered after the queued steps
+    if (!s->host_stage) {
+        cudaError_t e = cudaMallocHost(&s->host_stage, 7 * (size_t)nb * sizeof(double));
+        if (e != cudaSuccess) {
+            s->host_stage = nullptr;
+            return cuda_fail(s, e, "pinned staging for bead reads");
+        }
+    }
+    const fpd::BeadTab &t = s->tab[cur_tab(s)];
+    cudaError_t e = cudaMemcpyAsync(s->host_stage, t.Rx, 7 * (size_t)nb * sizeof(double), cudaMemcpyDeviceToHost,
+                                    s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "copy beads");
     int rc = fpd_sync(s);
     if (rc) return rc;
-    if (nb == 0) return FPD_OK;
-    const fpd::BeadTab &t = s->tab[cur_tab(s)];
-    std::vector<double> a(nb), b(nb);
-    auto pair = [&](double *dst, const double *dx, const double *dy) -> int {
-        if (!dst) return FPD_OK;
-        cudaError_t e = cudaMemcpy(a.data(), dx, nb * sizeof(double), cudaMemcpyDeviceToHost);
-        if (e == cudaSuccess) e = cudaMemcpy(b.data(), dy, nb * sizeof(double), cudaMemcpyDeviceToHost);
-        if (e != cudaSuccess) return cuda_fail(s, e, "copy beads");
+    const double *h = s->host_stage;
+    auto pair = [&](double *dst, int k) {
+        if (!dst) return;
+        const double *x = h + (size_t)k * nb, *y = x + nb;
         for (int i = 0; i < nb; ++i) {
-            dst[2 * i] = a[i];
-            dst[2 * i + 1] = b[i];
+            dst[2 * i] = x[i];
+            dst[2 * i + 1] = y[i];
         }
-        return FPD_OK;
     };
-    if ((rc = pair(pos, t.Rx, t.Ry))) return rc;
-    // the initial table keeps V = 0 until the second step overwrites it
-    if ((rc = pair(vel, t.Vx, t.Vy))) return rc;
-    if ((rc = pair(force, t.Fx, t.Fy))) return rc;
-    if (support) {
-        cudaError_t e = cudaMemcpy(support, t.S, nb * sizeof(double), cudaMemcpyDeviceToHost);
-        if (e != cudaSuccess) return cuda_fail(s, e, "copy support sums");
-    }
+    pair(pos, 0);
+    pair(vel, 2);  // the initial table keeps V = 0 until the second step overwrites it
+    pair(force, 4);
+    if (support) std::memcpy(support, h + 6 * (size_t)nb, nb * sizeof(double));
     return FPD_OK;
 }
 

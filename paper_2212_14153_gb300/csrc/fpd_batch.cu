@@ -102,12 +102,13 @@ struct fpd_batch {
     unsigned *counters = nullptr;
     int2 *tiles_d = nullptr;
     int tiles_cap = 0, ntiles = 0;
-    unsigned *masks = nullptr;  // 2 * tiles_cap * mask_words
+    unsigned *masks = nullptr;  // kMaskBufs * tiles_cap * mask_words, in rotation by global step
     int2 *beads_all_d = nullptr, *beads_old_d = nullptr, *beads_fresh_d = nullptr;  // (slot, bead)
     int n_all = 0, n_old = 0, n_fresh = 0;
     std::vector<Slot> slots;
     std::vector<fpd::Inst> insts_h;
     int64_t gstep = 0;
+    int64_t rebuild_gstep = -1;  // global step at which the masks were last reset
     double cell_updates = 0.0;
     bool dirty = true;
     int variant = 0;  // lattice sweep variant
@@ -190,7 +191,8 @@ int rebuild(fpd_batch *b) {
         b->masks = nullptr;
         const int cap = std::max(std::max(b->ntiles, 1), 2 * b->tiles_cap);
         if ((e = cudaMalloc(&b->tiles_d, cap * sizeof(int2))) != cudaSuccess) return bcuda(b, e, "cudaMalloc tiles");
-        if ((e = cudaMalloc(&b->masks, 2 * (size_t)cap * b->mask_words * sizeof(unsigned))) != cudaSuccess)
+        if ((e = cudaMalloc(&b->masks, fpd::kMaskBufs * (size_t)cap * b->mask_words * sizeof(unsigned))) !=
+            cudaSuccess)
             return bcuda(b, e, "cudaMalloc masks");
         b->tiles_cap = cap;
     }
@@ -202,7 +204,8 @@ int rebuild(fpd_batch *b) {
                              cudaMemcpyHostToDevice, b->stream)) != cudaSuccess)
         return bcuda(b, e, "copy instance records");
     if (b->tiles_cap > 0 &&
-        (e = cudaMemsetAsync(b->masks, 0, 2 * (size_t)b->tiles_cap * b->mask_words * sizeof(unsigned), b->stream)) !=
+        (e = cudaMemsetAsync(b->masks, 0, fpd::kMaskBufs * (size_t)b->tiles_cap * b->mask_words * sizeof(unsigned),
+                             b->stream)) !=
             cudaSuccess)
         return bcuda(b, e, "clear masks");
     // bead lists: (slot, global bead index) for every bead, for the beads of
@@ -232,12 +235,14 @@ int rebuild(fpd_batch *b) {
     // initial bead tables of new instances (local parity 0 -> table 0)
     if (b->n_fresh > 0) {
         e = fpd::launch_beads(b->precision, b->insts_d, b->beads_fresh_d, b->n_fresh, b->pool, b->tab[0], b->tab[1],
-                              b->masks + (size_t)gp * b->tiles_cap * b->mask_words, gp, 0, b->counters, 0, b->stream);
+                              b->masks + (size_t)(b->gstep % fpd::kMaskBufs) * b->tiles_cap * b->mask_words, gp, 0,
+                              b->counters, 0, b->stream);
         if (e != cudaSuccess) return bcuda(b, e, "initial bead tables");
     }
     for (auto &sl : b->slots)
         if (sl.state == kActive) sl.fresh = false;
     b->dirty = false;
+    b->rebuild_gstep = b->gstep;
     return FPD_OK;
 }
 
@@ -392,15 +397,21 @@ int fpd_batch_run(fpd_batch *b, int64_t max_steps, int64_t *steps_done) {
         const bool any_first = b->n_old != b->n_all;
         const int2 *blist = any_first ? b->beads_old_d : b->beads_all_d;
         const int nbl = any_first ? b->n_old : b->n_all;
-        unsigned *mw = b->masks + (size_t)gp * b->tiles_cap * b->mask_words;
-        unsigned *mc = b->masks + (size_t)(gp ^ 1) * b->tiles_cap * b->mask_words;
+        constexpr int M = fpd::kMaskBufs;
+        const size_t mstride = (size_t)b->tiles_cap * b->mask_words;
+        unsigned *mw = b->masks + (size_t)(b->gstep % M) * mstride;
+        // the previous buffer holds the previous bead phase's marks unless
+        // the masks were reset before this step
+        const fpd::SweepMasks mk{mw, b->masks + (size_t)((b->gstep + M - 1) % M) * mstride,
+                                 b->masks + (size_t)((b->gstep + 1) % M) * mstride,
+                                 b->gstep > b->rebuild_gstep ? 1 : 0};
         if (nbl > 0) {
             e = fpd::launch_beads(b->precision, b->insts_d, blist, nbl, b->pool, b->tab[0], b->tab[1], mw, gp, 1,
                                   b->counters, 1, b->stream);
             if (e != cudaSuccess) return bcuda(b, e, "batched bead phase");
         }
         e = fpd::launch_lattice_batch(b->precision, b->insts_d, b->tiles_d, b->ntiles, b->pool, b->tab[0], b->tab[1],
-                                      mw, mc, gp, nbl > 0 ? 1 : 0, b->variant, b->stream);
+                                      mk, gp, nbl > 0 ? 1 : 0, b->variant, b->stream);
         if (e != cudaSuccess) return bcuda(b, e, "batched lattice sweep");
         b->gstep++;
         if (any_first) {
@@ -490,6 +501,28 @@ int fpd_batch_read_fields(fpd_batch *b, int32_t slot, double *ux, double *uy, do
                                            b->stream)) != cudaSuccess)
             return bcuda(b, e, "copy fields");
     return fpd_batch_sync(b);
+}
+
+int fpd_batch_internal_flow(fpd_batch *b, int32_t slot, double *eps) {
+    int rc = slot_ok(b, slot);
+    if (rc) return rc;
+    if (!eps) return bfail(b, FPD_EINVAL, "NULL output");
+    const Slot &sl = b->slots[slot];
+    const fpd::Inst &I = sl.inst;
+    if (I.nb == 0) return fpd_batch_sync(b);
+    if ((rc = ensure_bscratch(b, 2 * (size_t)I.nb * sizeof(double)))) return rc;
+    const int64_t l = sl.steps_done;
+    const int ct = l == 0 ? 0 : (int)((l - 1) & 1);
+    cudaError_t e = fpd::launch_internal_flow(b->precision, I, b->pool, b->tab[ct], (int)(l & 1), b->scratch,
+                                              b->stream);
+    if (e != cudaSuccess) return bcuda(b, e, "internal-flow kernel");
+    std::vector<double> h(2 * (size_t)I.nb);
+    if ((e = cudaMemcpyAsync(h.data(), b->scratch, h.size() * sizeof(double), cudaMemcpyDeviceToHost, b->stream)) !=
+        cudaSuccess)
+        return bcuda(b, e, "copy internal flow");
+    if ((rc = fpd_batch_sync(b))) return rc;
+    for (int q = 0; q < I.nb; ++q) eps[q] = h[2 * q] / h[2 * q + 1];
+    return FPD_OK;
 }
 
 int fpd_batch_read_populations(fpd_batch *b, int32_t slot, double *f) {

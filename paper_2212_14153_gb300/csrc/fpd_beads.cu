@@ -110,75 +110,40 @@ __device__ __forceinline__ void block_sum2f_to0(float a, float b, double &ra, do
     }
 }
 
-// Cells whose centre may lie within the cutoff of (Rx, Ry): a box clipped at
-// the walls; in x it wraps periodically, or spans the lattice once.  iu is
-// the unwrapped x index of the first column (column c sits at iu + c).
-struct Box {
-    int i0, j0, w, h;
-    double iu;
-};
-__device__ __forceinline__ Box support_box(const Inst &I, double Rx, double Ry) {
-    Box b;
-    b.i0 = b.j0 = b.w = b.h = 0;
-    b.iu = 0.0;
-    // a non-finite or far-away bead has no support cells (the NaN then shows
-    // up in the diagnostics, not as an out-of-range index)
-    if (!isfinite(Rx) || !isfinite(Ry) || fabs(Rx) > 1.0e9 || fabs(Ry) > 1.0e9) return b;
-    int ylo, yhi, xlo, xhi;
-    if (fabs(Rx) < 1.0e6 && fabs(Ry) < 1.0e6) {
-        // bounds with one cell of margin: FP32 rounding (< 0.07 here) cannot
-        // drop a cell whose centre lies within the cutoff
-        const float rx = (float)Rx, ry = (float)Ry, rc = I.f_rcut;
-        ylo = (int)floorf(ry - rc - 0.5f) - 1;
-        yhi = (int)ceilf(ry + rc - 0.5f) + 1;
-        xlo = (int)floorf(rx - rc - 0.5f) - 1;
-        xhi = (int)ceilf(rx + rc - 0.5f) + 1;
-        if (xhi - xlo + 1 >= I.nx) {
-            xlo = (int)floorf(rx - 0.5f * (float)I.nx);
-            xhi = xlo + I.nx - 1;
-        }
-    } else {
-        ylo = (int)floor(Ry - I.rcut - 0.5) - 1;
-        yhi = (int)ceil(Ry + I.rcut - 0.5) + 1;
-        const double xl = floor(Rx - I.rcut - 0.5) - 1.0, xh = ceil(Rx + I.rcut - 0.5) + 1.0;
-        if (xh - xl + 1.0 >= (double)I.nx) {
-            const double x0 = floor(Rx - 0.5 * I.nx);
-            b.iu = x0;
-            const long long xi = (long long)x0;
-            b.i0 = (int)(((xi % I.nx) + I.nx) % I.nx);
-            b.w = I.nx;
-        } else {
-            b.iu = xl;
-            const long long xi = (long long)xl;
-            b.i0 = (int)(((xi % I.nx) + I.nx) % I.nx);
-            b.w = (int)(xh - xl) + 1;
-        }
-        ylo = ylo < 0 ? 0 : ylo;
-        yhi = yhi > I.ny - 1 ? I.ny - 1 : yhi;
-        if (yhi < ylo) {
-            b.w = 0;
-            return b;
-        }
-        b.j0 = ylo;
-        b.h = yhi - ylo + 1;
-        return b;
-    }
-    ylo = ylo < 0 ? 0 : ylo;
-    yhi = yhi > I.ny - 1 ? I.ny - 1 : yhi;
-    if (yhi < ylo) return b;
-    b.iu = (double)xlo;
-    b.i0 = ((xlo % I.nx) + I.nx) % I.nx;  // in [0, nx)
-    b.j0 = ylo;
-    b.w = xhi - xlo + 1;
-    b.h = yhi - ylo + 1;
-    return b;
-}
-
-// d reduced to its nearest periodic image in x: the image index is found in
-// FP32 (it is an integer) and removed exactly in FP64.
+// d reduced to its nearest periodic image (period L = nx, or ny): the image
+// index is found in FP32 (it is an integer) and removed exactly in FP64.
 __device__ __forceinline__ double min_image(double d, int nx, float inv_nx) {
     const float k = rintf((float)d * inv_nx);
     return d - (double)k * (double)nx;
+}
+// A box widened by one cell on every side: wrapped (x, and y when periodic),
+// clipped at the walls, covering each direction at most once.
+__device__ __forceinline__ Box widen_box(const Inst &I, Box b) {
+    if (b.w <= 0 || b.h <= 0) return b;
+    if (b.w < I.nx) {
+        b.i0 = (b.i0 == 0) ? I.nx - 1 : b.i0 - 1;
+        b.w = (b.w + 2 < I.nx) ? b.w + 2 : I.nx;
+    }
+    if (I.periodic_y) {
+        if (b.h < I.ny) {
+            b.j0 = (b.j0 == 0) ? I.ny - 1 : b.j0 - 1;
+            b.h = (b.h + 2 < I.ny) ? b.h + 2 : I.ny;
+        }
+    } else {
+        const int lo = b.j0 > 0 ? b.j0 - 1 : 0;
+        const int hi = (b.j0 + b.h < I.ny) ? b.j0 + b.h : I.ny - 1;
+        b.j0 = lo;
+        b.h = hi - lo + 1;
+    }
+    return b;
+}
+
+// the same for the y separation, applied only when y is periodic
+__device__ __forceinline__ double min_image_y(const Inst &I, double d) {
+    return I.periodic_y ? min_image(d, I.ny, I.f_inv_ny) : d;
+}
+__device__ __forceinline__ float min_image_yf(const Inst &I, float d) {
+    return I.periodic_y ? d - (float)I.ny * rintf(d * I.f_inv_ny) : d;
 }
 
 // Force on bead q (instance-local index), given the instance's positions
@@ -231,11 +196,11 @@ __device__ void bead_force(const Inst &I, const double *Rx, const double *Ry, co
         for (int p = 0; p < I.nb; ++p) {
             float fx = xq - Xf[p];
             fx -= fnx * rintf(fx * I.f_inv_nx);
-            const float fy = yq - Yf[p];
+            const float fy = min_image_yf(I, yq - Yf[p]);
             if (fx * fx + fy * fy >= l0f2) continue;
             if (p == q || (p >= lo && p < lo + N && abs(p - q) < 2)) continue;
             const double dx = min_image(Rqx - Rx[p], I.nx, I.f_inv_nx);
-            const double dy = Rqy - Ry[p];
+            const double dy = min_image_y(I, Rqy - Ry[p]);
             const double r = sqrt(dx * dx + dy * dy);
             if (r < I.l0 && r > 0.0) {
                 const double m = I.k_ev * (I.l0 - r) / r;
@@ -244,6 +209,9 @@ __device__ void bead_force(const Inst &I, const double *Rx, const double *Ry, co
             }
         }
     }
+    // constant external force F_0 (driven particle, Sec. 3.2)
+    Fx += I.ext_fx;
+    Fy += I.ext_fy;
 }
 
 // FP32 version of bead_force for the reduced-precision paths.  Positions
@@ -292,10 +260,10 @@ __device__ void bead_force_f32(const Inst &I, const double *Rx, const double *Ry
         for (int p = 0; p < I.nb; ++p) {
             float fx = xq - Xf[p];
             fx -= fnx * rintf(fx * I.f_inv_nx);
-            const float fy = yq - Yf[p];
+            const float fy = min_image_yf(I, yq - Yf[p]);
             if (fx * fx + fy * fy >= l0s2) continue;
             if (p == q || (p >= lo && p < lo + N && abs(p - q) < 2)) continue;
-            const double dx = min_image(Rx[q] - Rx[p], I.nx, I.f_inv_nx), dy = Ry[q] - Ry[p];
+            const double dx = min_image(Rx[q] - Rx[p], I.nx, I.f_inv_nx), dy = min_image_y(I, Ry[q] - Ry[p]);
             const float r = sqrtf((float)(dx * dx + dy * dy));
             if (r < l0 && r > 0.f) {
                 const float m = kev * (l0 - r) / r;
@@ -304,6 +272,8 @@ __device__ void bead_force_f32(const Inst &I, const double *Rx, const double *Ry
             }
         }
     }
+    Fx += I.f_ext_fx;
+    Fy += I.f_ext_fy;
 }
 
 template <class S>
@@ -353,7 +323,7 @@ __global__ void __launch_bounds__(kBeadThreads)
             s_R[1] = Ry;
             s_box = bx;
             s_rel[0] = (float)(bx.iu + 0.5 - Rx);
-            s_rel[1] = (float)(bx.j0 + 0.5 - Ry);
+            s_rel[1] = (float)(bx.ju + 0.5 - Ry);
         }
         __syncthreads();
         const double Rx = s_R[0], Ry = s_R[1];
@@ -370,7 +340,7 @@ __global__ void __launch_bounds__(kBeadThreads)
                     qy = told.Ry[I.bead_off + q];
                     float dx = (float)(qx - Rx);
                     dx -= fnx * rintf(dx * I.f_inv_nx);
-                    const float dy = (float)(qy - Ry);
+                    const float dy = min_image_yf(I, (float)(qy - Ry));
                     hit = dx * dx + dy * dy < reach * reach;
                 }
                 const unsigned m = __ballot_sync(0xffffffffu, hit);
@@ -379,7 +349,7 @@ __global__ void __launch_bounds__(kBeadThreads)
                     s_rx[pos] = qx;
                     s_ry[pos] = qy;
                     s_ox[pos] = (float)min_image(Rx - qx, I.nx, I.f_inv_nx);
-                    s_oy[pos] = (float)(Ry - qy);
+                    s_oy[pos] = (float)min_image_y(I, Ry - qy);
                     const double gx = told.Gx[I.bead_off + q], gy = told.Gy[I.bead_off + q];
                     s_gx[pos] = gx;
                     s_gy[pos] = gy;
@@ -399,11 +369,13 @@ __global__ void __launch_bounds__(kBeadThreads)
         const Box bx = s_box;
         const float rel0x = s_rel[0], rel0y = s_rel[1];
         const float hnx = 0.5f * (float)I.nx, fnx = (float)I.nx;
+        const float hny = 0.5f * (float)I.ny, fny = (float)I.ny;
         double ax = 0.0, ay = 0.0;
         float axf = 0.0f, ayf = 0.0f;  // FP32 paths: per-thread partials (few terms)
         for (int c = tid; c < bx.w * bx.h; c += blockDim.x) {
             const int cj = c / bx.w, ci = c - cj * bx.w;
-            const int j = bx.j0 + cj;
+            int j = bx.j0 + cj;
+            j = (j >= I.ny) ? j - I.ny : j;
             int i = bx.i0 + ci;
             i = (i >= I.nx) ? i - I.nx : i;
             if constexpr (kF64) {
@@ -441,7 +413,9 @@ __global__ void __launch_bounds__(kBeadThreads)
                 for (int q = 0; q < nn; ++q) {
                     float ddx = dx + s_ox[q];
                     ddx = (ddx > hnx) ? ddx - fnx : ((ddx < -hnx) ? ddx + fnx : ddx);
-                    const float ph = phi_f32(ddx, dy + s_oy[q], I.f_a, I.f_inv_xi, I.f_rcut2);
+                    float ddy = dy + s_oy[q];
+                    if (I.periodic_y) ddy = (ddy > hny) ? ddy - fny : ((ddy < -hny) ? ddy + fny : ddy);
+                    const float ph = phi_f32(ddx, ddy, I.f_a, I.f_inv_xi, I.f_rcut2);
                     fx += ph * s_gxf[q];
                     fy += ph * s_gyf[q];
                 }
@@ -465,7 +439,7 @@ __global__ void __launch_bounds__(kBeadThreads)
             s_R[1] = Rny;
             s_box = nb_;
             s_rel[0] = (float)(nb_.iu + 0.5 - Rnx);
-            s_rel[1] = (float)(nb_.j0 + 0.5 - Rny);
+            s_rel[1] = (float)(nb_.ju + 0.5 - Rny);
         }
     } else if (tid == 0) {
         pdl_wait();
@@ -476,25 +450,42 @@ __global__ void __launch_bounds__(kBeadThreads)
         s_R[1] = Ry;
         s_box = bx;
         s_rel[0] = (float)(bx.iu + 0.5 - Rx);
-        s_rel[1] = (float)(bx.j0 + 0.5 - Ry);
+        s_rel[1] = (float)(bx.ju + 0.5 - Ry);
     }
     __syncthreads();
 
-    // mark bead b in the mask of every lattice tile its support box reaches
-    // (one atomicOr per tile row and tile column the box starts in)
+    // mark bead b in the mask of every lattice tile its support box, widened
+    // by one cell, reaches (one atomicOr per tile row and tile column the box
+    // starts in); the widening covers the bead's move in the next step, so
+    // the next sweep may update unmarked tiles before its bead phase ends
     {
-        const Box bx = s_box;
+        const Box bx = widen_box(I, s_box);
         const int lb = b - I.bead_off;
         const unsigned bit = 1u << (lb & 31);
-        const int tr0 = bx.j0 / kTileY;
-        const int nrows = bx.h > 0 ? (bx.j0 + bx.h - 1) / kTileY - tr0 + 1 : 0;
-        for (int t = tid; t < nrows * bx.w; t += blockDim.x) {
-            const int r = tr0 + t / bx.w, ci = t - (t / bx.w) * bx.w;
-            int col = bx.i0 + ci;
-            col = (col >= I.nx) ? col - I.nx : col;
-            if (ci != 0 && (col % kTileX) != 0) continue;
-            const int tile = I.tile_base + r * I.ntx + col / kTileX;
-            atomicOr(mask_write + tile * I.mask_words + (lb >> 5), bit);
+        if (!I.periodic_y) {
+            const int tr0 = bx.j0 / kTileY;
+            const int nrows = bx.h > 0 ? (bx.j0 + bx.h - 1) / kTileY - tr0 + 1 : 0;
+            for (int t = tid; t < nrows * bx.w; t += blockDim.x) {
+                const int r = tr0 + t / bx.w, ci = t - (t / bx.w) * bx.w;
+                int col = bx.i0 + ci;
+                col = (col >= I.nx) ? col - I.nx : col;
+                if (ci != 0 && (col % kTileX) != 0) continue;
+                const int tile = I.tile_base + r * I.ntx + col / kTileX;
+                atomicOr(mask_write + tile * I.mask_words + (lb >> 5), bit);
+            }
+        } else {
+            // rows wrap: visit each cell of the box that starts a tile row or
+            // column inside the box
+            for (int t = tid; t < bx.h * bx.w; t += blockDim.x) {
+                const int cj = t / bx.w, ci = t - cj * bx.w;
+                int row = bx.j0 + cj;
+                row = (row >= I.ny) ? row - I.ny : row;
+                int col = bx.i0 + ci;
+                col = (col >= I.nx) ? col - I.nx : col;
+                if ((cj != 0 && (row % kTileY) != 0) || (ci != 0 && (col % kTileX) != 0)) continue;
+                const int tile = I.tile_base + (row / kTileY) * I.ntx + col / kTileX;
+                atomicOr(mask_write + tile * I.mask_words + (lb >> 5), bit);
+            }
         }
     }
 
@@ -510,7 +501,9 @@ __global__ void __launch_bounds__(kBeadThreads)
             if constexpr (kF64) {
                 int i = bx.i0 + ci;
                 i = (i >= I.nx) ? i - I.nx : i;
-                acc += phi_f64(I, i + 0.5, bx.j0 + cj + 0.5, Rx, Ry);
+                int j = bx.j0 + cj;
+                j = (j >= I.ny) ? j - I.ny : j;
+                acc += phi_f64(I, i + 0.5, j + 0.5, Rx, Ry);
             } else {
                 // each thread sums at most a few terms in FP32 before the
                 // FP64 block reduction
@@ -585,11 +578,16 @@ __global__ void __launch_bounds__(kBeadThreads)
         tnew.Fy[gq] = Fy;
         tnew.Gx[gq] = Gx;
         tnew.Gy[gq] = Gy;
-        // FP32 overlay table: x wrapped into [0, nx), split into hi + lo
+        // FP32 overlay table: x (and y when periodic) wrapped into the
+        // lattice, split into hi + lo
         const double rx = s_rx[q];
         double xw = rx - (double)floorf((float)rx * I.f_inv_nx) * (double)I.nx;
         xw = (xw < 0.0) ? xw + I.nx : ((xw >= I.nx) ? xw - I.nx : xw);
-        const double yw = s_ry[q];
+        double yw = s_ry[q];
+        if (I.periodic_y) {
+            yw -= (double)floorf((float)yw * I.f_inv_ny) * (double)I.ny;
+            yw = (yw < 0.0) ? yw + I.ny : ((yw >= I.ny) ? yw - I.ny : yw);
+        }
         const float xh = (float)xw, yh = (float)yw;
         tnew.xh[gq] = xh;
         tnew.xl[gq] = (float)(xw - (double)xh);

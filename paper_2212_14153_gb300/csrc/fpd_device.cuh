@@ -55,6 +55,12 @@ struct Inst {
     int32_t sandwich, pad2_;
     double sw_zl, sw_zr, half_h;
     float f_sw_zl, f_sw_zr, f_half_h;
+    // periodic y without walls, and the constant external force on every
+    // bead (the driven particle of Sec. 3.2)
+    int32_t periodic_y;
+    float f_inv_ny;
+    double ext_fx, ext_fy;
+    float f_ext_fx, f_ext_fy;
 };
 
 // phi(y) of the sandwich layers (Eq. 14) at height y
@@ -125,11 +131,12 @@ template <> struct Store<__half> {
 // scale[opp p], so either content of a plane fits its range).
 
 // A cell with its periodic x neighbours and the element offsets of its row
-// and the rows above and below (those of a wall row are never used).
+// and the rows above and below (wrapped when y is periodic; the row beyond a
+// wall is never used).
 struct Cell {
     int x, xm, xp;  // column, column to the left / right (periodic)
     int r0, rm, rp; // element offsets of rows y, y - 1, y + 1
-    bool bot, top;  // first / last fluid row (wall half a cell beyond)
+    bool bot, top;  // first / last fluid row next to a wall (half a cell beyond)
 };
 __device__ __forceinline__ Cell make_cell(const Inst &I, int x, int y) {
     Cell c;
@@ -137,10 +144,10 @@ __device__ __forceinline__ Cell make_cell(const Inst &I, int x, int y) {
     c.xm = (x == 0) ? I.nx - 1 : x - 1;
     c.xp = (x == I.nx - 1) ? 0 : x + 1;
     c.r0 = y * I.pitch;
-    c.rm = c.r0 - I.pitch;
-    c.rp = c.r0 + I.pitch;
-    c.bot = (y == 0);
-    c.top = (y == I.ny - 1);
+    c.rm = ((y == 0) ? I.ny - 1 : y - 1) * I.pitch;
+    c.rp = ((y == I.ny - 1) ? 0 : y + 1) * I.pitch;
+    c.bot = (y == 0) && !I.periodic_y;
+    c.top = (y == I.ny - 1) && !I.periodic_y;
     return c;
 }
 
@@ -218,13 +225,91 @@ __device__ __forceinline__ double min_image_rn(double d, double L) {
 }
 
 // phi_i at cell centre (xc, yc) of bead (Rx, Ry); 0 beyond the cutoff.
+// Minimum image in x, and in y when the lattice is periodic in y.
 __device__ __forceinline__ double phi_f64(const Inst &I, double xc, double yc, double Rx, double Ry) {
     const double dx = min_image_rn(__dsub_rn(xc, Rx), (double)I.nx);
-    const double dy = __dsub_rn(yc, Ry);
+    double dy = __dsub_rn(yc, Ry);
+    if (I.periodic_y) dy = min_image_rn(dy, (double)I.ny);
     const double r2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
     if (!(r2 < I.rcut2)) return 0.0;
     const double r = sqrt(r2);
     return 0.5 * (tanh((I.a - r) / I.xi) + 1.0);
+}
+
+// Cells whose centre may lie within the cutoff of (Rx, Ry): a box that wraps
+// periodically in x (and in y when y is periodic), or spans that direction
+// once, and is clipped at the walls otherwise.  (iu, ju) are the unwrapped
+// indices of its first column and row (column c, row r sit at iu + c, ju + r);
+// (i0, j0) the same wrapped into the lattice.
+struct Box {
+    int i0, j0, w, h;
+    double iu, ju;
+};
+
+// Rows [lo, hi] of a box: wrapped (periodic y; spanning the lattice once at
+// most, starting at span_lo when it would wrap onto itself) or clipped at the
+// walls.  Returns false when no row is left.
+__device__ __forceinline__ bool box_rows(const Inst &I, long long lo, long long hi, long long span_lo, Box &b) {
+    if (I.periodic_y) {
+        if (hi - lo + 1 >= I.ny) {
+            lo = span_lo;
+            hi = lo + I.ny - 1;
+        }
+        b.ju = (double)lo;
+        b.j0 = (int)(((lo % I.ny) + I.ny) % I.ny);
+        b.h = (int)(hi - lo + 1);
+        return true;
+    }
+    lo = lo < 0 ? 0 : lo;
+    hi = hi > I.ny - 1 ? I.ny - 1 : hi;
+    if (hi < lo) return false;
+    b.ju = (double)lo;
+    b.j0 = (int)lo;
+    b.h = (int)(hi - lo + 1);
+    return true;
+}
+
+__device__ __forceinline__ Box support_box(const Inst &I, double Rx, double Ry) {
+    Box b;
+    b.i0 = b.j0 = b.w = b.h = 0;
+    b.iu = b.ju = 0.0;
+    // a non-finite or far-away bead has no support cells (the NaN then shows
+    // up in the diagnostics, not as an out-of-range index)
+    if (!isfinite(Rx) || !isfinite(Ry) || fabs(Rx) > 1.0e9 || fabs(Ry) > 1.0e9) return b;
+    if (fabs(Rx) < 1.0e6 && fabs(Ry) < 1.0e6) {
+        // bounds with one cell of margin: FP32 rounding (< 0.07 here) cannot
+        // drop a cell whose centre lies within the cutoff
+        const float rx = (float)Rx, ry = (float)Ry, rc = I.f_rcut;
+        const int ylo = (int)floorf(ry - rc - 0.5f) - 1;
+        const int yhi = (int)ceilf(ry + rc - 0.5f) + 1;
+        int xlo = (int)floorf(rx - rc - 0.5f) - 1;
+        int xhi = (int)ceilf(rx + rc - 0.5f) + 1;
+        if (xhi - xlo + 1 >= I.nx) {
+            xlo = (int)floorf(rx - 0.5f * (float)I.nx);
+            xhi = xlo + I.nx - 1;
+        }
+        if (!box_rows(I, ylo, yhi, (long long)floorf(ry - 0.5f * (float)I.ny), b)) return b;
+        b.iu = (double)xlo;
+        b.i0 = ((xlo % I.nx) + I.nx) % I.nx;  // in [0, nx)
+        b.w = xhi - xlo + 1;
+        return b;
+    }
+    const long long ylo = (long long)floor(Ry - I.rcut - 0.5) - 1, yhi = (long long)ceil(Ry + I.rcut - 0.5) + 1;
+    if (!box_rows(I, ylo, yhi, (long long)floor(Ry - 0.5 * I.ny), b)) return b;
+    const double xl = floor(Rx - I.rcut - 0.5) - 1.0, xh = ceil(Rx + I.rcut - 0.5) + 1.0;
+    if (xh - xl + 1.0 >= (double)I.nx) {
+        const double x0 = floor(Rx - 0.5 * I.nx);
+        b.iu = x0;
+        const long long xi = (long long)x0;
+        b.i0 = (int)(((xi % I.nx) + I.nx) % I.nx);
+        b.w = I.nx;
+    } else {
+        b.iu = xl;
+        const long long xi = (long long)xl;
+        b.i0 = (int)(((xi % I.nx) + I.nx) % I.nx);
+        b.w = (int)(xh - xl) + 1;
+    }
+    return b;
 }
 
 // FP32 variant for the reduced-precision lattice path: dx, dy relative to a

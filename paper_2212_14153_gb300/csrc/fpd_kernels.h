@@ -12,11 +12,28 @@ constexpr int kTileY = 8;
 constexpr int kMaxBeads = 256;   // beads per instance (shared-memory tables)
 constexpr int kBeadThreads = 256;
 constexpr int kGraphSteps = 32;  // time steps per captured graph chunk
+// Tile-mask buffers, used in rotation: the bead phase of step t marks buffer
+// t % kMaskBufs; the sweep of step t reads it (hot tiles) and buffer
+// (t - 1) % kMaskBufs (tiles it may update without waiting), and zeroes
+// buffer (t + 1) % kMaskBufs for the next bead phase.  kGraphSteps is a
+// multiple of kMaskBufs, so a captured chunk depends on t % kMaskBufs only.
+constexpr int kMaskBufs = 4;
+static_assert(kGraphSteps % kMaskBufs == 0, "graph chunks must keep the mask rotation");
+
+// The masks one sweep uses.  early_cold = 1 lets tiles that no bead marked
+// in the previous bead phase (read) update without waiting for the current
+// one; valid when `prev` holds that phase's marks (not after the masks were
+// reset) and the sweep follows the bead phase as a programmatic dependent.
+struct SweepMasks {
+    const unsigned *read;  // this step's marks
+    const unsigned *prev;  // the previous bead phase's marks
+    unsigned *clear;       // zeroed for the next bead phase
+    int early_cold;
+};
 
 // One fused collide-stream-bounce-back sweep of a single instance (Sec. 2.3
-// item (2) with the item-(1) overlay of Eqs. 1, 2, 4 evaluated in hot tiles).
-// mask_read: the per-tile bead masks written by the bead phase of this step;
-// mask_clear: the other mask buffer, zeroed for the next bead phase.
+// item (2) with the item-(1) overlay of Eqs. 1, 2, 4 evaluated in hot tiles),
+// with the tile masks of SweepMasks.
 // after_beads = 1 when the previous launch on the stream is the bead phase
 // of the same step: the sweep is then launched as a programmatic dependent
 // of it and loads its populations before waiting for it.
@@ -27,8 +44,7 @@ constexpr int kGraphSteps = 32;  // time steps per captured graph chunk
 constexpr int kLatticeVariants = 3;
 inline int lattice_vec_width(int precision) { return precision == 0 ? 2 : 4; }
 cudaError_t launch_lattice(int precision, const Inst *inst_d, const Inst &inst_h, void *pool, BeadTab tab,
-                           const unsigned *mask_read, unsigned *mask_clear, int parity, int after_beads,
-                           int variant, cudaStream_t st);
+                           const SweepMasks &masks, int parity, int after_beads, int variant, cudaStream_t st);
 
 // Bead phase (items (3) then (1)): one CTA per bead of any instance
 // (blist[i] = (instance slot, global bead index); NULL = instance 0, bead i;
@@ -49,14 +65,19 @@ cudaError_t launch_beads(int precision, const Inst *inst_d, const int2 *blist, i
 // the tiles of an instance whose nx is not a multiple of the vector width
 // run with that many cells per thread along y on the same threads.
 cudaError_t launch_lattice_batch(int precision, const Inst *insts, const int2 *tiles, int ntiles, void *pool,
-                                 BeadTab tab0, BeadTab tab1, const unsigned *mask_read, unsigned *mask_clear,
-                                 int gparity, int after_beads, int variant, cudaStream_t st);
+                                 BeadTab tab0, BeadTab tab1, const SweepMasks &masks, int gparity, int after_beads,
+                                 int variant, cudaStream_t st);
 
 cudaError_t launch_init(int precision, const Inst *inst_d, const Inst &inst_h, void *pool, int couette,
                         cudaStream_t st);
 
 cudaError_t launch_fields(int precision, const Inst *inst_d, const Inst &inst_h, const void *pool, BeadTab tab,
                           const unsigned *mask, int parity, double *ux, double *uy, double *rho, cudaStream_t st);
+
+// eps_v numerator and denominator of every bead of the instance (Sec. 3.2):
+// out[2 q] = sum_x phi_q |u - V_q|^2, out[2 q + 1] = sum_x phi_q, FP64.
+cudaError_t launch_internal_flow(int precision, const Inst &inst_h, const void *pool, BeadTab tab, int parity,
+                                 double *out, cudaStream_t st);
 
 cudaError_t launch_read_pops(int precision, const Inst *inst_d, const Inst &inst_h, const void *pool,
                              int parity, double *f, cudaStream_t st);

@@ -44,7 +44,7 @@ __device__ __forceinline__ void cell_overlay(const Inst &I, const BeadTab &tab, 
         }
         const double xc = x + 0.5, yc = y + 0.5;
         double Phi = I.sandwich ? sandwich_phi_f64(I, yc) : 0.0;
-        for (int w = 0; w < W; ++w) {
+        for (int w = 0; w < W && any; ++w) {
             unsigned bits = m[w];
             while (bits) {
                 const int q = I.bead_off + 32 * w + __ffs(bits) - 1;
@@ -70,9 +70,10 @@ __device__ __forceinline__ void cell_overlay(const Inst &I, const BeadTab &tab, 
             return;
         }
         const float hnx = 0.5f * I.nx, fnx = (float)I.nx;
+        const float hny = 0.5f * I.ny, fny = (float)I.ny;
         const float xc = (float)x + 0.5f, yc = (float)y + 0.5f;
         float Phi = I.sandwich ? sandwich_phi_f32(I, yc) : 0.f;
-        for (int w = 0; w < W; ++w) {
+        for (int w = 0; w < W && any; ++w) {
             unsigned bits = m[w];
             while (bits) {
                 const int q = I.bead_off + 32 * w + __ffs(bits) - 1;
@@ -84,7 +85,13 @@ __device__ __forceinline__ void cell_overlay(const Inst &I, const BeadTab &tab, 
                 const float d0 = xcl - bx;
                 xcl = (d0 > hnx) ? xcl - fnx : ((d0 < -hnx) ? xcl + fnx : xcl);
                 const float dx = (xcl - bx) - tab.xl[q];
-                const float dy = (yc - tab.yh[q]) - tab.yl[q];
+                const float by_ = tab.yh[q];
+                float ycl = yc;
+                if (I.periodic_y) {
+                    const float e0 = ycl - by_;
+                    ycl = (e0 > hny) ? ycl - fny : ((e0 < -hny) ? ycl + fny : ycl);
+                }
+                const float dy = (ycl - by_) - tab.yl[q];
                 const float ph = phi_f32(dx, dy, I.f_a, I.f_inv_xi, I.f_rcut2);
                 Phi += ph;
                 Fx += ph * tab.gxf[q];
@@ -96,14 +103,31 @@ __device__ __forceinline__ void cell_overlay(const Inst &I, const BeadTab &tab, 
     }
 }
 
+// Whether a tile may be updated without waiting for this step's bead phase:
+// no bead marked it in the previous bead phase, whose marks cover each
+// support widened by a cell.  A bead moves less than a cell per step (its
+// velocity is a weighted mean of fluid velocities, which stay far below the
+// lattice's one cell per step), so no support reaches such a tile in this
+// step either, and the bead phase reads no population of it.  The lead CTA
+// always waits: the next launch in the stream then cannot start before the
+// bead phase has completed.
+__device__ __forceinline__ bool tile_cold_early(const unsigned *__restrict__ prev, const int W, const int early_cold,
+                                                const bool lead) {
+    if (!early_cold || lead) return false;
+    unsigned any = 0u;
+    for (int w = 0; w < W; ++w) any |= prev[w];
+    return any == 0u;
+}
+
 // One tile of the sweep: tile (bx, by) of instance I at the instance's step
 // parity, on kTileX x (kTileY / CY) threads; thread (tx, ty) owns the CY
 // cells (x, y0 + ty + k kTileY / CY), k < CY, of its column.
 template <class S, int CY>
 __device__ __forceinline__ void lattice_tile(const Inst &I, S *__restrict__ pool, const BeadTab &tab,
-                                             const unsigned *__restrict__ mask_read, unsigned *__restrict__ mask_clear,
+                                             const unsigned *__restrict__ mask_read,
+                                             const unsigned *__restrict__ mask_prev, unsigned *__restrict__ mask_clear,
                                              const int bx, const int by, const int parity, const int early_load,
-                                             const int tx, const int ty) {
+                                             const int early_cold, const bool lead, const int tx, const int ty) {
     using R = typename Real<S>::type;
     constexpr int RY = kTileY / CY;
     const int x = bx * kTileX + tx;
@@ -127,9 +151,10 @@ __device__ __forceinline__ void lattice_tile(const Inst &I, S *__restrict__ pool
         for (int k = 0; k < CY; ++k)
             if (valid[k]) load_pops<S, R>(A, I, C[k], parity, g[k]);
     }
-    pdl_wait();
+    const bool cold = tile_cold_early(mask_prev + tile * W, W, early_cold, lead);
+    if (!cold) pdl_wait();
     pdl_trigger();
-    if (tx == 0 && ty == 0)  // the other parity's mask, for the next bead phase
+    if (tx == 0 && ty == 0)  // a mask of two steps back, for the next bead phase
         for (int w = 0; w < W; ++w) mask_clear[tile * W + w] = 0u;
     if (!valid[0]) return;  // cells further down the column are invalid too
     if (!early_load) {
@@ -139,7 +164,8 @@ __device__ __forceinline__ void lattice_tile(const Inst &I, S *__restrict__ pool
     }
     const unsigned *m = mask_read + tile * W;
     unsigned any = 0u;
-    for (int w = 0; w < W; ++w) any |= m[w];
+    if (!cold)
+        for (int w = 0; w < W; ++w) any |= m[w];
 #pragma unroll
     for (int k = 0; k < CY; ++k) {
         if (!valid[k]) continue;
@@ -153,9 +179,10 @@ __device__ __forceinline__ void lattice_tile(const Inst &I, S *__restrict__ pool
 template <class S, int CY>
 __global__ void __launch_bounds__(kTileX *kTileY / CY)
     k_lattice(const Inst I, S *__restrict__ pool, const BeadTab tab, const unsigned *__restrict__ mask_read,
-              unsigned *__restrict__ mask_clear, const int parity, const int early_load) {
-    lattice_tile<S, CY>(I, pool, tab, mask_read, mask_clear, blockIdx.x, blockIdx.y, parity, early_load,
-                        threadIdx.x, threadIdx.y);
+              const unsigned *__restrict__ mask_prev, unsigned *__restrict__ mask_clear, const int parity,
+              const int early_load, const int early_cold) {
+    lattice_tile<S, CY>(I, pool, tab, mask_read, mask_prev, mask_clear, blockIdx.x, blockIdx.y, parity, early_load,
+                        early_cold, (blockIdx.x | blockIdx.y) == 0, threadIdx.x, threadIdx.y);
 }
 
 // Batched sweep over a packed tile list: tiles[t] = (instance slot,
@@ -165,7 +192,8 @@ template <class S, int CY>
 __global__ void __launch_bounds__(kTileX *kTileY / CY)
     k_lattice_batch(const Inst *__restrict__ insts, const int2 *__restrict__ tiles, S *__restrict__ pool,
                     const BeadTab tab0, const BeadTab tab1, const unsigned *__restrict__ mask_read,
-                    unsigned *__restrict__ mask_clear, const int gparity, const int early_load) {
+                    const unsigned *__restrict__ mask_prev, unsigned *__restrict__ mask_clear, const int gparity,
+                    const int early_load, const int early_cold) {
     __shared__ Inst sI;
     const int2 t = tiles[blockIdx.x];
     {
@@ -176,8 +204,8 @@ __global__ void __launch_bounds__(kTileX *kTileY / CY)
     }
     __syncthreads();
     const int parity = gparity ^ sI.par_xor;
-    lattice_tile<S, CY>(sI, pool, parity ? tab1 : tab0, mask_read, mask_clear, t.y & 0xffff, t.y >> 16, parity,
-                        early_load, threadIdx.x, threadIdx.y);
+    lattice_tile<S, CY>(sI, pool, parity ? tab1 : tab0, mask_read, mask_prev, mask_clear, t.y & 0xffff, t.y >> 16,
+                        parity, early_load, early_cold, blockIdx.x == 0, threadIdx.x, threadIdx.y);
 }
 
 // ------------------------------------------------ vectorised sweep (variant 2)
@@ -258,7 +286,7 @@ template <> struct VecWidth<__half> { static constexpr int value = 4; };
 // The NV cells x0 .. x0 + NV - 1 of row y owned by one thread.
 struct VCell {
     int x0, xm, xp;  // first cell, the cell left of it, the cell right of the last (periodic)
-    int r0, rm, rp;  // element offsets of rows y, y - 1, y + 1
+    int r0, rm, rp;  // element offsets of rows y, y - 1, y + 1 (wrapped when y is periodic)
     bool bot, top, valid;
     bool left, right;  // first lane of its segment / last lane holding cells of its row segment
 };
@@ -272,10 +300,10 @@ __device__ __forceinline__ VCell make_vcell(const Inst &I, int x0, int y, int la
     c.xm = (x0 == 0) ? I.nx - 1 : x0 - 1;
     c.xp = (x0 + NV >= I.nx) ? 0 : x0 + NV;
     c.r0 = yy * I.pitch;
-    c.rm = c.r0 - I.pitch;
-    c.rp = c.r0 + I.pitch;
-    c.bot = (yy == 0);
-    c.top = (yy == I.ny - 1);
+    c.rm = ((yy == 0) ? I.ny - 1 : yy - 1) * I.pitch;
+    c.rp = ((yy == I.ny - 1) ? 0 : yy + 1) * I.pitch;
+    c.bot = (yy == 0) && !I.periodic_y;
+    c.top = (yy == I.ny - 1) && !I.periodic_y;
     c.left = lane_in_seg == 0;
     c.right = lane_in_seg == G - 1 || x0 + NV == I.nx;
     return c;
@@ -412,8 +440,10 @@ __device__ __forceinline__ void vstore_pops(S *__restrict__ A, const Inst &I, co
 template <class S>
 __device__ __forceinline__ void lattice_tile_vec(const Inst &I, S *__restrict__ pool, const BeadTab &tab,
                                                  const unsigned *__restrict__ mask_read,
+                                                 const unsigned *__restrict__ mask_prev,
                                                  unsigned *__restrict__ mask_clear, const int bx, const int by,
-                                                 const int parity, const int early_load) {
+                                                 const int parity, const int early_load, const int early_cold,
+                                                 const bool lead) {
     using R = typename Real<S>::type;
     constexpr int NV = VecWidth<S>::value;
     const int x0 = bx * kTileX + threadIdx.x * NV;
@@ -424,7 +454,8 @@ __device__ __forceinline__ void lattice_tile_vec(const Inst &I, S *__restrict__ 
     const VCell C = make_vcell<NV>(I, x0, y, threadIdx.x);
     R g[NV][9];
     if (early_load) vload_pops<S, NV>(A, I, C, parity, g);
-    pdl_wait();
+    const bool cold = tile_cold_early(mask_prev + tile * W, W, early_cold, lead);
+    if (!cold) pdl_wait();
     pdl_trigger();
     if (threadIdx.x == 0 && threadIdx.y == 0)
         for (int w = 0; w < W; ++w) mask_clear[tile * W + w] = 0u;
@@ -432,7 +463,8 @@ __device__ __forceinline__ void lattice_tile_vec(const Inst &I, S *__restrict__ 
     if (C.valid) {
         const unsigned *m = mask_read + tile * W;
         unsigned any = 0u;
-        for (int w = 0; w < W; ++w) any |= m[w];
+        if (!cold)
+            for (int w = 0; w < W; ++w) any |= m[w];
 #pragma unroll
         for (int j = 0; j < NV; ++j) {
             R Fx, Fy, s_nu, s_e, s_eps, s_q;
@@ -446,8 +478,10 @@ __device__ __forceinline__ void lattice_tile_vec(const Inst &I, S *__restrict__ 
 template <class S>
 __global__ void __launch_bounds__(kTileX / VecWidth<S>::value * kTileY)
     k_lattice_vec(const Inst I, S *__restrict__ pool, const BeadTab tab, const unsigned *__restrict__ mask_read,
-                  unsigned *__restrict__ mask_clear, const int parity, const int early_load) {
-    lattice_tile_vec<S>(I, pool, tab, mask_read, mask_clear, blockIdx.x, blockIdx.y, parity, early_load);
+                  const unsigned *__restrict__ mask_prev, unsigned *__restrict__ mask_clear, const int parity,
+                  const int early_load, const int early_cold) {
+    lattice_tile_vec<S>(I, pool, tab, mask_read, mask_prev, mask_clear, blockIdx.x, blockIdx.y, parity, early_load,
+                        early_cold, (blockIdx.x | blockIdx.y) == 0);
 }
 
 // The column form needs more registers than the vector form: cap them at
@@ -458,7 +492,8 @@ template <class S>
 __global__ void __launch_bounds__(kTileX / VecWidth<S>::value * kTileY, BatchVecMinBlocks<S>::value)
     k_lattice_batch_vec(const Inst *__restrict__ insts, const int2 *__restrict__ tiles, S *__restrict__ pool,
                         const BeadTab tab0, const BeadTab tab1, const unsigned *__restrict__ mask_read,
-                        unsigned *__restrict__ mask_clear, const int gparity, const int early_load) {
+                        const unsigned *__restrict__ mask_prev, unsigned *__restrict__ mask_clear, const int gparity,
+                        const int early_load, const int early_cold) {
     constexpr int NT = kTileX / VecWidth<S>::value * kTileY;
     __shared__ Inst sI;
     const int2 t = tiles[blockIdx.x];
@@ -474,12 +509,13 @@ __global__ void __launch_bounds__(kTileX / VecWidth<S>::value * kTileY, BatchVec
     // on the same threads: NV cells per thread along y
     constexpr int NV = VecWidth<S>::value;
     if (sI.nx % NV == 0) {
-        lattice_tile_vec<S>(sI, pool, parity ? tab1 : tab0, mask_read, mask_clear, t.y & 0xffff, t.y >> 16,
-                            parity, early_load);
+        lattice_tile_vec<S>(sI, pool, parity ? tab1 : tab0, mask_read, mask_prev, mask_clear, t.y & 0xffff,
+                            t.y >> 16, parity, early_load, early_cold, blockIdx.x == 0);
     } else {
         const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-        lattice_tile<S, NV>(sI, pool, parity ? tab1 : tab0, mask_read, mask_clear, t.y & 0xffff, t.y >> 16,
-                            parity, early_load, tid % kTileX, tid / kTileX);
+        lattice_tile<S, NV>(sI, pool, parity ? tab1 : tab0, mask_read, mask_prev, mask_clear, t.y & 0xffff,
+                            t.y >> 16, parity, early_load, early_cold, blockIdx.x == 0, tid % kTileX,
+                            tid / kTileX);
     }
 }
 
@@ -545,6 +581,58 @@ __global__ void k_fields(const Inst I, const S *__restrict__ pool, const BeadTab
     ux[c] = (jx + 0.5 * fx) / r;
     uy[c] = (jy + 0.5 * fy) / r;
     rho[c] = r;
+}
+
+// eps_v of each bead (Sec. 3.2): one CTA per bead over its support box,
+// FP64; out[2 q] = sum phi_q |u - V_q|^2, out[2 q + 1] = sum phi_q.
+constexpr int kFlowThreads = 256;
+template <class S>
+__global__ void __launch_bounds__(kFlowThreads)
+    k_internal_flow(const Inst I, const S *__restrict__ pool, const BeadTab tab, int parity, double *__restrict__ out) {
+    __shared__ double sh[2][kFlowThreads / 32];
+    const int q = I.bead_off + blockIdx.x;
+    const double Rx = tab.Rx[q], Ry = tab.Ry[q], Vx = tab.Vx[q], Vy = tab.Vy[q];
+    const Box bx = support_box(I, Rx, Ry);
+    double num = 0.0, den = 0.0;
+    for (int c = threadIdx.x; c < bx.w * bx.h; c += blockDim.x) {
+        const int cj = c / bx.w, ci = c - cj * bx.w;
+        int i = bx.i0 + ci, j = bx.j0 + cj;
+        i = (i >= I.nx) ? i - I.nx : i;
+        j = (j >= I.ny) ? j - I.ny : j;
+        const double ph = phi_f64(I, i + 0.5, j + 0.5, Rx, Ry);
+        if (ph == 0.0) continue;
+        double g[9];
+        load_pops<S, double>(pool + I.pop_off, I, make_cell(I, i, j), parity, g);
+        double dr = 0.0;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) dr += g[k];
+        const double r = 1.0 + dr;
+        const double jx = g[1] - g[3] + g[5] - g[6] - g[7] + g[8];
+        const double jy = g[2] - g[4] + g[5] + g[6] - g[7] - g[8];
+        double fx, fy;
+        overlay_f64(I, tab, nullptr, i, j, fx, fy);
+        const double ex = (jx + 0.5 * fx) / r - Vx, ey = (jy + 0.5 * fy) / r - Vy;
+        num += ph * (ex * ex + ey * ey);
+        den += ph;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        num += __shfl_down_sync(0xffffffffu, num, o);
+        den += __shfl_down_sync(0xffffffffu, den, o);
+    }
+    if (lane_id() == 0) {
+        sh[0][threadIdx.x >> 5] = num;
+        sh[1][threadIdx.x >> 5] = den;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < kFlowThreads / 32; ++w) {
+            a += sh[0][w];
+            b += sh[1][w];
+        }
+        out[2 * blockIdx.x] = a;
+        out[2 * blockIdx.x + 1] = b;
+    }
 }
 
 template <class S>
@@ -639,114 +727,82 @@ __global__ void __launch_bounds__(kDiagThreads)
 }  // namespace
 
 // ---------------------------------------------------------------- launchers
-template <class S, int CY>
-static cudaError_t lattice_t(const Inst &I, void *pool, BeadTab tab, const unsigned *mask_read,
-                             unsigned *mask_clear, int parity, int after_beads, cudaStream_t st) {
+static cudaLaunchConfig_t sweep_config(dim3 grid, dim3 block, int after_beads, cudaStream_t st,
+                                       cudaLaunchAttribute *attr) {
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(I.ntx, I.nty);
-    cfg.blockDim = dim3(kTileX, kTileY / CY);
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
     cfg.stream = st;
-    cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = after_beads ? 1 : 0;
-    return cudaLaunchKernelEx(&cfg, k_lattice<S, CY>, I, (S *)pool, tab, mask_read, mask_clear, parity,
-                              after_beads);
+    return cfg;
 }
 
 template <class S>
-static cudaError_t lattice_vec_t(const Inst &I, void *pool, BeadTab tab, const unsigned *mask_read,
-                                 unsigned *mask_clear, int parity, int after_beads, cudaStream_t st) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(I.ntx, I.nty);
-    cfg.blockDim = dim3(kTileX / VecWidth<S>::value, kTileY);
-    cfg.stream = st;
+static cudaError_t lattice_v(int variant, const Inst &I, void *pool, BeadTab tab, const SweepMasks &mk, int parity,
+                             int after_beads, cudaStream_t st) {
     cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = after_beads ? 1 : 0;
-    return cudaLaunchKernelEx(&cfg, k_lattice_vec<S>, I, (S *)pool, tab, mask_read, mask_clear, parity,
-                              after_beads);
-}
-
-template <class S>
-static cudaError_t lattice_v(int variant, const Inst &I, void *pool, BeadTab tab, const unsigned *mask_read,
-                             unsigned *mask_clear, int parity, int after_beads, cudaStream_t st) {
-    if (variant == 2 && I.nx % VecWidth<S>::value == 0)
-        return lattice_vec_t<S>(I, pool, tab, mask_read, mask_clear, parity, after_beads, st);
-    if (variant == 1) return lattice_t<S, 2>(I, pool, tab, mask_read, mask_clear, parity, after_beads, st);
-    return lattice_t<S, 1>(I, pool, tab, mask_read, mask_clear, parity, after_beads, st);
+    const dim3 grid(I.ntx, I.nty);
+    const int ec = after_beads ? mk.early_cold : 0;
+    if (variant == 2 && I.nx % VecWidth<S>::value == 0) {
+        const cudaLaunchConfig_t cfg = sweep_config(grid, dim3(kTileX / VecWidth<S>::value, kTileY), after_beads,
+                                                    st, attr);
+        return cudaLaunchKernelEx(&cfg, k_lattice_vec<S>, I, (S *)pool, tab, mk.read, mk.prev, mk.clear, parity,
+                                  after_beads, ec);
+    }
+    if (variant == 1) {
+        const cudaLaunchConfig_t cfg = sweep_config(grid, dim3(kTileX, kTileY / 2), after_beads, st, attr);
+        return cudaLaunchKernelEx(&cfg, k_lattice<S, 2>, I, (S *)pool, tab, mk.read, mk.prev, mk.clear, parity,
+                                  after_beads, ec);
+    }
+    const cudaLaunchConfig_t cfg = sweep_config(grid, dim3(kTileX, kTileY), after_beads, st, attr);
+    return cudaLaunchKernelEx(&cfg, k_lattice<S, 1>, I, (S *)pool, tab, mk.read, mk.prev, mk.clear, parity,
+                              after_beads, ec);
 }
 
 cudaError_t launch_lattice(int precision, const Inst *, const Inst &inst_h, void *pool, BeadTab tab,
-                           const unsigned *mask_read, unsigned *mask_clear, int parity, int after_beads,
-                           int variant, cudaStream_t st) {
+                           const SweepMasks &masks, int parity, int after_beads, int variant, cudaStream_t st) {
     switch (precision) {
-        case 0: return lattice_v<double>(variant, inst_h, pool, tab, mask_read, mask_clear, parity, after_beads, st);
-        case 1: return lattice_v<float>(variant, inst_h, pool, tab, mask_read, mask_clear, parity, after_beads, st);
-        case 2: return lattice_v<__half>(variant, inst_h, pool, tab, mask_read, mask_clear, parity, after_beads, st);
+        case 0: return lattice_v<double>(variant, inst_h, pool, tab, masks, parity, after_beads, st);
+        case 1: return lattice_v<float>(variant, inst_h, pool, tab, masks, parity, after_beads, st);
+        case 2: return lattice_v<__half>(variant, inst_h, pool, tab, masks, parity, after_beads, st);
     }
     return cudaErrorInvalidValue;
 }
 
-template <class S, int CY>
-static cudaError_t lattice_batch_t(const Inst *insts, const int2 *tiles, int ntiles, void *pool, BeadTab tab0,
-                                   BeadTab tab1, const unsigned *mask_read, unsigned *mask_clear, int gparity,
-                                   int after_beads, cudaStream_t st) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(ntiles);
-    cfg.blockDim = dim3(kTileX, kTileY / CY);
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = after_beads ? 1 : 0;
-    return cudaLaunchKernelEx(&cfg, k_lattice_batch<S, CY>, insts, tiles, (S *)pool, tab0, tab1, mask_read,
-                              mask_clear, gparity, after_beads);
-}
-
-template <class S>
-static cudaError_t lattice_batch_vec_t(const Inst *insts, const int2 *tiles, int ntiles, void *pool, BeadTab tab0,
-                                       BeadTab tab1, const unsigned *mask_read, unsigned *mask_clear, int gparity,
-                                       int after_beads, cudaStream_t st) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(ntiles);
-    cfg.blockDim = dim3(kTileX / VecWidth<S>::value, kTileY);
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = after_beads ? 1 : 0;
-    return cudaLaunchKernelEx(&cfg, k_lattice_batch_vec<S>, insts, tiles, (S *)pool, tab0, tab1, mask_read,
-                              mask_clear, gparity, after_beads);
-}
-
 template <class S>
 static cudaError_t lattice_batch_v(int variant, const Inst *insts, const int2 *tiles, int ntiles, void *pool,
-                                   BeadTab tab0, BeadTab tab1, const unsigned *mask_read, unsigned *mask_clear,
-                                   int gparity, int after_beads, cudaStream_t st) {
-    if (variant == 2)
-        return lattice_batch_vec_t<S>(insts, tiles, ntiles, pool, tab0, tab1, mask_read, mask_clear, gparity,
-                                      after_beads, st);
-    if (variant == 1)
-        return lattice_batch_t<S, 2>(insts, tiles, ntiles, pool, tab0, tab1, mask_read, mask_clear, gparity,
-                                     after_beads, st);
-    return lattice_batch_t<S, 1>(insts, tiles, ntiles, pool, tab0, tab1, mask_read, mask_clear, gparity,
-                                 after_beads, st);
+                                   BeadTab tab0, BeadTab tab1, const SweepMasks &mk, int gparity, int after_beads,
+                                   cudaStream_t st) {
+    cudaLaunchAttribute attr[1];
+    const dim3 grid(ntiles);
+    const int ec = after_beads ? mk.early_cold : 0;
+    if (variant == 2) {
+        const cudaLaunchConfig_t cfg = sweep_config(grid, dim3(kTileX / VecWidth<S>::value, kTileY), after_beads,
+                                                    st, attr);
+        return cudaLaunchKernelEx(&cfg, k_lattice_batch_vec<S>, insts, tiles, (S *)pool, tab0, tab1, mk.read,
+                                  mk.prev, mk.clear, gparity, after_beads, ec);
+    }
+    if (variant == 1) {
+        const cudaLaunchConfig_t cfg = sweep_config(grid, dim3(kTileX, kTileY / 2), after_beads, st, attr);
+        return cudaLaunchKernelEx(&cfg, k_lattice_batch<S, 2>, insts, tiles, (S *)pool, tab0, tab1, mk.read,
+                                  mk.prev, mk.clear, gparity, after_beads, ec);
+    }
+    const cudaLaunchConfig_t cfg = sweep_config(grid, dim3(kTileX, kTileY), after_beads, st, attr);
+    return cudaLaunchKernelEx(&cfg, k_lattice_batch<S, 1>, insts, tiles, (S *)pool, tab0, tab1, mk.read, mk.prev,
+                              mk.clear, gparity, after_beads, ec);
 }
 
 cudaError_t launch_lattice_batch(int precision, const Inst *insts, const int2 *tiles, int ntiles, void *pool,
-                                 BeadTab tab0, BeadTab tab1, const unsigned *mask_read, unsigned *mask_clear,
-                                 int gparity, int after_beads, int variant, cudaStream_t st) {
+                                 BeadTab tab0, BeadTab tab1, const SweepMasks &masks, int gparity, int after_beads,
+                                 int variant, cudaStream_t st) {
     if (ntiles <= 0) return cudaSuccess;
     switch (precision) {
-        case 0: return lattice_batch_v<double>(variant, insts, tiles, ntiles, pool, tab0, tab1, mask_read, mask_clear, gparity, after_beads, st);
-        case 1: return lattice_batch_v<float>(variant, insts, tiles, ntiles, pool, tab0, tab1, mask_read, mask_clear, gparity, after_beads, st);
-        case 2: return lattice_batch_v<__half>(variant, insts, tiles, ntiles, pool, tab0, tab1, mask_read, mask_clear, gparity, after_beads, st);
+        case 0: return lattice_batch_v<double>(variant, insts, tiles, ntiles, pool, tab0, tab1, masks, gparity, after_beads, st);
+        case 1: return lattice_batch_v<float>(variant, insts, tiles, ntiles, pool, tab0, tab1, masks, gparity, after_beads, st);
+        case 2: return lattice_batch_v<__half>(variant, insts, tiles, ntiles, pool, tab0, tab1, masks, gparity, after_beads, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -770,6 +826,13 @@ cudaError_t launch_fields(int precision, const Inst *, const Inst &I, const void
                           const unsigned *mask, int parity, double *ux, double *uy, double *rho, cudaStream_t st) {
     FPD_DISPATCH(precision, (k_fields<S><<<row_grid(I, 128), 128, 0, st>>>(I, (const S *)pool, tab, mask, parity,
                                                                               ux, uy, rho)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_internal_flow(int precision, const Inst &I, const void *pool, BeadTab tab, int parity,
+                                 double *out, cudaStream_t st) {
+    if (I.nb <= 0) return cudaSuccess;
+    FPD_DISPATCH(precision, (k_internal_flow<S><<<I.nb, kFlowThreads, 0, st>>>(I, (const S *)pool, tab, parity, out)));
     return cudaGetLastError();
 }
 

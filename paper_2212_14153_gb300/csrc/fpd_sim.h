@@ -19,7 +19,7 @@ struct fpd_sim {
     double *tabmem = nullptr;       // two bead tables
     fpd::BeadTab tab[2]{};
     unsigned *counters = nullptr;   // one per instance (bead-phase last-block)
-    unsigned *masks[2] = {nullptr, nullptr};  // per-tile bead masks, by step parity
+    unsigned *masks[fpd::kMaskBufs] = {};  // per-tile bead masks, in rotation by step (t % kMaskBufs)
     double *scratch = nullptr;      // fields / populations / diagnostics
     size_t scratch_bytes = 0;
     cudaStream_t stream = nullptr;
@@ -37,9 +37,11 @@ struct fpd_sim {
     double launches[2] = {0, 0};
     // captured step chunks, one per starting parity (see fpd_step)
     bool use_graphs = true;
+    double *host_stage = nullptr;  // pinned staging for bead reads (7 nb doubles)
+    bool early_cold = true;  // unmarked tiles update before the bead phase ends (same results)
     int variant = 0;  // lattice sweep variant (see launch_lattice)
     cudaStream_t cap_stream = nullptr;
-    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    cudaGraphExec_t graph[fpd::kMaskBufs] = {};  // captured step chunks, by first step % kMaskBufs
 };
 
 namespace fpd {

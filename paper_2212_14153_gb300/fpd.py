@@ -40,6 +40,8 @@ class fpd_params(ctypes.Structure):
         ("s_e", ctypes.c_double), ("s_eps", ctypes.c_double), ("s_q", ctypes.c_double),
         ("centre_xy", _DP), ("theta0", _DP), ("bead_xy", _DP),
         ("sandwich_zl", ctypes.c_double), ("sandwich_zr", ctypes.c_double),
+        ("periodic_y", ctypes.c_int32), ("bead_force_x", ctypes.c_double),
+        ("bead_force_y", ctypes.c_double),
     ]
 
 
@@ -60,6 +62,8 @@ SIGNATURES = {
     "fpd_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
     "fpd_sync": (ctypes.c_int, [ctypes.c_void_p]),
     "fpd_read_fields": (ctypes.c_int, [ctypes.c_void_p, _DP, _DP, _DP]),
+    "fpd_internal_flow": (ctypes.c_int, [ctypes.c_void_p, _DP]),
+    "fpd_batch_internal_flow": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, _DP]),
     "fpd_read_beads": (ctypes.c_int, [ctypes.c_void_p, _DP, _DP, _DP, _DP]),
     "fpd_read_populations": (ctypes.c_int, [ctypes.c_void_p, _DP]),
     "fpd_write_populations": (ctypes.c_int, [ctypes.c_void_p, _DP]),
@@ -153,6 +157,14 @@ def fpd_read_fields(h, ux, uy, rho) -> None:
     _check(load_library().fpd_read_fields(h, _ptr(ux), _ptr(uy), _ptr(rho)), h)
 
 
+def fpd_internal_flow(h, eps) -> None:
+    _check(load_library().fpd_internal_flow(h, _ptr(eps)), h)
+
+
+def fpd_batch_internal_flow(b, slot: int, eps) -> None:
+    _bcheck(load_library().fpd_batch_internal_flow(b, int(slot), _ptr(eps)), b)
+
+
 def fpd_read_beads(h, pos, vel, force, support=None) -> None:
     _check(load_library().fpd_read_beads(h, _ptr(pos), _ptr(vel), _ptr(force), _ptr(support)), h)
 
@@ -225,7 +237,8 @@ def params_from_config(cfg: dict) -> tuple[fpd_params, list]:
                   k_ev="k_ev", phi_cut="phi_cut", gx="body_force_x", gy="body_force_y",
                   precision="precision", collision="collision", init_couette="init_couette",
                   s_e="s_e", s_eps="s_eps", s_q="s_q", sandwich_zl="sandwich_zl",
-                  sandwich_zr="sandwich_zr")
+                  sandwich_zr="sandwich_zr", periodic_y="periodic_y", bead_fx="bead_force_x",
+                  bead_fy="bead_force_y")
     for k, field in simple.items():
         if k in cfg:
             setattr(p, field, cfg[k])
@@ -286,6 +299,12 @@ class Simulation:
         fpd_read_beads(self.h, R, V, F, S)
         k = self.nb
         return R[:k], V[:k], F[:k], S[:k]
+
+    def internal_flow(self) -> np.ndarray:
+        """eps_v of every bead (Sec. 3.2)."""
+        out = np.zeros(max(self.nb, 1))
+        fpd_internal_flow(self.h, out)
+        return out[:self.nb]
 
     def populations(self):
         f = np.zeros((9, self.ny, self.nx))
@@ -459,6 +478,13 @@ class Batch:
         f = np.zeros((9, i["ny"], i["nx"]))
         fpd_batch_read_populations(self.h, slot, f)
         return f
+
+    def internal_flow(self, slot: int) -> np.ndarray:
+        """eps_v of every bead of a slot (Sec. 3.2)."""
+        n = self.info(slot)["beads"]
+        out = np.zeros(max(n, 1))
+        fpd_batch_internal_flow(self.h, slot, out)
+        return out[:n]
 
     def remove(self, slot: int):
         fpd_batch_remove(self.h, slot)

@@ -15,6 +15,15 @@ grows toward a critical Re_ps or confinement C:
   flex-re     fairly flexible fiber (K = 3.3e-5), C = 0.5, Re_ps swept (Fig. 8a: beta = 0.3)
   flex-c      fairly flexible fiber, Re_ps = 1.5, C swept (Fig. 8b: beta = 0.6)
 
+and the driven-particle benchmark of Sec. 3.2 (one bead in a box periodic in
+x and y, H = 10 d, pushed by a constant force F_0 against a uniform counter
+force on the fluid):
+
+  internal-flow  eps_v / V_0^2 against r_eta (r_xi = 0.01, Fig. 3d), against
+              r_xi (r_eta = 100, Fig. 3e) and against Re_p; with each point the
+              drag F_0 / (eta V_0) against Hasimoto's periodic array of rigid
+              discs and the disc radius that reproduces it
+
 Run: python -m paper_2212_14153_gb300.studies <study> [--a A] [--precision P]
 """
 from __future__ import annotations
@@ -98,9 +107,75 @@ def sweep(name: str, a: float = 2.0, precision: int = 1, values=None) -> dict:
     return out
 
 
+def hasimoto_drag(a: float, L: float) -> float:
+    """F / (eta V) of a square array (period L) of rigid discs of radius a in
+    Stokes flow (Hasimoto 1959), to third order in the area fraction c."""
+    c = math.pi * a * a / (L * L)
+    return 4 * math.pi / (-0.5 * math.log(c) - 0.738 + c - 0.887 * c * c + 2.039 * c ** 3)
+
+
+def hasimoto_radius(k: float, L: float) -> float:
+    """Disc radius whose periodic-array drag F / (eta V) equals k (bisection)."""
+    lo, hi = 1e-3 * L, 0.45 * L
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if hasimoto_drag(mid, L) < k:
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)
+
+
+def driven_case(a: float, r_eta: float, r_xi: float, Re_p: float, h_over_d: float = 10.0,
+                nu: float = 1.0 / 6.0) -> dict:
+    """One bead of radius a in a periodic box of side h_over_d * d, driven
+    along x by F_0 chosen from Hasimoto's drag for a target Re_p = V_0 d / nu;
+    the fluid carries the counter force -F_0 / L^2 (Sec. 3.2)."""
+    d = 2.0 * a
+    L = int(round(h_over_d * d))
+    V0 = Re_p * nu / d
+    F0 = hasimoto_drag(a, L) * nu * V0
+    return dict(nx=L, ny=L, u_bottom=0.0, u_top=0.0, nu_f=nu, re=1.0, visc_ratio=r_eta, xi=r_xi * d, a=a,
+                n_beads=1, n_fibers=1, k_s=-1.0, k_b=0.0, stiffness_K=0.0, k_ev=-1.0, phi_cut=8.0,
+                gx=-F0 / (L * L), gy=0.0, collision=0, s_e=1.64, s_eps=1.54, s_q=1.9, init_couette=0,
+                periodic_y=1, bead_fx=F0, bead_fy=0.0, centres=[[L / 2.0, L / 2.0]], theta0=[0.0])
+
+
+INTERNAL_FLOW = (
+    [("r_eta", r, 0.01, 0.1) for r in (1.0, 2.0, 5.0, 10.0, 20.0, 50.0, 100.0, 200.0)]
+    + [("r_xi", 100.0, x, 0.1) for x in (0.01, 0.03, 0.0625, 0.125, 0.25)]
+    + [("Re_p", 100.0, 0.0625, r) for r in (0.1, 1.0, 3.0)]
+)
+
+
+def internal_flow(a: float = 8.0, precision: int = 1, points=INTERNAL_FLOW, viscous_times: float = 3.0) -> dict:
+    from . import fpd
+    cfgs = [driven_case(a, r_eta, r_xi, Re_p) for _, r_eta, r_xi, Re_p in points]
+    nu, L, d = cfgs[0]["nu_f"], cfgs[0]["nx"], 2.0 * a
+    steps = int(viscous_times * L * L / nu)
+    cells = sum(c["nx"] * c["ny"] for c in cfgs)
+    es = {0: 8, 1: 4, 2: 2}[precision]
+    b = fpd.Batch(precision, len(cfgs), 9 * es * (cells + 64 * L * len(cfgs)) + 4096 * len(cfgs), len(cfgs))
+    slots = [b.add(dict(c, precision=precision), steps) for c in cfgs]
+    b.run(int(0.9 * steps))
+    V_early = [b.beads(s)[1][0, 0] for s in slots]
+    while b.run(steps):
+        pass
+    rows = []
+    for (group, r_eta, r_xi, Re_t), c, s, ve in zip(points, cfgs, slots, V_early):
+        V = b.beads(s)[1][0, 0]
+        eps = float(b.internal_flow(s)[0])
+        k = c["bead_fx"] / (nu * V)
+        rows.append(dict(group=group, r_eta=r_eta, r_xi=r_xi, Re_p=V * d / nu, eps_rel=eps / V ** 2,
+                         drag=k, drag_over_hasimoto=k / hasimoto_drag(a, L),
+                         a_eff_over_a=hasimoto_radius(k, L) / a, V_drift=abs(V / ve - 1)))
+    b.close()
+    return dict(study="internal-flow", a=a, L=L, nu=nu, steps=steps, rows=rows)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("study", choices=["resolution"] + sorted(SWEEPS))
+    ap.add_argument("study", choices=["resolution", "internal-flow"] + sorted(SWEEPS))
     ap.add_argument("--a", type=float, default=2.0, help="bead radius in lattice units")
     ap.add_argument("--precision", type=int, default=1, choices=[0, 1, 2])
     args = ap.parse_args(argv)
@@ -109,8 +184,12 @@ def main(argv=None):
         raise SystemExit("the studies run on the CUDA library: no CUDA device")
     from . import build
     build.build()
-    out = resolution(precision=args.precision) if args.study == "resolution" else \
-        sweep(args.study, a=args.a, precision=args.precision)
+    if args.study == "resolution":
+        out = resolution(precision=args.precision)
+    elif args.study == "internal-flow":
+        out = internal_flow(a=args.a if args.a != 2.0 else 8.0, precision=args.precision)
+    else:
+        out = sweep(args.study, a=args.a, precision=args.precision)
     print(json.dumps(out, indent=1, default=float))
 
 

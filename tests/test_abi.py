@@ -39,7 +39,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 def test_version_and_defaults(lib):
     from paper_2212_14153_gb300 import fpd
-    assert fpd.fpd_version() == 1
+    assert fpd.fpd_version() == 2
     assert fpd.fpd_sweep_variants() == 3
     p = fpd.fpd_default_params()
     assert (p.nx, p.ny, p.u_bottom, p.u_top, p.visc_ratio, p.phi_cut) == (80, 40, -0.01, 0.01, 50.0, 8.0)
@@ -53,6 +53,9 @@ def test_version_and_defaults(lib):
     ("n_beads", 300, "at most"),
     ("visc_ratio", -1.0, "visc_ratio"),
     ("xi", 0.0, "xi"),
+    ("periodic_y", 2, "periodic_y"),
+    ("bead_force_x", float("nan"), "bead_force"),
+    ("sandwich_zl", 5.0, "sandwich"),      # with periodic_y below
 ])
 def test_invalid_parameters_rejected_before_any_device_call(lib, field, value, needle):
     from paper_2212_14153_gb300 import fpd
@@ -63,6 +66,8 @@ def test_invalid_parameters_rejected_before_any_device_call(lib, field, value, n
     p.centre_xy = cen.ctypes.data_as(fpd._DP)
     p.theta0 = th.ctypes.data_as(fpd._DP)
     setattr(p, field, value)
+    if field == "sandwich_zl":
+        p.sandwich_zr, p.periodic_y = 10.0, 1
     with pytest.raises(fpd.FpdError) as e:
         fpd.fpd_create(p, None)
     assert e.value.code == fpd.FPD_EINVAL

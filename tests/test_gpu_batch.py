@@ -154,3 +154,23 @@ def test_batched_sweep_instances_run_and_conserve_mass(fpd):
         R = b.beads(s)[0]
         assert np.all(np.isfinite(R))
     b.close()
+
+
+def test_periodic_driven_instances_in_a_batch(fpd):
+    # periodic boxes with a driven bead next to walled Couette cells: each
+    # instance gives exactly what it gives alone
+    cases = [
+        dict(nx=40, ny=40, u_bottom=0.0, u_top=0.0, nu_f=1.0 / 6.0, visc_ratio=100.0, xi=0.5, a=2.0,
+             n_beads=1, n_fibers=1, init_couette=0, periodic_y=1, bead_fx=2e-5, gx=-2e-5 / 1600,
+             centres=[[39.5, 0.2]], theta0=[0.0], precision=p)
+        for p in (0, 1)
+    ]
+    for p in (0, 1):
+        mixed = [cases[p], _cases(p)[0]]
+        b = fpd.Batch(p, max_slots=4, pool_bytes=32 << 20, max_beads=64)
+        slots = [b.add(c, 120) for c in mixed]
+        while b.run(1000):
+            pass
+        for c, s in zip(mixed, slots):
+            _same((b.populations(s), b.beads(s)), _alone(fpd, c, 120))
+        b.close()

@@ -383,3 +383,102 @@ def test_sandwich_couette_parity():
     g32 = gpu_sim(dict(cfg, precision=1))
     g32.step(3000)
     assert rel_l2(g32.fields()[0], g.fields()[0]) < 1e-4
+
+
+# ------------------------------------------------------------ periodic box, driven bead (Sec. 3.2)
+def driven_cfg(L, a, xi, r_eta, centres, F0=(2e-5, 0.0), n_beads=1, precision=0, **kw):
+    nf = len(centres)
+    nb = n_beads * nf
+    cfg = dict(nx=L, ny=L, u_bottom=0.0, u_top=0.0, nu_f=1.0 / 6.0, re=1.0, visc_ratio=r_eta, xi=xi, a=a,
+               n_beads=n_beads, n_fibers=nf, k_s=-1.0, k_b=0.0, stiffness_K=0.0, k_ev=-1.0, phi_cut=8.0,
+               collision=0, s_e=1.64, s_eps=1.54, s_q=1.9, init_couette=0, periodic_y=1,
+               bead_fx=F0[0], bead_fy=F0[1], gx=-F0[0] * nb / (L * L), gy=-F0[1] * nb / (L * L),
+               centres=centres, theta0=[0.0] * nf, precision=precision)
+    cfg.update(kw)
+    return cfg
+
+
+@pytest.mark.parametrize("centre", [[20.3, 20.6], [39.2, 39.7], [0.4, 17.0], [13.0, 0.1]])
+def test_driven_bead_fp64_parity_across_periodic_edges(centre):
+    # F_0 large enough (V ~ 1.5e-2, Re_p ~ 0.4) that the flow stands well
+    # above the rounding floor of the oracle's plain-f storage: ulp(f) ~ 6e-17
+    # per population and step gives ~1e-13 of |u| here, ~1e-12 at F_0 / 10
+    cfg = driven_cfg(40, 2.0, 0.5, 100.0, [centre], F0=(2e-2, -1.3e-2))
+    g, o = run_both(cfg, 301)
+    compare_f64(g, o)
+    eg, eo = g.internal_flow(), o.internal_flow()
+    assert abs(eg[0] / eo[0] - 1) < 1e-9, (eg, eo)
+
+
+def test_periodic_fibers_excluded_volume_across_y_edge_fp64_parity():
+    # two 4-bead fibers, one along the bottom edge and one along the top edge
+    # one bead diameter apart through the periodic boundary: the excluded
+    # volume acts across the edge; each fiber is pushed by F_0
+    cfg = driven_cfg(48, 2.0, 0.5, 50.0, [[20.0, 1.5], [20.0, 46.0]], F0=(1e-3, 3e-4), n_beads=4,
+                     stiffness_K=0.0, k_b=0.002, k_s=0.05, k_ev=0.01)
+    o = orc_sim(cfg)
+    g = gpu_sim(cfg)
+    # beads 3.5 apart through the edge: fiber 1 is pushed up, fiber 2 down
+    F = o.beads()[2]
+    assert F[:4, 1].min() > 1e-3 and F[4:, 1].max() < -1e-3
+    assert np.abs(g.beads()[2] - F).max() < 1e-12
+    R0 = g.beads()[0]
+    g.step(250)
+    o.step(250)
+    compare_f64(g, o)
+    assert np.abs(g.beads()[0] - R0).max() > 1e-3
+
+
+@pytest.mark.parametrize("precision,tol", [(1, 1e-5), (2, 2e-2)])
+def test_driven_bead_reduced_precision(precision, tol):
+    base = driven_cfg(40, 2.0, 0.5, 100.0, [[39.6, 0.3]], F0=(2e-3, 0.0))
+    ref = gpu_sim(base)
+    ref.step(2000)
+    Vr = ref.beads()[1][0]
+    for variant in (0, 1, 2):
+        s = gpu_sim(dict(base, precision=precision))
+        s.set_tuning(variant)
+        s.step(2000)
+        V = s.beads()[1][0]
+        e = float(np.abs(V - Vr).max() / np.abs(Vr).max())
+        print(f"driven bead, precision {precision}, variant {variant}: V rel err {e:.2e}")
+        assert e < tol
+        assert abs(s.internal_flow()[0] / ref.internal_flow()[0] - 1) < 50 * tol
+
+
+def test_periodic_shear_wave_on_gpu():
+    # u_x = U sin(k y) over the periodic y direction decays as exp(-nu k^2 t)
+    L, nu = 64, 0.1
+    k = 2 * math.pi / L
+    cfg = dict(wl.couette_only(8, L, u=0.0, nu=nu, init_couette=0), periodic_y=1)
+    y = np.arange(L) + 0.5
+    fy = np.stack([oracle.feq(1.0, ux, 0.0) for ux in 1e-3 * np.sin(k * y)], axis=1)
+    f0 = np.repeat(fy[:, :, None], 8, axis=2).copy()
+    for p in (0, 1):
+        s = gpu_sim(dict(cfg, precision=p))
+        s.set_populations(f0)
+        s.step(200)
+        a1 = 2.0 / L * float(np.sum(s.fields()[0][:, 0] * np.sin(k * y)))
+        s.step(2000)
+        a2 = 2.0 / L * float(np.sum(s.fields()[0][:, 0] * np.sin(k * y)))
+        rate = math.log(a1 / a2) / 2000
+        assert abs(rate / (nu * k * k) - 1) < 2e-3
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_early_cold_tiles_give_identical_results(precision, monkeypatch):
+    # updating unmarked tiles before the bead phase ends changes only the
+    # order of independent work: bit-identical to waiting in every tile
+    rng = np.random.default_rng(91)
+    cfg = wl.random_fiber(rng, 160, 64, n_beads=6, a=2.0, xi=1.0, n_fibers=2, precision=precision)
+    a = gpu_sim(cfg)
+    monkeypatch.setenv("FPD_NO_EARLY_COLD", "1")
+    b = gpu_sim(cfg)
+    monkeypatch.delenv("FPD_NO_EARLY_COLD")
+    for s in (a, b):
+        s.step(3)
+        s.step(64)      # graph chunks
+        s.step(5)
+    assert np.array_equal(a.populations(), b.populations())
+    for x, y in zip(a.beads(), b.beads()):
+        assert np.array_equal(x, y)

@@ -102,3 +102,16 @@ def test_tumbling_case_geometry():
     assert cfg["re"] == 6.0 and cfg["xi"] == 0.125 * d      # Re = 4 Re_ps, xi = r_xi d
     assert g == 2 * 0.02 / 200
     assert cfg["centres"] == [[50.0, 100.0]]
+
+
+def test_hasimoto_inversion_and_driven_case():
+    from paper_2212_14153_gb300 import studies
+    for a, L in ((2.0, 40.0), (8.0, 160.0), (5.0, 30.0)):
+        assert abs(studies.hasimoto_radius(studies.hasimoto_drag(a, L), L) / a - 1) < 1e-9
+    # dilute limit: 4 pi / (ln(1/sqrt(c)) - 0.738)
+    c = math.pi * 1e-4
+    assert abs(studies.hasimoto_drag(1.0, 100.0) / (4 * math.pi / (-0.5 * math.log(c) - 0.738)) - 1) < 1e-3
+    cfg = studies.driven_case(8.0, 100.0, 0.0625, 0.1)
+    L = cfg["nx"]
+    assert L == cfg["ny"] == 160 and cfg["periodic_y"] == 1 and cfg["xi"] == 1.0
+    assert cfg["gx"] * L * L == pytest.approx(-cfg["bead_fx"], rel=1e-15)   # no net force on the box
