@@ -121,6 +121,22 @@ void fpd_default_params(fpd_params *p);
  * parameter, message names it), FPD_ENOMEM, FPD_ECUDA. */
 int fpd_create(const fpd_params *p, void *stream, fpd_sim **out);
 
+/* Device bytes of the state of one instance with parameters p (populations,
+ * both bead tables, tile masks, a counter and the instance record, each part
+ * 256-byte aligned): the workspace fpd_create_ex needs.  FPD_EINVAL for
+ * invalid parameters (as fpd_create). */
+int fpd_workspace_bytes(const fpd_params *p, uint64_t *bytes);
+
+/* As fpd_create, with the state placed in caller-owned device memory
+ * `workspace` of workspace_bytes bytes (at least fpd_workspace_bytes, at a
+ * 256-byte aligned address; e.g. the data of a torch tensor), which the
+ * caller keeps valid until fpd_destroy and frees afterwards: the library
+ * never frees it.  Buffers for reads (fpd_read_*, fpd_internal_flow) and
+ * host staging are still allocated by the library on first use.  The paper
+ * has no counterpart: this serves applications that own device memory.
+ * FPD_EINVAL for a NULL or short or misaligned workspace. */
+int fpd_create_ex(const fpd_params *p, void *stream, void *workspace, uint64_t workspace_bytes, fpd_sim **out);
+
 /* Enqueue n_steps >= 0 time steps (Sec. 2.3 items (1)-(3)).  Asynchronous:
  * returns launch errors only. */
 int fpd_step(fpd_sim *s, int64_t n_steps);
@@ -158,6 +174,22 @@ int fpd_write_populations(fpd_sim *s, const double *f);
  * force), out[3] = completed steps.  FP64 reduction on the device.  Returns
  * FPD_ENAN if the state holds a non-finite value.  Synchronises. */
 int fpd_diag(fpd_sim *s, double out[4]);
+
+/* Checkpoint / resume (the paper has no counterpart: long runs, Sec. 4,
+ * survive restarts).  fpd_save writes the whole device state of the handle
+ * to the file `path` (created or truncated): the stored populations in their
+ * storage precision, both bead tables, the tile masks, the step count and
+ * the derived per-instance constants, behind a header with a format tag and
+ * the ABI version.  fpd_load reads such a file into a handle created with
+ * the same parameters (same lattice, precision, beads and derived
+ * constants; the stream may differ) and replaces its state: the run then
+ * continues exactly as the saved one would have, bit for bit.  Both
+ * synchronise.  FPD_EINVAL for a NULL argument, a file that cannot be
+ * opened, read or written, a file that is not a checkpoint of this format
+ * or ABI version, or one written with other parameters (the handle is then
+ * unchanged). */
+int fpd_save(fpd_sim *s, const char *path);
+int fpd_load(fpd_sim *s, const char *path);
 
 /* Same result as fpd_diag, computed without allocating any device memory.
  * The paper has no counterpart: this is a library service.  fpd_diag keeps

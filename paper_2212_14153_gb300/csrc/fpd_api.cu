@@ -225,12 +225,12 @@ void drop_graphs(fpd_sim *s) {
 
 void free_all(fpd_sim *s) {
     if (!s) return;
-    cudaFree(s->pool);
-    cudaFree(s->tabmem);
-    cudaFree(s->counters);
-    cudaFree(s->masks[0]);
+    if (s->owns_state) cudaFree(s->state);
+    s->state = nullptr;
     cudaFree(s->scratch);
-    cudaFree(s->inst_d);
+    s->inst_d = nullptr;
+    s->counters = nullptr;
+    for (auto &m : s->masks) m = nullptr;
     if (s->host_stage) cudaFreeHost(s->host_stage);
     s->host_stage = nullptr;
     drop_graphs(s);
@@ -418,7 +418,60 @@ void fpd_default_params(fpd_params *p) {
     p->s_q = 1.9;
 }
 
+namespace {
+
+// Device state of one instance, every part 256-byte aligned, in one block:
+// populations, the two bead tables, the tile masks, the bead counter and the
+// instance record.
+constexpr size_t kStateAlign = 256;
+struct StateLayout {
+    size_t pool, tab, masks, counters, inst, total;  // offsets; total = block size
+    size_t pool_bytes, tab_bytes, tab_one, mask_bytes, mask_words;
+};
+size_t up(size_t v) { return (v + kStateAlign - 1) / kStateAlign * kStateAlign; }
+StateLayout state_layout(const fpd::Inst &I, size_t elem) {
+    StateLayout L{};
+    const size_t nbm = I.nb > 0 ? (size_t)I.nb : 1;
+    L.pool_bytes = 9 * (size_t)I.plane * elem;
+    // each table: 9 doubles then 6 floats per bead
+    L.tab_one = nbm * (fpd::kTabDoubles * sizeof(double) + fpd::kTabFloats * sizeof(float));
+    L.tab_bytes = 2 * L.tab_one;
+    L.mask_words = (size_t)I.ntx * I.nty * I.mask_words;
+    L.mask_bytes = fpd::kMaskBufs * L.mask_words * sizeof(unsigned);
+    L.pool = 0;
+    L.tab = up(L.pool + L.pool_bytes);
+    L.masks = up(L.tab + L.tab_bytes);
+    L.counters = up(L.masks + L.mask_bytes);
+    L.inst = up(L.counters + sizeof(unsigned));
+    L.total = up(L.inst + sizeof(fpd::Inst));
+    return L;
+}
+
+int create_impl(const fpd_params *p, void *stream, void *workspace, uint64_t workspace_bytes, fpd_sim **out);
+
+}  // namespace
+
+int fpd_workspace_bytes(const fpd_params *p, uint64_t *bytes) {
+    if (!p || !bytes) return fail(nullptr, FPD_EINVAL, "fpd_workspace_bytes: NULL argument");
+    fpd_sim tmp;
+    int rc = derive(&tmp, *p);
+    if (rc != FPD_OK) return rc;
+    *bytes = state_layout(tmp.inst, elem_size(p->precision)).total;
+    return FPD_OK;
+}
+
 int fpd_create(const fpd_params *p, void *stream, fpd_sim **out) {
+    return create_impl(p, stream, nullptr, 0, out);
+}
+
+int fpd_create_ex(const fpd_params *p, void *stream, void *workspace, uint64_t workspace_bytes, fpd_sim **out) {
+    if (!workspace) return fail(nullptr, FPD_EINVAL, "fpd_create_ex: NULL workspace");
+    return create_impl(p, stream, workspace, workspace_bytes, out);
+}
+
+namespace {
+
+int create_impl(const fpd_params *p, void *stream, void *workspace, uint64_t workspace_bytes, fpd_sim **out) {
     if (!p || !out) return fail(nullptr, FPD_EINVAL, "fpd_create: NULL argument");
     *out = nullptr;
     fpd_sim *s = new (std::nothrow) fpd_sim();
@@ -453,29 +506,39 @@ int fpd_create(const fpd_params *p, void *stream, fpd_sim **out) {
             return code;                                    \
         }                                                   \
     } while (0)
-    FPD_TRY(cudaMalloc(&s->pool, 9 * (size_t)I.plane * s->elem), "cudaMalloc populations");
-    FPD_TRY(cudaMemsetAsync(s->pool, 0, 9 * (size_t)I.plane * s->elem, s->stream), "cudaMemset populations");
+    const StateLayout L = state_layout(I, s->elem);
+    if (workspace) {
+        if (workspace_bytes < L.total || ((uintptr_t)workspace % kStateAlign) != 0) {
+            fail(nullptr, FPD_EINVAL, "workspace must hold %llu bytes at a %zu-byte aligned address",
+                 (unsigned long long)L.total, kStateAlign);
+            delete s;
+            return FPD_EINVAL;
+        }
+        s->state = workspace;
+        s->owns_state = false;
+    } else {
+        FPD_TRY(cudaMalloc(&s->state, L.total), "cudaMalloc simulation state");
+    }
+    FPD_TRY(cudaMemsetAsync(s->state, 0, L.total, s->stream), "cudaMemset simulation state");
+    char *base = (char *)s->state;
     const int nbm = nb > 0 ? nb : 1;
-    // two bead tables: 9 doubles then 6 floats per bead each
-    const size_t tab_bytes = (size_t)nbm * (fpd::kTabDoubles * sizeof(double) + fpd::kTabFloats * sizeof(float));
-    FPD_TRY(cudaMalloc(&s->tabmem, 2 * tab_bytes), "cudaMalloc bead tables");
-    FPD_TRY(cudaMemsetAsync(s->tabmem, 0, 2 * tab_bytes, s->stream), "cudaMemset tables");
+    s->pool = base + L.pool;
+    s->pool_bytes = L.pool_bytes;
+    s->tabmem = (double *)(base + L.tab);
+    s->tab_bytes = L.tab_bytes;
     for (int t = 0; t < 2; ++t) {
-        double *b = (double *)((char *)s->tabmem + t * tab_bytes);
+        double *b = (double *)((char *)s->tabmem + t * L.tab_one);
         float *f = (float *)(b + fpd::kTabDoubles * nbm);
         s->tab[t] = fpd::BeadTab{b,           b + nbm,     b + 2 * nbm, b + 3 * nbm, b + 4 * nbm,
                                  b + 5 * nbm, b + 6 * nbm, b + 7 * nbm, b + 8 * nbm, f,
                                  f + nbm,     f + 2 * nbm, f + 3 * nbm, f + 4 * nbm, f + 5 * nbm};
     }
-    // tile masks, one buffer per step of the rotation, zeroed
-    const size_t mask_words = (size_t)I.ntx * I.nty * I.mask_words;
-    FPD_TRY(cudaMalloc(&s->masks[0], fpd::kMaskBufs * mask_words * sizeof(unsigned)), "cudaMalloc tile masks");
-    for (int m = 1; m < fpd::kMaskBufs; ++m) s->masks[m] = s->masks[0] + m * mask_words;
-    FPD_TRY(cudaMemsetAsync(s->masks[0], 0, fpd::kMaskBufs * mask_words * sizeof(unsigned), s->stream),
-            "cudaMemset masks");
-    FPD_TRY(cudaMalloc(&s->counters, sizeof(unsigned)), "cudaMalloc counters");
-    FPD_TRY(cudaMemsetAsync(s->counters, 0, sizeof(unsigned), s->stream), "cudaMemset counters");
-    FPD_TRY(cudaMalloc(&s->inst_d, sizeof(fpd::Inst)), "cudaMalloc instance");
+    // tile masks, one buffer per step of the rotation (zeroed with the block)
+    s->masks[0] = (unsigned *)(base + L.masks);
+    for (int m = 1; m < fpd::kMaskBufs; ++m) s->masks[m] = s->masks[0] + m * L.mask_words;
+    s->mask_bytes = L.mask_bytes;
+    s->counters = (unsigned *)(base + L.counters);
+    s->inst_d = (fpd::Inst *)(base + L.inst);
     FPD_TRY(cudaMemcpyAsync(s->inst_d, &I, sizeof I, cudaMemcpyHostToDevice, s->stream), "copy instance");
     FPD_TRY(fpd::launch_init(s->precision, s->inst_d, I, s->pool, p->init_couette, s->stream), "init kernel");
     if (nb > 0) {
@@ -498,6 +561,8 @@ int fpd_create(const fpd_params *p, void *stream, fpd_sim **out) {
     *out = s;
     return FPD_OK;
 }
+
+}  // namespace
 
 int fpd_step(fpd_sim *s, int64_t n_steps) {
     if (!s) return fail(nullptr, FPD_EINVAL, "fpd_step: NULL handle");
@@ -626,6 +691,90 @@ int fpd_read_beads(fpd_sim *s, double *pos, double *vel, double *force, double *
     pair(vel, 2);  // the initial table keeps V = 0 until the second step overwrites it
     pair(force, 4);
     if (support) std::memcpy(support, h + 6 * (size_t)nb, nb * sizeof(double));
+    return FPD_OK;
+}
+
+namespace {
+
+// Checkpoint file: header, the derived instance record, then the device
+// blobs in this order: populations, bead tables, tile masks.
+struct CkptHeader {
+    char tag[8];
+    uint32_t abi, inst_bytes;
+    uint64_t pool_bytes, tab_bytes, mask_bytes;
+    int64_t nstep;
+};
+constexpr char kCkptTag[8] = {'F', 'P', 'D', 'C', 'K', 'P', 'T', '1'};
+
+}  // namespace
+
+int fpd_save(fpd_sim *s, const char *path) {
+    if (!s) return fail(nullptr, FPD_EINVAL, "fpd_save: NULL handle");
+    if (!path) return fail(s, FPD_EINVAL, "fpd_save: NULL path");
+    int rc = fpd_sync(s);
+    if (rc) return rc;
+    std::vector<char> pool(s->pool_bytes), tabs(s->tab_bytes), masks(s->mask_bytes);
+    cudaError_t e = cudaMemcpy(pool.data(), s->pool, pool.size(), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(tabs.data(), s->tabmem, tabs.size(), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(masks.data(), s->masks[0], masks.size(), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(s, e, "fpd_save");
+    CkptHeader h{};
+    std::memcpy(h.tag, kCkptTag, sizeof h.tag);
+    h.abi = FPD_ABI_VERSION;
+    h.inst_bytes = (uint32_t)sizeof(fpd::Inst);
+    h.pool_bytes = pool.size();
+    h.tab_bytes = tabs.size();
+    h.mask_bytes = masks.size();
+    h.nstep = s->nstep;
+    std::FILE *f = std::fopen(path, "wb");
+    if (!f) return fail(s, FPD_EINVAL, "fpd_save: cannot open %s for writing", path);
+    bool ok = std::fwrite(&h, sizeof h, 1, f) == 1 && std::fwrite(&s->inst, sizeof(fpd::Inst), 1, f) == 1 &&
+              std::fwrite(pool.data(), 1, pool.size(), f) == pool.size() &&
+              std::fwrite(tabs.data(), 1, tabs.size(), f) == tabs.size() &&
+              std::fwrite(masks.data(), 1, masks.size(), f) == masks.size();
+    ok = (std::fclose(f) == 0) && ok;
+    if (!ok) return fail(s, FPD_EINVAL, "fpd_save: writing %s failed", path);
+    return FPD_OK;
+}
+
+int fpd_load(fpd_sim *s, const char *path) {
+    if (!s) return fail(nullptr, FPD_EINVAL, "fpd_load: NULL handle");
+    if (!path) return fail(s, FPD_EINVAL, "fpd_load: NULL path");
+    std::FILE *f = std::fopen(path, "rb");
+    if (!f) return fail(s, FPD_EINVAL, "fpd_load: cannot open %s", path);
+    CkptHeader h{};
+    fpd::Inst inst;
+    std::vector<char> pool, tabs, masks;
+    const char *why = nullptr;
+    if (std::fread(&h, sizeof h, 1, f) != 1 || std::memcmp(h.tag, kCkptTag, sizeof h.tag) != 0) {
+        why = "not a checkpoint of this format";
+    } else if (h.abi != FPD_ABI_VERSION || h.inst_bytes != sizeof(fpd::Inst)) {
+        why = "written by another ABI version";
+    } else if (std::fread(&inst, sizeof inst, 1, f) != 1) {
+        why = "truncated";
+    } else if (std::memcmp(&inst, &s->inst, sizeof inst) != 0 || h.pool_bytes != s->pool_bytes ||
+               h.tab_bytes != s->tab_bytes || h.mask_bytes != s->mask_bytes || h.nstep < 0) {
+        why = "written with other parameters";
+    } else {
+        pool.resize(h.pool_bytes);
+        tabs.resize(h.tab_bytes);
+        masks.resize(h.mask_bytes);
+        if (std::fread(pool.data(), 1, pool.size(), f) != pool.size() ||
+            std::fread(tabs.data(), 1, tabs.size(), f) != tabs.size() ||
+            std::fread(masks.data(), 1, masks.size(), f) != masks.size())
+            why = "truncated";
+        else if (std::fgetc(f) != EOF)
+            why = "longer than a checkpoint";
+    }
+    std::fclose(f);
+    if (why) return fail(s, FPD_EINVAL, "fpd_load: %s: %s", path, why);
+    int rc = fpd_sync(s);
+    if (rc) return rc;
+    cudaError_t e = cudaMemcpy(s->pool, pool.data(), pool.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(s->tabmem, tabs.data(), tabs.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(s->masks[0], masks.data(), masks.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(s, e, "fpd_load");
+    s->nstep = h.nstep;
     return FPD_OK;
 }
 

@@ -276,11 +276,15 @@ __device__ void bead_force_f32(const Inst &I, const double *Rx, const double *Ry
     Fy += I.f_ext_fy;
 }
 
+// Persistent: CTA c handles beads c, c + gridDim.x, ... of the list, so a
+// grid that fits on the GPU at once reaches its dependents' launch point
+// (every CTA past griddepcontrol.launch_dependents) right away, however many
+// beads there are.
 template <class S>
 __global__ void __launch_bounds__(kBeadThreads)
-    k_beads(const Inst *__restrict__ insts, const int2 *__restrict__ blist, const S *__restrict__ pool,
-            const BeadTab tab0, const BeadTab tab1, unsigned *__restrict__ mask_write, int gparity, int advance,
-            unsigned *__restrict__ counters) {
+    k_beads(const Inst *__restrict__ insts, const int2 *__restrict__ blist, const int nb_total,
+            const S *__restrict__ pool, const BeadTab tab0, const BeadTab tab1, unsigned *__restrict__ mask_write,
+            int gparity, int advance, unsigned *__restrict__ counters) {
     constexpr bool kF64 = std::is_same<S, double>::value;
     __shared__ Inst sI;
     // neighbour beads: old-table position (FP64 path), offset R_b - R_q and
@@ -296,8 +300,10 @@ __global__ void __launch_bounds__(kBeadThreads)
     __shared__ Box s_box;
     __shared__ int s_last, s_nn;
 
+    for (int it = blockIdx.x; it < nb_total; it += gridDim.x) {
+    __syncthreads();  // the shared state of the previous bead is no longer read
     // blist[i] = (instance slot, global bead index); NULL: instance 0, bead i
-    const int2 bi = blist ? blist[blockIdx.x] : make_int2(0, (int)blockIdx.x);
+    const int2 bi = blist ? blist[it] : make_int2(0, it);
     const int ii = bi.x, b = bi.y;
     const int tid = threadIdx.x;
     {
@@ -523,7 +529,7 @@ __global__ void __launch_bounds__(kBeadThreads)
         s_last = (prev == (unsigned)(I.nb - 1));
     }
     __syncthreads();
-    if (!s_last) return;
+    if (s_last) {
     __threadfence();
     // stage the instance's new positions and support sums (written by every
     // CTA; the L2-coherent loads see them), then every segment once
@@ -597,16 +603,40 @@ __global__ void __launch_bounds__(kBeadThreads)
         tnew.gyf[gq] = (float)Gy;
     }
     if (tid == 0) counters[ii] = 0u;
+    }  // last bead of the instance
+    }  // beads of this CTA
 }
 
 }  // namespace
+
+// CTAs of k_beads<S> that the device holds at once (cached per device).
+template <class S>
+static int bead_grid_cap() {
+    static int cap[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1 << 30;
+    if (cap[dev] == 0) {
+        int per_sm = 0, sms = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_beads<S>, kBeadThreads, 0) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || per_sm < 1)
+            return 1 << 30;  // unknown: one CTA per bead
+        cap[dev] = per_sm * sms;
+    }
+    return cap[dev];
+}
 
 cudaError_t launch_beads(int precision, const Inst *inst_d, const int2 *blist, int nb_total, const void *pool,
                          BeadTab tab0, BeadTab tab1, unsigned *mask_write, int gparity, int advance,
                          unsigned *counters, int pdl, cudaStream_t st) {
     if (nb_total <= 0) return cudaSuccess;
+    int cap = 1 << 30;
+    switch (precision) {
+        case 0: cap = bead_grid_cap<double>(); break;
+        case 1: cap = bead_grid_cap<float>(); break;
+        case 2: cap = bead_grid_cap<__half>(); break;
+    }
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(nb_total);
+    cfg.gridDim = dim3(nb_total < cap ? nb_total : cap);
     cfg.blockDim = dim3(kBeadThreads);
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
@@ -616,14 +646,14 @@ cudaError_t launch_beads(int precision, const Inst *inst_d, const int2 *blist, i
     cfg.numAttrs = pdl ? 1 : 0;
     switch (precision) {
         case 0:
-            return cudaLaunchKernelEx(&cfg, k_beads<double>, inst_d, blist, (const double *)pool, tab0, tab1,
-                                      mask_write, gparity, advance, counters);
+            return cudaLaunchKernelEx(&cfg, k_beads<double>, inst_d, blist, nb_total, (const double *)pool, tab0,
+                                      tab1, mask_write, gparity, advance, counters);
         case 1:
-            return cudaLaunchKernelEx(&cfg, k_beads<float>, inst_d, blist, (const float *)pool, tab0, tab1,
-                                      mask_write, gparity, advance, counters);
+            return cudaLaunchKernelEx(&cfg, k_beads<float>, inst_d, blist, nb_total, (const float *)pool, tab0,
+                                      tab1, mask_write, gparity, advance, counters);
         case 2:
-            return cudaLaunchKernelEx(&cfg, k_beads<__half>, inst_d, blist, (const __half *)pool, tab0, tab1,
-                                      mask_write, gparity, advance, counters);
+            return cudaLaunchKernelEx(&cfg, k_beads<__half>, inst_d, blist, nb_total, (const __half *)pool, tab0,
+                                      tab1, mask_write, gparity, advance, counters);
     }
     return cudaErrorInvalidValue;
 }

@@ -15,7 +15,10 @@ struct fpd_sim {
     fpd::Inst *inst_d = nullptr;
     int precision = 0;
     size_t elem = 8;
+    void *state = nullptr;          // one block holding pool, tables, masks, counters, instance record
+    bool owns_state = true;         // false: caller workspace (fpd_create_ex), never freed here
     void *pool = nullptr;           // 9 planes of pitch * ny elements
+    size_t pool_bytes = 0, tab_bytes = 0, mask_bytes = 0;  // sizes of pool, both tables, all masks
     double *tabmem = nullptr;       // two bead tables
     fpd::BeadTab tab[2]{};
     unsigned *counters = nullptr;   // one per instance (bead-phase last-block)

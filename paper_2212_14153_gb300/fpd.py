@@ -63,6 +63,11 @@ SIGNATURES = {
     "fpd_sync": (ctypes.c_int, [ctypes.c_void_p]),
     "fpd_read_fields": (ctypes.c_int, [ctypes.c_void_p, _DP, _DP, _DP]),
     "fpd_internal_flow": (ctypes.c_int, [ctypes.c_void_p, _DP]),
+    "fpd_workspace_bytes": (ctypes.c_int, [ctypes.POINTER(fpd_params), ctypes.POINTER(ctypes.c_uint64)]),
+    "fpd_create_ex": (ctypes.c_int, [ctypes.POINTER(fpd_params), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64,
+                                     ctypes.POINTER(ctypes.c_void_p)]),
+    "fpd_save": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p]),
+    "fpd_load": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p]),
     "fpd_batch_internal_flow": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, _DP]),
     "fpd_read_beads": (ctypes.c_int, [ctypes.c_void_p, _DP, _DP, _DP, _DP]),
     "fpd_read_populations": (ctypes.c_int, [ctypes.c_void_p, _DP]),
@@ -145,6 +150,20 @@ def fpd_create(params: fpd_params, stream=None) -> ctypes.c_void_p:
     return h
 
 
+def fpd_workspace_bytes(params: fpd_params) -> int:
+    n = ctypes.c_uint64()
+    _check(load_library().fpd_workspace_bytes(ctypes.byref(params), ctypes.byref(n)), None)
+    return int(n.value)
+
+
+def fpd_create_ex(params: fpd_params, stream, workspace_ptr: int, workspace_bytes: int) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    rc = load_library().fpd_create_ex(ctypes.byref(params), stream, ctypes.c_void_p(workspace_ptr),
+                                      int(workspace_bytes), ctypes.byref(h))
+    _check(rc, None)
+    return h
+
+
 def fpd_step(h, n_steps: int) -> None:
     _check(load_library().fpd_step(h, int(n_steps)), h)
 
@@ -155,6 +174,14 @@ def fpd_sync(h) -> None:
 
 def fpd_read_fields(h, ux, uy, rho) -> None:
     _check(load_library().fpd_read_fields(h, _ptr(ux), _ptr(uy), _ptr(rho)), h)
+
+
+def fpd_save(h, path: str) -> None:
+    _check(load_library().fpd_save(h, os.fsencode(path)), h)
+
+
+def fpd_load(h, path: str) -> None:
+    _check(load_library().fpd_load(h, os.fsencode(path)), h)
 
 
 def fpd_internal_flow(h, eps) -> None:
@@ -256,10 +283,19 @@ def params_from_config(cfg: dict) -> tuple[fpd_params, list]:
     return p, keep
 
 
+def workspace_bytes(cfg: dict) -> int:
+    """Device bytes a Simulation of cfg needs when given a workspace."""
+    p, keep = params_from_config(cfg)
+    return fpd_workspace_bytes(p)
+
+
 class Simulation:
     """One FPD instance on the GPU, driven through the C ABI."""
 
-    def __init__(self, cfg: dict, stream=None):
+    def __init__(self, cfg: dict, stream=None, workspace=None):
+        """workspace: optional CUDA tensor (any dtype, contiguous, at least
+        workspace_bytes(cfg) bytes, 256-byte aligned) that holds the state;
+        it is kept referenced for the handle's lifetime."""
         if stream is None:
             import torch
             if not torch.cuda.is_available():
@@ -267,7 +303,11 @@ class Simulation:
             stream = torch.cuda.current_stream().cuda_stream
         self.cfg = dict(cfg)
         p, keep = params_from_config(cfg)
-        self.h = fpd_create(p, stream)
+        self._ws = workspace
+        if workspace is not None:
+            self.h = fpd_create_ex(p, stream, workspace.data_ptr(), workspace.numel() * workspace.element_size())
+        else:
+            self.h = fpd_create(p, stream)
         self.nx, self.ny = p.nx, p.ny
         self.nb = p.n_beads * p.n_fibers
 
@@ -299,6 +339,14 @@ class Simulation:
         fpd_read_beads(self.h, R, V, F, S)
         k = self.nb
         return R[:k], V[:k], F[:k], S[:k]
+
+    def save(self, path: str):
+        """Checkpoint the whole device state to a file."""
+        fpd_save(self.h, path)
+
+    def load(self, path: str):
+        """Resume from a checkpoint written with the same parameters."""
+        fpd_load(self.h, path)
 
     def internal_flow(self) -> np.ndarray:
         """eps_v of every bead (Sec. 3.2)."""

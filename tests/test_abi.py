@@ -106,3 +106,23 @@ def _load_fresh(fpd, path):
         return fpd.load_library(path)
     finally:
         fpd._lib = saved
+
+
+def test_workspace_bytes_without_a_device(lib):
+    # the size query is host-only: the state layout of the parameters
+    from paper_2212_14153_gb300 import fpd
+    import numpy as np
+    p = fpd.fpd_default_params()
+    p.n_beads, p.n_fibers = 8, 1
+    cen = np.array([40.0, 20.0]); th = np.array([0.5])
+    p.centre_xy = cen.ctypes.data_as(fpd._DP)
+    p.theta0 = th.ctypes.data_as(fpd._DP)
+    for prec, es in ((0, 8), (1, 4), (2, 2)):
+        p.precision = prec
+        n = fpd.fpd_workspace_bytes(p)
+        pitch = -(-p.nx * es // 128) * 128 // es
+        assert n % 256 == 0 and n >= 9 * pitch * p.ny * es
+    p.nx = 0
+    with pytest.raises(fpd.FpdError) as e:
+        fpd.fpd_workspace_bytes(p)
+    assert e.value.code == fpd.FPD_EINVAL

@@ -167,10 +167,12 @@ def test_fp64_parity_small_fiber_config_full_run():
     cfg = wl.single_fiber_small()
     g, o = run_both(cfg, cfg["steps"])
     res = compare_f64(g, o)
-    # the fiber actually moved and rotated
+    # the fiber actually moved and rotated, its springs within 2 % strain
     R = g.beads()[0]
     R0 = gpu_sim(cfg).beads()[0]
     assert np.abs(R - R0).max() > 0.05
+    L = np.linalg.norm(np.diff(R, axis=0), axis=1)
+    assert np.abs(L / (2 * cfg["a"]) - 1).max() < 0.02
     print("config parity", res)
 
 
@@ -482,3 +484,75 @@ def test_early_cold_tiles_give_identical_results(precision, monkeypatch):
     assert np.array_equal(a.populations(), b.populations())
     for x, y in zip(a.beads(), b.beads()):
         assert np.array_equal(x, y)
+
+
+# ------------------------------------------------------------ checkpoint / resume
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_checkpoint_resume_is_bit_identical(precision, tmp_path):
+    rng = np.random.default_rng(55)
+    cfg = wl.random_fiber(rng, 70, 37, n_beads=5, a=2.0, xi=1.0, n_fibers=2, precision=precision)
+    a = gpu_sim(cfg)
+    for split in (41, 42):               # both step parities at the save
+        a = gpu_sim(cfg)
+        a.step(split)
+        path = str(tmp_path / f"ck{split}.fpd")
+        a.save(path)
+        a.step(70)                       # two graph chunks and a remainder
+        b = gpu_sim(cfg)
+        b.step(3)                        # a different state, overwritten by the load
+        b.load(path)
+        assert b.diag()[3] == split
+        b.step(70)
+        assert np.array_equal(a.populations(), b.populations())
+        for x, y in zip(a.beads(), b.beads()):
+            assert np.array_equal(x, y)
+
+
+def test_checkpoint_rejects_other_parameters_and_bad_files(tmp_path):
+    from paper_2212_14153_gb300 import fpd
+    rng = np.random.default_rng(56)
+    cfg = wl.random_fiber(rng, 64, 32, n_beads=4, a=2.0, xi=1.0, precision=1)
+    a = gpu_sim(cfg)
+    a.step(10)
+    path = str(tmp_path / "ck.fpd")
+    a.save(path)
+    ref = a.populations()
+    for other in (dict(cfg, nx=66), dict(cfg, precision=0), dict(cfg, visc_ratio=49.0)):
+        c = gpu_sim(other)
+        with pytest.raises(fpd.FpdError) as e:
+            c.load(path)
+        assert e.value.code == fpd.FPD_EINVAL
+    raw = open(path, "rb").read()
+    bad = {"trunc.fpd": raw[:-7], "junk.fpd": b"not a checkpoint" + raw[16:], "long.fpd": raw + b"x"}
+    for name, data in bad.items():
+        p = str(tmp_path / name)
+        open(p, "wb").write(data)
+        with pytest.raises(fpd.FpdError):
+            a.load(p)
+    with pytest.raises(fpd.FpdError):
+        a.load(str(tmp_path / "missing.fpd"))
+    # a failed load leaves the handle as it was
+    assert np.array_equal(a.populations(), ref)
+
+
+def test_caller_workspace_gives_identical_results():
+    import torch
+    from paper_2212_14153_gb300 import fpd
+    rng = np.random.default_rng(57)
+    cfg = wl.random_fiber(rng, 70, 37, n_beads=5, a=2.0, xi=1.0, precision=1)
+    n = fpd.workspace_bytes(cfg)
+    ws = torch.empty(n + 512, dtype=torch.uint8, device="cuda")
+    a = gpu_sim(cfg)
+    b = fpd.Simulation(cfg, workspace=ws[:n])
+    a.step(77)
+    b.step(77)
+    assert np.array_equal(a.populations(), b.populations())
+    for x, y in zip(a.beads(), b.beads()):
+        assert np.array_equal(x, y)
+    b.close()
+    ws.fill_(7)                      # still the caller's memory after destroy
+    torch.cuda.synchronize()
+    for bad in (ws[:n - 256], ws[1:n + 1]):   # too short; misaligned
+        with pytest.raises(fpd.FpdError) as e:
+            fpd.Simulation(cfg, workspace=bad)
+        assert e.value.code == fpd.FPD_EINVAL

@@ -31,6 +31,13 @@ def fpd():
     return binding
 
 
+def max_strain(R, n_beads, l0):
+    """Largest |L / l0 - 1| over the springs of every fiber."""
+    R = R.reshape(-1, n_beads, 2)
+    L = np.linalg.norm(np.diff(R, axis=1), axis=2)
+    return float(np.abs(L / l0 - 1).max())
+
+
 def rel(a, b):
     return float(np.sqrt(np.sum((a - b) ** 2) / np.sum(b ** 2)))
 
@@ -67,6 +74,7 @@ def test_two_fiber_lattice_long_against_fp64_gpu(fpd):
     ux, uy, _ = ref.fields()
     ref_u, ref_R = np.stack([ux, uy]), ref.beads()[0]
     ref.close()
+    assert max_strain(ref_R, base["n_beads"], 2 * base["a"]) < 0.02
     for p, bu in ((1, 1e-4), (2, 3e-2)):
         s = fpd.Simulation(dict(base, precision=p))
         s.step(steps)
@@ -89,6 +97,12 @@ def test_single_fiber_long_run_drift(fpd):
         done = c
         ux, uy, _ = sims[0].fields()
         ref_u, ref_R = np.stack([ux, uy]), sims[0].beads()[0]
+        for p in (0, 1, 2):
+            # the default spring stays within 2 % strain (the inextensible
+            # limit's gate) all along the flexible fiber's tumbling
+            st = max_strain(sims[p].beads()[0], base["n_beads"], 2 * base["a"])
+            print(f"single-fiber 1024x256, {c} steps, {NAMES[p]}: max spring strain {st:.2e}")
+            assert st < 0.02
         for p in (1, 2):
             e = errors(sims[p], ref_u, ref_R)
             print(f"single-fiber 1024x256, {c} steps, {NAMES[p]} vs f64 GPU: {e}")
