@@ -19,7 +19,7 @@
 // support are FP64.  In the FP64 (parity) path phi is evaluated in FP64
 // exactly as a plain IEEE evaluation would; in the FP32/FP16-storage paths
 // phi and u are FP32 from bead-relative offsets, each thread adds its few
-// support cells (ceil(cells / 256), 3 for a = 4, xi = 1) in FP32 and the
+// support cells (ceil(cells / 128), 7 for a = 4, xi = 1) in FP32 and the
 // partials are reduced in FP64.  FP64 instructions are kept out of per-cell
 // work: this GPU issues one FP64 warp instruction per ~16 cycles per SM.
 // Only beads whose support can overlap bead b's support are visited per
@@ -612,9 +612,10 @@ cudaError_t launch_beads(int precision, const Inst *inst_d, const int2 *blist, i
                          unsigned *counters, int pdl, cudaStream_t st) {
     if (nb_total <= 0) return cudaSuccess;
     // one CTA per bead: a grid capped at the resident CTAs (persistent) keeps
-    // all 256-thread bead CTAs on the SMs at once and leaves the sweep that
-    // follows no registers to start its unmarked tiles with (measured: the
-    // batched step 8 % slower), so every bead gets its own CTA
+    // the bead CTAs on the SMs at once and leaves the sweep that follows
+    // too few registers to start its unmarked tiles with (measured with
+    // 256-thread CTAs: the batched step 8 % slower), so every bead gets its
+    // own CTA
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(nb_total);
     cfg.blockDim = dim3(kBeadThreads);
