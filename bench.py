@@ -230,7 +230,7 @@ def run_gpu(args, rank: int, world: int):
                 "workload": cfg["name"], "nx": cfg["nx"], "ny": cfg["ny"], "fibers": cfg["n_fibers"],
                 "beads_per_fiber": cfg["n_beads"], "storage": {0: "f64", 1: "f32", 2: "f16x2^s"}[args.precision],
                 "bytes_per_cell_update": bpc, "per_gpu": "one independent instance",
-                "l2": l2_note(bpc // 2 * cells), "sweep_variant": variant, "variant_ms_per_step": variant_ms,
+                "l2": l2_note(bpc * cells), "sweep_variant": variant, "variant_ms_per_step": variant_ms,
                 "parallelism": f"replicas x{world}",
             },
             "roofline": {

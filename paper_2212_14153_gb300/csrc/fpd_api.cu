@@ -421,8 +421,8 @@ void fpd_default_params(fpd_params *p) {
 namespace {
 
 // Device state of one instance, every part 256-byte aligned, in one block:
-// populations, the two bead tables, the tile masks, the bead counter and the
-// instance record.
+// the two population buffers, the two bead tables, the tile masks, the bead
+// counter and the instance record.
 constexpr size_t kStateAlign = 256;
 struct StateLayout {
     size_t pool, tab, masks, counters, inst, total;  // offsets; total = block size
@@ -432,7 +432,7 @@ size_t up(size_t v) { return (v + kStateAlign - 1) / kStateAlign * kStateAlign; 
 StateLayout state_layout(const fpd::Inst &I, size_t elem) {
     StateLayout L{};
     const size_t nbm = I.nb > 0 ? (size_t)I.nb : 1;
-    L.pool_bytes = 9 * (size_t)I.plane * elem;
+    L.pool_bytes = 2 * 9 * (size_t)I.plane * elem;  // two population buffers
     // each table: 9 doubles then 6 floats per bead
     L.tab_one = nbm * (fpd::kTabDoubles * sizeof(double) + fpd::kTabFloats * sizeof(float));
     L.tab_bytes = 2 * L.tab_one;

@@ -317,7 +317,7 @@ int fpd_batch_add(fpd_batch *b, const fpd_params *p, int64_t n_steps, int32_t *s
             break;
         }
     if (s < 0) return bfail(b, FPD_EBUSY, "no free slot (%d in use)", b->max_slots);
-    const int64_t pop_len = 9 * I.plane;
+    const int64_t pop_len = 2 * 9 * I.plane;  // two population buffers
     const int64_t off = b->pop_alloc.alloc(pop_len, (int64_t)(256 / b->elem));
     if (off < 0) return bfail(b, FPD_EBUSY, "no room for %lld population elements", (long long)pop_len);
     int boff = 0;

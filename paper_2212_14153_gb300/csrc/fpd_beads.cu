@@ -313,9 +313,10 @@ __global__ void __launch_bounds__(kBeadThreads)
     }
     __syncthreads();
     const Inst &I = sI;
-    const S *A = pool + I.pop_off;
+    // populations are pulled from the current buffer (the instance's parity)
     // this instance's step parity selects the table pair and the layout
     const int parity = gparity ^ I.par_xor;
+    const S *A = pop_buffer(pool, I, parity);
     const BeadTab &told = parity ? tab0 : tab1;
     const BeadTab &tnew = parity ? tab1 : tab0;
 
@@ -387,7 +388,7 @@ __global__ void __launch_bounds__(kBeadThreads)
                 const double phb = phi_f64(I, xc, yc, Rx, Ry);
                 if (phb == 0.0) continue;
                 double g[9];
-                load_pops<S, double>(A, I, make_cell(I, i, j), parity, g);
+                pull_pops<S, double>(A, I, make_cell(I, i, j), g);
                 double dr = 0.0;
 #pragma unroll
                 for (int k = 0; k < 9; ++k) dr += g[k];
@@ -409,7 +410,7 @@ __global__ void __launch_bounds__(kBeadThreads)
                 const float phb = phi_f32(dx, dy, I.f_a, I.f_inv_xi, I.f_rcut2);
                 if (phb == 0.0f) continue;
                 float g[9];
-                load_pops<S, float>(A, I, make_cell(I, i, j), parity, g);
+                pull_pops<S, float>(A, I, make_cell(I, i, j), g);
                 const float rho = 1.0f + (((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8]);
                 const float jx = (g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]);
                 const float jy = (g[2] - g[4]) + (g[5] + g[6]) - (g[7] + g[8]);

@@ -119,16 +119,23 @@ template <> struct Store<__half> {
     }
 };
 
-// -------------------------------------------------- AA-pattern population access
-// Storage A[k][y][x] holds deviations g_k = f_k - w_k.  With t the number of
-// completed steps, step t reads and writes:
-//   t even:  g_k(x) = A[k][x]               ->  A[opp k][x] = g*_k(x)
-//   t odd :  g_k(x) = A[opp k][x - c_k]     ->  A[k][x + c_k] = g*_k(x)
-// A neighbour beyond a wall is replaced by half-way bounce-back from the
-// same cell: arriving  g_k = g*_{opp k} + 6 w_k (c_k . u_w)  (read side of an
-// odd step) and leaving  g_{opp k} = g*_k - 6 w_k (c_k . u_w)  (write side).
-// FP16 storage: plane p is always encoded with scale[p] (scale[p] ==
-// scale[opp p], so either content of a plane fits its range).
+// ------------------------------------------------------ population access
+// Two buffers of 9 planes A[k][y][x] per instance hold deviations g_k =
+// f_k - w_k.  After t completed steps, buffer t & 1 holds the post-collision
+// populations g*_k(x) of the last step at their own cell (the initial state
+// is placed so that the same pull yields it).  A step pulls
+//   g_k(x) = g*_k(x - c_k)                          (streaming, Sec. 2.3)
+// from it, collides, and stores g*_k(x) at x in the other buffer.  A source
+// beyond a wall is replaced by half-way bounce-back from the same cell:
+//   g_k(x) = g*_{opp k}(x) + 6 w_k (c_k . u_w).
+// Pulling costs only shifted reads; every store is aligned.  FP16 storage:
+// plane k is encoded with scale[k] (scale[k] == scale[opp k]).
+
+// Buffer `which` (0 or 1) of an instance.
+template <class S>
+__device__ __forceinline__ S *pop_buffer(S *pool, const Inst &I, int which) {
+    return pool + I.pop_off + (which ? (int64_t)9 * I.plane : (int64_t)0);
+}
 
 // A cell with its periodic x neighbours and the element offsets of its row
 // and the rows above and below (wrapped when y is periodic; the row beyond a
@@ -151,69 +158,67 @@ __device__ __forceinline__ Cell make_cell(const Inst &I, int x, int y) {
     return c;
 }
 
+// g_k(x) from the current buffer A.
 template <int k, class S, class R>
-__device__ __forceinline__ void load_one(const S *__restrict__ A, const Inst &I, const Cell &C, int parity, R &g) {
+__device__ __forceinline__ void pull_one(const S *__restrict__ A, const Inst &I, const Cell &C, R &g) {
     constexpr int cx = Q<k>::cx, cy = Q<k>::cy, o = Q<k>::opp;
-    if (parity == 0) {
-        g = (R)Store<S>::ld(A + (k * I.plane32 + C.r0 + C.x), I.inv_scale[k]);
+    // source cell x - c_k; beyond a wall when it is row -1 or row ny
+    const bool wall = (cy > 0 && C.bot) || (cy < 0 && C.top);
+    if (wall) {
+        g = (R)Store<S>::ld(A + (o * I.plane32 + C.r0 + C.x), I.inv_scale[o]) + bb_term<R>(I, cy > 0 ? 0 : 1, k);
     } else {
-        // source cell x - c_k; beyond a wall when it is row -1 or row ny
-        const bool wall = (cy > 0 && C.bot) || (cy < 0 && C.top);
-        if (wall) {
-            g = (R)Store<S>::ld(A + (k * I.plane32 + C.r0 + C.x), I.inv_scale[k]) +
-                bb_term<R>(I, cy > 0 ? 0 : 1, k);
-        } else {
-            const int rs = cy > 0 ? C.rm : (cy < 0 ? C.rp : C.r0);
-            const int xs = cx > 0 ? C.xm : (cx < 0 ? C.xp : C.x);
-            g = (R)Store<S>::ld(A + (o * I.plane32 + rs + xs), I.inv_scale[o]);
-        }
+        const int rs = cy > 0 ? C.rm : (cy < 0 ? C.rp : C.r0);
+        const int xs = cx > 0 ? C.xm : (cx < 0 ? C.xp : C.x);
+        g = (R)Store<S>::ld(A + (k * I.plane32 + rs + xs), I.inv_scale[k]);
     }
 }
 
+// Inverse of pull_one: store g so that the next pull of direction k at x
+// yields it (initial state, writes of a given state).
 template <int k, class S, class R>
-__device__ __forceinline__ void store_one(S *__restrict__ A, const Inst &I, const Cell &C, int parity, R g) {
+__device__ __forceinline__ void place_one(S *__restrict__ A, const Inst &I, const Cell &C, R g) {
     constexpr int cx = Q<k>::cx, cy = Q<k>::cy, o = Q<k>::opp;
-    if (parity == 0) {
-        Store<S>::st(A + (o * I.plane32 + C.r0 + C.x), g, I.scale[o]);
+    const bool wall = (cy > 0 && C.bot) || (cy < 0 && C.top);
+    if (wall) {
+        Store<S>::st(A + (o * I.plane32 + C.r0 + C.x), g - bb_term<R>(I, cy > 0 ? 0 : 1, k), I.scale[o]);
     } else {
-        // destination cell x + c_k; beyond a wall when it is row ny or row -1
-        const bool wall = (cy > 0 && C.top) || (cy < 0 && C.bot);
-        if (wall) {
-            Store<S>::st(A + (o * I.plane32 + C.r0 + C.x), g - bb_term<R>(I, cy > 0 ? 1 : 0, k), I.scale[o]);
-        } else {
-            const int rd = cy > 0 ? C.rp : (cy < 0 ? C.rm : C.r0);
-            const int xd = cx > 0 ? C.xp : (cx < 0 ? C.xm : C.x);
-            Store<S>::st(A + (k * I.plane32 + rd + xd), g, I.scale[k]);
-        }
+        const int rs = cy > 0 ? C.rm : (cy < 0 ? C.rp : C.r0);
+        const int xs = cx > 0 ? C.xm : (cx < 0 ? C.xp : C.x);
+        Store<S>::st(A + (k * I.plane32 + rs + xs), g, I.scale[k]);
     }
 }
 
 template <class S, class R>
-__device__ __forceinline__ void load_pops(const S *__restrict__ A, const Inst &I, const Cell &C, int parity,
-                                          R g[9]) {
-    load_one<0>(A, I, C, parity, g[0]);
-    load_one<1>(A, I, C, parity, g[1]);
-    load_one<2>(A, I, C, parity, g[2]);
-    load_one<3>(A, I, C, parity, g[3]);
-    load_one<4>(A, I, C, parity, g[4]);
-    load_one<5>(A, I, C, parity, g[5]);
-    load_one<6>(A, I, C, parity, g[6]);
-    load_one<7>(A, I, C, parity, g[7]);
-    load_one<8>(A, I, C, parity, g[8]);
+__device__ __forceinline__ void pull_pops(const S *__restrict__ A, const Inst &I, const Cell &C, R g[9]) {
+    pull_one<0>(A, I, C, g[0]);
+    pull_one<1>(A, I, C, g[1]);
+    pull_one<2>(A, I, C, g[2]);
+    pull_one<3>(A, I, C, g[3]);
+    pull_one<4>(A, I, C, g[4]);
+    pull_one<5>(A, I, C, g[5]);
+    pull_one<6>(A, I, C, g[6]);
+    pull_one<7>(A, I, C, g[7]);
+    pull_one<8>(A, I, C, g[8]);
+}
+
+// Post-collision populations of cell C, stored at the cell (aligned).
+template <class S, class R>
+__device__ __forceinline__ void put_pops(S *__restrict__ D, const Inst &I, const Cell &C, const R g[9]) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Store<S>::st(D + (k * I.plane32 + C.r0 + C.x), g[k], I.scale[k]);
 }
 
 template <class S, class R>
-__device__ __forceinline__ void store_pops(S *__restrict__ A, const Inst &I, const Cell &C, int parity,
-                                           const R g[9]) {
-    store_one<0>(A, I, C, parity, g[0]);
-    store_one<1>(A, I, C, parity, g[1]);
-    store_one<2>(A, I, C, parity, g[2]);
-    store_one<3>(A, I, C, parity, g[3]);
-    store_one<4>(A, I, C, parity, g[4]);
-    store_one<5>(A, I, C, parity, g[5]);
-    store_one<6>(A, I, C, parity, g[6]);
-    store_one<7>(A, I, C, parity, g[7]);
-    store_one<8>(A, I, C, parity, g[8]);
+__device__ __forceinline__ void place_pops(S *__restrict__ A, const Inst &I, const Cell &C, const R g[9]) {
+    place_one<0>(A, I, C, g[0]);
+    place_one<1>(A, I, C, g[1]);
+    place_one<2>(A, I, C, g[2]);
+    place_one<3>(A, I, C, g[3]);
+    place_one<4>(A, I, C, g[4]);
+    place_one<5>(A, I, C, g[5]);
+    place_one<6>(A, I, C, g[6]);
+    place_one<7>(A, I, C, g[7]);
+    place_one<8>(A, I, C, g[8]);
 }
 
 // ---------------------------------------------------------------- Eq. 2

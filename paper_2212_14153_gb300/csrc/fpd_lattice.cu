@@ -10,7 +10,8 @@
 // viscosity of Eq. 1 and the spread force of Eq. 4 per cell, visiting the
 // marked beads in bead order.  Every cell gathers its 9 populations (AA
 // pattern, bounce-back at the walls), collides (MRT + Guo) and scatters them
-// back in place.  No block-wide barrier: each thread reads the tile's mask.
+// to the other population buffer.  No block-wide barrier: each thread reads
+// the tile's mask.
 #include <cuda_fp16.h>
 
 #include <type_traits>
@@ -133,7 +134,8 @@ __device__ __forceinline__ void lattice_tile(const Inst &I, S *__restrict__ pool
     const int x = bx * kTileX + tx;
     const int tile = I.tile_base + by * I.ntx + bx;
     const int W = I.mask_words;
-    S *A = pool + I.pop_off;
+    const S *Asrc = pop_buffer(pool, I, parity);
+    S *Adst = pop_buffer(pool, I, parity ^ 1);
     int y[CY];
     bool valid[CY];
     Cell C[CY];
@@ -149,7 +151,7 @@ __device__ __forceinline__ void lattice_tile(const Inst &I, S *__restrict__ pool
     if (early_load) {
 #pragma unroll
         for (int k = 0; k < CY; ++k)
-            if (valid[k]) load_pops<S, R>(A, I, C[k], parity, g[k]);
+            if (valid[k]) pull_pops<S, R>(Asrc, I, C[k], g[k]);
     }
     const bool cold = tile_cold_early(mask_prev + tile * W, W, early_cold, lead);
     if (!cold) pdl_wait();
@@ -160,7 +162,7 @@ __device__ __forceinline__ void lattice_tile(const Inst &I, S *__restrict__ pool
     if (!early_load) {
 #pragma unroll
         for (int k = 0; k < CY; ++k)
-            if (valid[k]) load_pops<S, R>(A, I, C[k], parity, g[k]);
+            if (valid[k]) pull_pops<S, R>(Asrc, I, C[k], g[k]);
     }
     const unsigned *m = mask_read + tile * W;
     unsigned any = 0u;
@@ -172,7 +174,7 @@ __device__ __forceinline__ void lattice_tile(const Inst &I, S *__restrict__ pool
         R Fx, Fy, s_nu, s_e, s_eps, s_q;
         cell_overlay<R>(I, tab, m, W, any, x, y[k], Fx, Fy, s_nu, s_e, s_eps, s_q);
         collide<R>(g[k], Fx, Fy, s_nu, s_e, s_eps, s_q);
-        store_pops<S, R>(A, I, C[k], parity, g[k]);
+        put_pops<S, R>(Adst, I, C[k], g[k]);
     }
 }
 
@@ -211,14 +213,12 @@ __global__ void __launch_bounds__(kTileX *kTileY / CY)
 // ------------------------------------------------ vectorised sweep (variant 2)
 // Each thread owns NV consecutive cells of one tile row and moves each of its
 // nine planes with one 16-byte access (8 bytes for FP16 storage).  A tile row
-// of 32 cells is a segment of G = 32 / NV lanes of one warp.  Even steps are
-// purely local.  On odd steps a direction with c_kx = +1 needs the element
-// one to the left of the thread's vector and one of its results lands one to
-// the right (mirrored for c_kx = -1): the missing element comes from the
-// neighbouring lane by a shuffle; at the segment ends (tile edges, the
-// periodic wrap, the last cell of a row) the edge lane reads or writes that
-// single element with a scalar access, and leaves out of its vector store
-// the element its neighbour tile writes.  Requires nx % NV == 0.
+// of 32 cells is a segment of G = 32 / NV lanes of one warp.  Stores are
+// aligned.  A pulled direction with c_kx = +1 needs the element one to the
+// left of the thread's vector (mirrored for c_kx = -1): it comes from the
+// neighbouring lane by a shuffle, and at the segment ends (tile edges, the
+// periodic wrap, the last cell of a row) the edge lane reads that single
+// element with a scalar access.  Requires nx % NV == 0.
 
 template <class S, int NV> struct VecIO;
 template <> struct VecIO<float, 4> {
@@ -229,16 +229,6 @@ template <> struct VecIO<float, 4> {
     static __device__ __forceinline__ void st(float *p, const float v[4], float) {
         *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
     }
-    // elements 1..3 (the first is written by the tile to the left)
-    static __device__ __forceinline__ void st_tail(float *p, const float v[4], float) {
-        p[1] = v[1];
-        *reinterpret_cast<float2 *>(p + 2) = make_float2(v[2], v[3]);
-    }
-    // elements 0..2 (the last is written by the tile to the right)
-    static __device__ __forceinline__ void st_head(float *p, const float v[4], float) {
-        *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
-        p[2] = v[2];
-    }
 };
 template <> struct VecIO<double, 2> {
     static __device__ __forceinline__ void ld(const double *p, float, double v[2]) {
@@ -248,8 +238,6 @@ template <> struct VecIO<double, 2> {
     static __device__ __forceinline__ void st(double *p, const double v[2], float) {
         *reinterpret_cast<double2 *>(p) = make_double2(v[0], v[1]);
     }
-    static __device__ __forceinline__ void st_tail(double *p, const double v[2], float) { p[1] = v[1]; }
-    static __device__ __forceinline__ void st_head(double *p, const double v[2], float) { p[0] = v[0]; }
 };
 template <> struct VecIO<__half, 4> {
     // same rounding as the scalar path: exact widening, then one multiply;
@@ -269,14 +257,6 @@ template <> struct VecIO<__half, 4> {
         t.x = *reinterpret_cast<const unsigned *>(&a);
         t.y = *reinterpret_cast<const unsigned *>(&b);
         *reinterpret_cast<uint2 *>(p) = t;
-    }
-    static __device__ __forceinline__ void st_tail(__half *p, const float v[4], float scale) {
-        p[1] = __float2half_rn(v[1] * scale);
-        *reinterpret_cast<__half2 *>(p + 2) = pack(v[2], v[3], scale);
-    }
-    static __device__ __forceinline__ void st_head(__half *p, const float v[4], float scale) {
-        *reinterpret_cast<__half2 *>(p) = pack(v[0], v[1], scale);
-        p[2] = __float2half_rn(v[2] * scale);
     }
 };
 
@@ -309,24 +289,17 @@ __device__ __forceinline__ VCell make_vcell(const Inst &I, int x0, int y, int la
     return c;
 }
 
-// Gather of direction k into g[j][k] for the thread's NV cells (see load_one
-// for the scalar form of both parities).  Every lane executes the shuffles.
+// Pull of direction k into g[j][k] for the thread's NV cells (see pull_one
+// for the scalar form).  Every lane executes the shuffles.
 template <int k, class S, int NV, class R>
-__device__ __forceinline__ void vload_one(const S *__restrict__ A, const Inst &I, const VCell &C, int parity,
-                                          R g[NV][9]) {
+__device__ __forceinline__ void vload_one(const S *__restrict__ A, const Inst &I, const VCell &C, R g[NV][9]) {
     constexpr int cx = Q<k>::cx, cy = Q<k>::cy, o = Q<k>::opp;
     constexpr int G = kTileX / NV;
     R v[NV];
-    if (parity == 0) {
-        if (C.valid) VecIO<S, NV>::ld(A + (k * I.plane32 + C.r0 + C.x0), I.inv_scale[k], v);
-#pragma unroll
-        for (int j = 0; j < NV; ++j) g[j][k] = C.valid ? v[j] : (R)0;
-        return;
-    }
     const bool wall = (cy > 0 && C.bot) || (cy < 0 && C.top);
     const int row = wall ? C.r0 : (cy > 0 ? C.rm : (cy < 0 ? C.rp : C.r0));
     // scale[k] == scale[opp k]: one factor serves both planes
-    if (C.valid) VecIO<S, NV>::ld(A + ((wall ? k : o) * I.plane32 + row + C.x0), I.inv_scale[k], v);
+    if (C.valid) VecIO<S, NV>::ld(A + ((wall ? o : k) * I.plane32 + row + C.x0), I.inv_scale[k], v);
     else {
 #pragma unroll
         for (int j = 0; j < NV; ++j) v[j] = (R)0;
@@ -344,94 +317,52 @@ __device__ __forceinline__ void vload_one(const S *__restrict__ A, const Inst &I
 #pragma unroll
         for (int j = 0; j < NV; ++j) g[j][k] = v[j];
     } else if constexpr (cx > 0) {
-        if (C.left && C.valid) nb = (R)Store<S>::ld(A + (o * I.plane32 + row + C.xm), I.inv_scale[o]);
+        if (C.left && C.valid) nb = (R)Store<S>::ld(A + (k * I.plane32 + row + C.xm), I.inv_scale[k]);
         g[0][k] = nb;
 #pragma unroll
         for (int j = 1; j < NV; ++j) g[j][k] = v[j - 1];
     } else {
-        if (C.right && C.valid) nb = (R)Store<S>::ld(A + (o * I.plane32 + row + C.xp), I.inv_scale[o]);
+        if (C.right && C.valid) nb = (R)Store<S>::ld(A + (k * I.plane32 + row + C.xp), I.inv_scale[k]);
 #pragma unroll
         for (int j = 0; j < NV - 1; ++j) g[j][k] = v[j + 1];
         g[NV - 1][k] = nb;
     }
 }
 
-// Scatter of direction k (see store_one for the scalar form).
+// Aligned store of the post-collision populations of direction k.
 template <int k, class S, int NV, class R>
-__device__ __forceinline__ void vstore_one(S *__restrict__ A, const Inst &I, const VCell &C, int parity,
-                                           const R g[NV][9]) {
-    constexpr int cx = Q<k>::cx, cy = Q<k>::cy, o = Q<k>::opp;
-    constexpr int G = kTileX / NV;
-    R v[NV];
-    if (parity == 0) {
-        if (!C.valid) return;
-#pragma unroll
-        for (int j = 0; j < NV; ++j) v[j] = g[j][k];
-        VecIO<S, NV>::st(A + (o * I.plane32 + C.r0 + C.x0), v, I.scale[o]);
-        return;
-    }
-    // the results shifted by c_kx within the vector, the neighbour's in the gap
-    if constexpr (cx > 0) {
-        v[0] = __shfl_up_sync(0xffffffffu, g[NV - 1][k], 1, G);
-#pragma unroll
-        for (int j = 1; j < NV; ++j) v[j] = g[j - 1][k];
-    } else if constexpr (cx < 0) {
-        v[NV - 1] = __shfl_down_sync(0xffffffffu, g[0][k], 1, G);
-#pragma unroll
-        for (int j = 0; j < NV - 1; ++j) v[j] = g[j + 1][k];
-    }
+__device__ __forceinline__ void vstore_one(S *__restrict__ D, const Inst &I, const VCell &C, const R g[NV][9]) {
     if (!C.valid) return;
-    const bool wall = (cy > 0 && C.top) || (cy < 0 && C.bot);
-    if (wall) {
-        const R b = bb_term<R>(I, cy > 0 ? 1 : 0, k);
+    R v[NV];
 #pragma unroll
-        for (int j = 0; j < NV; ++j) v[j] = g[j][k] - b;
-        VecIO<S, NV>::st(A + (o * I.plane32 + C.r0 + C.x0), v, I.scale[o]);
-        return;
-    }
-    const int row = cy > 0 ? C.rp : (cy < 0 ? C.rm : C.r0);
-    S *p = A + (k * I.plane32 + row + C.x0);
-    if constexpr (cx == 0) {
-#pragma unroll
-        for (int j = 0; j < NV; ++j) v[j] = g[j][k];
-        VecIO<S, NV>::st(p, v, I.scale[k]);
-    } else if constexpr (cx > 0) {
-        if (C.left) VecIO<S, NV>::st_tail(p, v, I.scale[k]);
-        else VecIO<S, NV>::st(p, v, I.scale[k]);
-        if (C.right) Store<S>::st(A + (k * I.plane32 + row + C.xp), g[NV - 1][k], I.scale[k]);
-    } else {
-        if (C.right) VecIO<S, NV>::st_head(p, v, I.scale[k]);
-        else VecIO<S, NV>::st(p, v, I.scale[k]);
-        if (C.left) Store<S>::st(A + (k * I.plane32 + row + C.xm), g[0][k], I.scale[k]);
-    }
+    for (int j = 0; j < NV; ++j) v[j] = g[j][k];
+    VecIO<S, NV>::st(D + (k * I.plane32 + C.r0 + C.x0), v, I.scale[k]);
 }
 
 template <class S, int NV, class R>
-__device__ __forceinline__ void vload_pops(const S *__restrict__ A, const Inst &I, const VCell &C, int parity,
-                                           R g[NV][9]) {
-    vload_one<0, S, NV>(A, I, C, parity, g);
-    vload_one<1, S, NV>(A, I, C, parity, g);
-    vload_one<2, S, NV>(A, I, C, parity, g);
-    vload_one<3, S, NV>(A, I, C, parity, g);
-    vload_one<4, S, NV>(A, I, C, parity, g);
-    vload_one<5, S, NV>(A, I, C, parity, g);
-    vload_one<6, S, NV>(A, I, C, parity, g);
-    vload_one<7, S, NV>(A, I, C, parity, g);
-    vload_one<8, S, NV>(A, I, C, parity, g);
+__device__ __forceinline__ void vload_pops(const S *__restrict__ A, const Inst &I, const VCell &C, R g[NV][9]) {
+    vload_one<0, S, NV>(A, I, C, g);
+    vload_one<1, S, NV>(A, I, C, g);
+    vload_one<2, S, NV>(A, I, C, g);
+    vload_one<3, S, NV>(A, I, C, g);
+    vload_one<4, S, NV>(A, I, C, g);
+    vload_one<5, S, NV>(A, I, C, g);
+    vload_one<6, S, NV>(A, I, C, g);
+    vload_one<7, S, NV>(A, I, C, g);
+    vload_one<8, S, NV>(A, I, C, g);
 }
 
 template <class S, int NV, class R>
-__device__ __forceinline__ void vstore_pops(S *__restrict__ A, const Inst &I, const VCell &C, int parity,
-                                            const R g[NV][9]) {
-    vstore_one<0, S, NV>(A, I, C, parity, g);
-    vstore_one<1, S, NV>(A, I, C, parity, g);
-    vstore_one<2, S, NV>(A, I, C, parity, g);
-    vstore_one<3, S, NV>(A, I, C, parity, g);
-    vstore_one<4, S, NV>(A, I, C, parity, g);
-    vstore_one<5, S, NV>(A, I, C, parity, g);
-    vstore_one<6, S, NV>(A, I, C, parity, g);
-    vstore_one<7, S, NV>(A, I, C, parity, g);
-    vstore_one<8, S, NV>(A, I, C, parity, g);
+__device__ __forceinline__ void vstore_pops(S *__restrict__ A, const Inst &I, const VCell &C, const R g[NV][9]) {
+    vstore_one<0, S, NV>(A, I, C, g);
+    vstore_one<1, S, NV>(A, I, C, g);
+    vstore_one<2, S, NV>(A, I, C, g);
+    vstore_one<3, S, NV>(A, I, C, g);
+    vstore_one<4, S, NV>(A, I, C, g);
+    vstore_one<5, S, NV>(A, I, C, g);
+    vstore_one<6, S, NV>(A, I, C, g);
+    vstore_one<7, S, NV>(A, I, C, g);
+    vstore_one<8, S, NV>(A, I, C, g);
 }
 
 // One tile with (32 / NV) x 8 threads; thread (tx, ty) owns cells
@@ -450,16 +381,17 @@ __device__ __forceinline__ void lattice_tile_vec(const Inst &I, S *__restrict__ 
     const int y = by * kTileY + threadIdx.y;
     const int tile = I.tile_base + by * I.ntx + bx;
     const int W = I.mask_words;
-    S *A = pool + I.pop_off;
+    const S *Asrc = pop_buffer(pool, I, parity);
+    S *Adst = pop_buffer(pool, I, parity ^ 1);
     const VCell C = make_vcell<NV>(I, x0, y, threadIdx.x);
     R g[NV][9];
-    if (early_load) vload_pops<S, NV>(A, I, C, parity, g);
+    if (early_load) vload_pops<S, NV>(Asrc, I, C, g);
     const bool cold = tile_cold_early(mask_prev + tile * W, W, early_cold, lead);
     if (!cold) pdl_wait();
     pdl_trigger();
     if (threadIdx.x == 0 && threadIdx.y == 0)
         for (int w = 0; w < W; ++w) mask_clear[tile * W + w] = 0u;
-    if (!early_load) vload_pops<S, NV>(A, I, C, parity, g);
+    if (!early_load) vload_pops<S, NV>(Asrc, I, C, g);
     if (C.valid) {
         const unsigned *m = mask_read + tile * W;
         unsigned any = 0u;
@@ -472,7 +404,7 @@ __device__ __forceinline__ void lattice_tile_vec(const Inst &I, S *__restrict__ 
             collide<R>(g[j], Fx, Fy, s_nu, s_e, s_eps, s_q);
         }
     }
-    vstore_pops<S, NV>(A, I, C, parity, g);
+    vstore_pops<S, NV>(Adst, I, C, g);
 }
 
 template <class S>
@@ -520,23 +452,24 @@ __global__ void __launch_bounds__(kTileX / VecWidth<S>::value * kTileY, BatchVec
 }
 
 // Equilibrium start: f_k = f_k^eq(rho = 1, u = (u_wall(y), 0)) with the
-// linear wall profile, or the rest state; stored as deviations for parity 0.
+// linear wall profile, or the rest state; placed (as deviations) in buffer 0
+// so that the first step pulls exactly these values.
 template <class S>
 __global__ void k_init(const Inst I, S *__restrict__ pool, int couette) {
+    using R = typename Real<S>::type;
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
     if (x >= I.nx || y >= I.ny) return;
     const double ux = couette ? I.u_bot + (I.u_top - I.u_bot) * (y + 0.5) / I.ny : 0.0;
-    S *A = pool + I.pop_off;
     const int cxs[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
     const double ws[9] = {4.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0,
                           1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
+    R g[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
         const double cu = cxs[k] * ux;
-        const double gk = ws[k] * (3.0 * cu + 4.5 * cu * cu - 1.5 * ux * ux);
-        Store<S>::st(A + (int64_t)k * I.plane + (int64_t)y * I.pitch + x,
-                     (typename Real<S>::type)gk, I.scale[k]);
+        g[k] = (R)(ws[k] * (3.0 * cu + 4.5 * cu * cu - 1.5 * ux * ux));
     }
+    place_pops<S, R>(pop_buffer(pool, I, 0), I, make_cell(I, x, y), g);
 }
 
 // Force density of Eq. 4 at a cell from the beads marked in its tile.
@@ -568,7 +501,7 @@ __global__ void k_fields(const Inst I, const S *__restrict__ pool, const BeadTab
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
     if (x >= I.nx || y >= I.ny) return;
     double g[9];
-    load_pops<S, double>(pool + I.pop_off, I, make_cell(I, x, y), parity, g);
+    pull_pops<S, double>(pop_buffer(pool, I, parity), I, make_cell(I, x, y), g);
     double dr = 0.0;
 #pragma unroll
     for (int k = 0; k < 9; ++k) dr += g[k];
@@ -602,7 +535,7 @@ __global__ void __launch_bounds__(kFlowThreads)
         const double ph = phi_f64(I, i + 0.5, j + 0.5, Rx, Ry);
         if (ph == 0.0) continue;
         double g[9];
-        load_pops<S, double>(pool + I.pop_off, I, make_cell(I, i, j), parity, g);
+        pull_pops<S, double>(pop_buffer(pool, I, parity), I, make_cell(I, i, j), g);
         double dr = 0.0;
 #pragma unroll
         for (int k = 0; k < 9; ++k) dr += g[k];
@@ -640,7 +573,7 @@ __global__ void k_read_pops(const Inst I, const S *__restrict__ pool, int parity
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
     if (x >= I.nx || y >= I.ny) return;
     double g[9];
-    load_pops<S, double>(pool + I.pop_off, I, make_cell(I, x, y), parity, g);
+    pull_pops<S, double>(pop_buffer(pool, I, parity), I, make_cell(I, x, y), g);
     const double ws[9] = {4.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0,
                           1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
     const int64_t n = (int64_t)I.nx * I.ny, c = (int64_t)y * I.nx + x;
@@ -648,42 +581,19 @@ __global__ void k_read_pops(const Inst I, const S *__restrict__ pool, int parity
     for (int k = 0; k < 9; ++k) f[k * n + c] = g[k] + ws[k];
 }
 
-// Inverse of the parity read: place the deviations of a given state where
-// the next step will gather them (bounce-back term removed at the walls).
-template <int k, class S>
-__device__ __forceinline__ void write_one(S *A, const Inst &I, const Cell &C, int parity, double gk) {
-    using R = typename Real<S>::type;
-    constexpr int cx = Q<k>::cx, cy = Q<k>::cy, o = Q<k>::opp;
-    if (parity == 0) {
-        Store<S>::st(A + (k * I.plane32 + C.r0 + C.x), (R)gk, I.scale[k]);
-        return;
-    }
-    const bool wall = (cy > 0 && C.bot) || (cy < 0 && C.top);
-    if (wall) {
-        Store<S>::st(A + (k * I.plane32 + C.r0 + C.x), (R)(gk - I.bbd[cy > 0 ? 0 : 1][k]), I.scale[k]);
-    } else {
-        const int rs = cy > 0 ? C.rm : (cy < 0 ? C.rp : C.r0);
-        const int xs = cx > 0 ? C.xm : (cx < 0 ? C.xp : C.x);
-        Store<S>::st(A + (o * I.plane32 + rs + xs), (R)gk, I.scale[o]);
-    }
-}
-
+// Place a given state (populations f) where the next step pulls it from.
 template <class S>
 __global__ void k_write_pops(const Inst I, S *__restrict__ pool, int parity, const double *__restrict__ f) {
+    using R = typename Real<S>::type;
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
     if (x >= I.nx || y >= I.ny) return;
-    S *A = pool + I.pop_off;
-    const Cell C = make_cell(I, x, y);
     const int64_t n = (int64_t)I.nx * I.ny, c = (int64_t)y * I.nx + x;
-    write_one<0>(A, I, C, parity, f[0 * n + c] - Q<0>::w);
-    write_one<1>(A, I, C, parity, f[1 * n + c] - Q<1>::w);
-    write_one<2>(A, I, C, parity, f[2 * n + c] - Q<2>::w);
-    write_one<3>(A, I, C, parity, f[3 * n + c] - Q<3>::w);
-    write_one<4>(A, I, C, parity, f[4 * n + c] - Q<4>::w);
-    write_one<5>(A, I, C, parity, f[5 * n + c] - Q<5>::w);
-    write_one<6>(A, I, C, parity, f[6 * n + c] - Q<6>::w);
-    write_one<7>(A, I, C, parity, f[7 * n + c] - Q<7>::w);
-    write_one<8>(A, I, C, parity, f[8 * n + c] - Q<8>::w);
+    const double ws[9] = {4.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0,
+                          1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
+    R g[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) g[k] = (R)(f[k * n + c] - ws[k]);
+    place_pops<S, R>(pop_buffer(pool, I, parity), I, make_cell(I, x, y), g);
 }
 
 constexpr int kDiagThreads = 256;
@@ -698,7 +608,7 @@ __global__ void __launch_bounds__(kDiagThreads)
          c += (int64_t)gridDim.x * blockDim.x) {
         const int y = (int)(c / I.nx), x = (int)(c - (int64_t)y * I.nx);
         double g[9];
-        load_pops<S, double>(pool + I.pop_off, I, make_cell(I, x, y), parity, g);
+        pull_pops<S, double>(pop_buffer(pool, I, parity), I, make_cell(I, x, y), g);
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
             m += g[k];

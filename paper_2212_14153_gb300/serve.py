@@ -34,11 +34,12 @@ class Request:
 
 
 def state_bytes(cfg: dict, precision: int) -> int:
-    """Device bytes of one instance's populations (9 planes, 128-byte rows)."""
+    """Device bytes of one instance's populations (two buffers of 9 planes,
+    128-byte rows)."""
     es = {0: 8, 1: 4, 2: 2}[precision]
     align = 128 // es
     pitch = (int(cfg["nx"]) + align - 1) // align * align
-    return 9 * pitch * int(cfg["ny"]) * es
+    return 2 * 9 * pitch * int(cfg["ny"]) * es
 
 
 class Server:

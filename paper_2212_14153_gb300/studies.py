@@ -155,7 +155,7 @@ def internal_flow(a: float = 8.0, precision: int = 1, points=INTERNAL_FLOW, visc
     steps = int(viscous_times * L * L / nu)
     cells = sum(c["nx"] * c["ny"] for c in cfgs)
     es = {0: 8, 1: 4, 2: 2}[precision]
-    b = fpd.Batch(precision, len(cfgs), 9 * es * (cells + 64 * L * len(cfgs)) + 4096 * len(cfgs), len(cfgs))
+    b = fpd.Batch(precision, len(cfgs), 18 * es * (cells + 64 * L * len(cfgs)) + 4096 * len(cfgs), len(cfgs))
     slots = [b.add(dict(c, precision=precision), steps) for c in cfgs]
     b.run(int(0.9 * steps))
     V_early = [b.beads(s)[1][0, 0] for s in slots]

@@ -209,7 +209,7 @@ def measure_periods(configs: list[dict], max_steps: int, sample_every: int = 200
     W = stuck_window or max(sample_every, max_steps // 5)
     cells = sum(int(c["nx"]) * int(c["ny"]) for c in configs)
     es = {0: 8, 1: 4, 2: 2}[precision]
-    pool = 9 * es * (cells + 64 * sum(int(c["ny"]) for c in configs)) + 4096 * len(configs)
+    pool = 18 * es * (cells + 64 * sum(int(c["ny"]) for c in configs)) + 4096 * len(configs)
     nbeads = sum(int(c["n_beads"]) * int(c["n_fibers"]) for c in configs)
     b = fpd.Batch(precision, len(configs), pool, nbeads, stream)
     slots = [b.add(dict(c, precision=precision), max_steps) for c in configs]
@@ -264,7 +264,7 @@ def run_tracks(configs: list[dict], steps: int, sample_every: int, precision: in
     l0 = [2.0 * c["a"] for c in configs]
     cells = sum(int(c["nx"]) * int(c["ny"]) for c in configs)
     es = {0: 8, 1: 4, 2: 2}[precision]
-    pool = 9 * es * (cells + 64 * sum(int(c["ny"]) for c in configs)) + 4096 * len(configs)
+    pool = 18 * es * (cells + 64 * sum(int(c["ny"]) for c in configs)) + 4096 * len(configs)
     nbeads = sum(int(c["n_beads"]) * int(c["n_fibers"]) for c in configs)
     b = fpd.Batch(precision, len(configs), pool, nbeads, stream)
     slots = [b.add(dict(c, precision=precision), steps) for c in configs]

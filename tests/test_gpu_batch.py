@@ -121,7 +121,7 @@ def test_staggered_admission_and_slot_reuse(fpd):
 
 def test_admission_limits(fpd):
     cfg = wl.couette_only(64, 64, precision=1)
-    pool = 9 * 64 * 64 * 4 * 2 + 4096          # room for two such lattices
+    pool = 2 * 9 * 64 * 64 * 4 * 2 + 4096      # room for two such lattices (two buffers each)
     b = fpd.Batch(1, max_slots=4, pool_bytes=pool, max_beads=8)
     b.add(cfg, 5)
     b.add(cfg, 5)

@@ -101,6 +101,7 @@ def test_memory_cap_limits_residency(fake):
 
 
 def test_state_bytes_pads_rows_to_128_bytes():
-    assert serve.state_bytes(dict(nx=80, ny=40), 1) == 9 * 96 * 40 * 4
-    assert serve.state_bytes(dict(nx=80, ny=40), 2) == 9 * 128 * 40 * 2
-    assert serve.state_bytes(dict(nx=64, ny=10), 0) == 9 * 64 * 10 * 8
+    # two buffers of 9 planes
+    assert serve.state_bytes(dict(nx=80, ny=40), 1) == 2 * 9 * 96 * 40 * 4
+    assert serve.state_bytes(dict(nx=80, ny=40), 2) == 2 * 9 * 128 * 40 * 2
+    assert serve.state_bytes(dict(nx=64, ny=10), 0) == 2 * 9 * 64 * 10 * 8
