@@ -97,6 +97,10 @@ int derive(fpd_sim *s, const fpd_params &p) {
     if (9 * I.plane > (int64_t)INT32_MAX)
         return fail(nullptr, FPD_EINVAL, "lattice of %d x %d cells exceeds 32-bit element offsets", p.nx, p.ny);
     I.plane32 = (int32_t)I.plane;
+    {
+        static const int cx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1}, cy[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+        for (int k = 0; k < 9; ++k) I.pull_off[k] = k * I.plane32 - cy[k] * I.pitch - cx[k];
+    }
     I.pop_off = 0;
     I.ntx = (p.nx + fpd::kTileX - 1) / fpd::kTileX;
     I.nty = (p.ny + fpd::kTileY - 1) / fpd::kTileY;

@@ -1,5 +1,5 @@
 // fpd_device.cuh -- device-side building blocks of the FPD-MRT step:
-// D2Q9 constants, the in-place (AA) population access with half-way
+// D2Q9 constants, the two-buffer pull population access with half-way
 // moving-wall bounce-back, the bead support profile of Eq. 2 and the MRT
 // collision with Guo forcing written out in moment space.
 #pragma once
@@ -61,6 +61,10 @@ struct Inst {
     float f_inv_ny;
     double ext_fx, ext_fy;
     float f_ext_fx, f_ext_fy;
+    // k plane - c_ky pitch - c_kx: element offset of the pull source of
+    // direction k from a cell's own element in plane 0, for cells with no
+    // wall and no periodic wrap among their neighbours
+    int32_t pull_off[9];
 };
 
 // phi(y) of the sandwich layers (Eq. 14) at height y
@@ -201,11 +205,19 @@ __device__ __forceinline__ void pull_pops(const S *__restrict__ A, const Inst &I
     pull_one<8>(A, I, C, g[8]);
 }
 
-// Post-collision populations of cell C, stored at the cell (aligned).
+// Pull of all nine directions for a cell with no wall and no periodic wrap
+// among its neighbours; p points at the cell's element in plane 0.
 template <class S, class R>
-__device__ __forceinline__ void put_pops(S *__restrict__ D, const Inst &I, const Cell &C, const R g[9]) {
+__device__ __forceinline__ void pull_inner(const S *__restrict__ p, const Inst &I, R g[9]) {
 #pragma unroll
-    for (int k = 0; k < 9; ++k) Store<S>::st(D + (k * I.plane32 + C.r0 + C.x), g[k], I.scale[k]);
+    for (int k = 0; k < 9; ++k) g[k] = (R)Store<S>::ld(p + I.pull_off[k], I.inv_scale[k]);
+}
+
+// Post-collision populations stored at the cell whose plane-0 element p is.
+template <class S, class R>
+__device__ __forceinline__ void put_at(S *__restrict__ p, const Inst &I, const R g[9]) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Store<S>::st(p + k * I.plane32, g[k], I.scale[k]);
 }
 
 template <class S, class R>

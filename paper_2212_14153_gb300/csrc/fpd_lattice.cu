@@ -8,10 +8,12 @@
 // can reach the tile; a tile whose mask is empty ("cold") uses the fluid
 // rates and the uniform body force, a "hot" tile evaluates phi_i, the
 // viscosity of Eq. 1 and the spread force of Eq. 4 per cell, visiting the
-// marked beads in bead order.  Every cell gathers its 9 populations (AA
-// pattern, bounce-back at the walls), collides (MRT + Guo) and scatters them
-// to the other population buffer.  No block-wide barrier: each thread reads
-// the tile's mask.
+// marked beads in bead order.  Every cell pulls its 9 populations from the
+// current buffer (shifted reads, bounce-back at the walls), collides (MRT +
+// Guo) and stores them at the cell in the other buffer.  Tiles with no wall
+// and no periodic wrap among their cells' neighbours address every source
+// with one precomputed offset per direction.  No block-wide barrier: each
+// thread reads the tile's mask.
 #include <cuda_fp16.h>
 
 #include <type_traits>
@@ -122,8 +124,10 @@ __device__ __forceinline__ bool tile_cold_early(const unsigned *__restrict__ pre
 
 // One tile of the sweep: tile (bx, by) of instance I at the instance's step
 // parity, on kTileX x (kTileY / CY) threads; thread (tx, ty) owns the CY
-// cells (x, y0 + ty + k kTileY / CY), k < CY, of its column.
-template <class S, int CY>
+// cells (x, y0 + ty + k kTileY / CY), k < CY, of its column.  kInner: tiles
+// away from walls and periodic edges use the precomputed pull offsets (the
+// batched sweep keeps the general form, which fits it in 32 registers).
+template <class S, int CY, bool kInner>
 __device__ __forceinline__ void lattice_tile(const Inst &I, S *__restrict__ pool, const BeadTab &tab,
                                              const unsigned *__restrict__ mask_read,
                                              const unsigned *__restrict__ mask_prev, unsigned *__restrict__ mask_clear,
@@ -136,34 +140,39 @@ __device__ __forceinline__ void lattice_tile(const Inst &I, S *__restrict__ pool
     const int W = I.mask_words;
     const S *Asrc = pop_buffer(pool, I, parity);
     S *Adst = pop_buffer(pool, I, parity ^ 1);
+    // every cell of the tile and its neighbours lie inside the lattice
+    const bool inner = kInner && bx > 0 && by > 0 && (bx + 1) * kTileX < I.nx && (by + 1) * kTileY < I.ny;
     int y[CY];
     bool valid[CY];
-    Cell C[CY];
+    Cell C[CY];  // general form only
     R g[CY][9];
 #pragma unroll
     for (int k = 0; k < CY; ++k) {
         y[k] = by * kTileY + ty + k * RY;
         valid[k] = x < I.nx && y[k] < I.ny;
-        C[k] = make_cell(I, x, valid[k] ? y[k] : 0);
+        if constexpr (!kInner) C[k] = make_cell(I, x, valid[k] ? y[k] : 0);
     }
+    auto pull = [&]() {
+        if (inner) {
+            const S *p = Asrc + (y[0] * I.pitch + x);
+#pragma unroll
+            for (int k = 0; k < CY; ++k) pull_inner<S, R>(p + k * RY * I.pitch, I, g[k]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < CY; ++k)
+                if (valid[k]) pull_pops<S, R>(Asrc, I, kInner ? make_cell(I, x, y[k]) : C[k], g[k]);
+        }
+    };
     // populations come from the previous sweep; when the bead phase runs
     // between the two sweeps they may be loaded before waiting on it
-    if (early_load) {
-#pragma unroll
-        for (int k = 0; k < CY; ++k)
-            if (valid[k]) pull_pops<S, R>(Asrc, I, C[k], g[k]);
-    }
+    if (early_load) pull();
     const bool cold = tile_cold_early(mask_prev + tile * W, W, early_cold, lead);
     if (!cold) pdl_wait();
     pdl_trigger();
     if (tx == 0 && ty == 0)  // a mask of two steps back, for the next bead phase
         for (int w = 0; w < W; ++w) mask_clear[tile * W + w] = 0u;
     if (!valid[0]) return;  // cells further down the column are invalid too
-    if (!early_load) {
-#pragma unroll
-        for (int k = 0; k < CY; ++k)
-            if (valid[k]) pull_pops<S, R>(Asrc, I, C[k], g[k]);
-    }
+    if (!early_load) pull();
     const unsigned *m = mask_read + tile * W;
     unsigned any = 0u;
     if (!cold)
@@ -174,7 +183,7 @@ __device__ __forceinline__ void lattice_tile(const Inst &I, S *__restrict__ pool
         R Fx, Fy, s_nu, s_e, s_eps, s_q;
         cell_overlay<R>(I, tab, m, W, any, x, y[k], Fx, Fy, s_nu, s_e, s_eps, s_q);
         collide<R>(g[k], Fx, Fy, s_nu, s_e, s_eps, s_q);
-        put_pops<S, R>(Adst, I, C[k], g[k]);
+        put_at<S, R>(Adst + (kInner ? y[k] * I.pitch + x : C[k].r0 + C[k].x), I, g[k]);
     }
 }
 
@@ -183,8 +192,8 @@ __global__ void __launch_bounds__(kTileX *kTileY / CY)
     k_lattice(const Inst I, S *__restrict__ pool, const BeadTab tab, const unsigned *__restrict__ mask_read,
               const unsigned *__restrict__ mask_prev, unsigned *__restrict__ mask_clear, const int parity,
               const int early_load, const int early_cold) {
-    lattice_tile<S, CY>(I, pool, tab, mask_read, mask_prev, mask_clear, blockIdx.x, blockIdx.y, parity, early_load,
-                        early_cold, (blockIdx.x | blockIdx.y) == 0, threadIdx.x, threadIdx.y);
+    lattice_tile<S, CY, true>(I, pool, tab, mask_read, mask_prev, mask_clear, blockIdx.x, blockIdx.y, parity,
+                              early_load, early_cold, (blockIdx.x | blockIdx.y) == 0, threadIdx.x, threadIdx.y);
 }
 
 // Batched sweep over a packed tile list: tiles[t] = (instance slot,
@@ -206,8 +215,8 @@ __global__ void __launch_bounds__(kTileX *kTileY / CY)
     }
     __syncthreads();
     const int parity = gparity ^ sI.par_xor;
-    lattice_tile<S, CY>(sI, pool, parity ? tab1 : tab0, mask_read, mask_prev, mask_clear, t.y & 0xffff, t.y >> 16,
-                        parity, early_load, early_cold, blockIdx.x == 0, threadIdx.x, threadIdx.y);
+    lattice_tile<S, CY, false>(sI, pool, parity ? tab1 : tab0, mask_read, mask_prev, mask_clear, t.y & 0xffff,
+                               t.y >> 16, parity, early_load, early_cold, blockIdx.x == 0, threadIdx.x, threadIdx.y);
 }
 
 // ------------------------------------------------ vectorised sweep (variant 2)
@@ -445,9 +454,9 @@ __global__ void __launch_bounds__(kTileX / VecWidth<S>::value * kTileY, BatchVec
                             t.y >> 16, parity, early_load, early_cold, blockIdx.x == 0);
     } else {
         const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-        lattice_tile<S, NV>(sI, pool, parity ? tab1 : tab0, mask_read, mask_prev, mask_clear, t.y & 0xffff,
-                            t.y >> 16, parity, early_load, early_cold, blockIdx.x == 0, tid % kTileX,
-                            tid / kTileX);
+        lattice_tile<S, NV, false>(sI, pool, parity ? tab1 : tab0, mask_read, mask_prev, mask_clear, t.y & 0xffff,
+                                   t.y >> 16, parity, early_load, early_cold, blockIdx.x == 0, tid % kTileX,
+                                   tid / kTileX);
     }
 }
 
