@@ -11,6 +11,11 @@ constexpr int kTileX = 32;       // lattice tile: 32 x 8 cells, one thread each
 constexpr int kTileY = 8;
 constexpr int kMaxBeads = 256;   // beads per instance (shared-memory tables)
 constexpr int kBeadThreads = 128;  // per bead CTA: more beads resident at once (batched sweep +9 %)
+constexpr int kBeadThreadsFew = 256;  // per bead CTA when the beads fit on the SMs one per SM
+constexpr int kBeadLanes = 256;  // virtual lanes of the per-bead sums (any CTA size gives the same bits)
+static_assert(kBeadLanes % kBeadThreads == 0 && kBeadLanes % kBeadThreadsFew == 0 &&
+                  kBeadLanes / kBeadThreads <= 2 && kBeadLanes / kBeadThreadsFew <= 2,
+              "a bead thread holds one or two virtual lanes");
 constexpr int kGraphSteps = 32;  // time steps per captured graph chunk
 // Tile-mask buffers, used in rotation: the bead phase of step t marks buffer
 // t % kMaskBufs; the sweep of step t reads it (hot tiles) and buffer
@@ -54,8 +59,8 @@ cudaError_t launch_lattice(int precision, const Inst *inst_d, const Inst &inst_h
 // (initialisation).  Every bead ORs its bit into the mask of each lattice
 // tile its support reaches (mask_write, zeroed beforehand).
 // pdl = 1 launches the bead phase as a programmatic dependent of the
-// previous sweep: its prologue (instance record, neighbour list, support
-// box, all from the previous bead table) overlaps the sweep's tail.
+// previous sweep: it waits for that sweep first thing and releases the next
+// sweep at once, so the next sweep's unmarked tiles overlap the whole phase.
 cudaError_t launch_beads(int precision, const Inst *inst_d, const int2 *blist, int nb_total,
                          const void *pool, BeadTab tab0, BeadTab tab1, unsigned *mask_write, int gparity,
                          int advance, unsigned *counters, int pdl, cudaStream_t st);

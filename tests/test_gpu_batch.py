@@ -70,6 +70,28 @@ def test_batch_equals_alone_bit_for_bit(fpd, precision):
     b.close()
 
 
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_batch_longer_than_the_sms_equals_alone(fpd, precision):
+    # a bead list longer than the GPU's SM count runs in narrower bead CTAs
+    # than an instance alone; the per-bead sums are taken over the same
+    # virtual lanes either way, so every instance still agrees bit for bit
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    rng = np.random.default_rng(70 + precision)
+    per = 16                                    # beads per instance (2 fibers x 8)
+    n_inst = sms // per + 2
+    assert n_inst * per > sms >= per
+    cases = [wl.random_fiber(rng, 80, 48, n_beads=8, a=2.0, xi=1.0, n_fibers=2, precision=precision)
+             for _ in range(n_inst)]
+    b = fpd.Batch(precision, max_slots=n_inst, pool_bytes=128 << 20, max_beads=per * n_inst)
+    slots = [b.add(c, 12) for c in cases]
+    while b.run(1000):
+        pass
+    for c, s in zip(cases, slots):
+        _same((b.populations(s), b.beads(s)), _alone(fpd, c, 12))
+    b.close()
+
+
 @pytest.mark.parametrize("precision,tol", [(0, 1e-13), (1, 1e-5), (2, 1e-2)])
 def test_batch_vector_variant(fpd, precision, tol):
     # variant 2 in a batch: instances whose nx is a multiple of the vector
