@@ -211,6 +211,7 @@ def run_gpu(args, rank: int, world: int):
         bpc = 18 * STORE_BYTES[args.precision]
         lat_ms = kt["lattice_ms"] / max(kt["lattice_launches"], 1)
         achieved = bpc * cells / (lat_ms * 1e-3) / 1e9
+        step_gbs = bpc * cells * args.steps / (ms * 1e-3) / 1e9
         traffic = ncu_traffic(cfg["name"], args.precision, variant)
         gpu_launches = kt["lattice_launches"] + kt["bead_launches"]  # per timed region
         line = {
@@ -238,6 +239,9 @@ def run_gpu(args, rank: int, world: int):
                 "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
                 "kernel": "k_lattice", "kernel_ms": lat_ms, "peak_source": peaks["source"],
                 "bead_kernel_ms": kt["bead_ms"] / max(kt["bead_launches"], 1),
+                # the whole step (bead phase included) as a fraction of the
+                # roofline: bytes per cell update x cell updates per second
+                "step_achieved": round(step_gbs, 1), "step_frac": round(step_gbs / peaks["hbm_gbs"], 4),
             },
             "gpu_launches": gpu_launches,
             "e2e": {"value": round(e2e_mlups, 1), "unit": "MLUPS", "h2d_bytes_per_step": h2d_total / e2e_steps,
