@@ -398,12 +398,12 @@ def run_serve(args, rank: int, world: int):
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     build.build()
     out = []
-    probe = workloads.serving_requests(args.instances, 1.0, seed=5, steps_lo=args.serve_steps_lo,
+    probe = workloads.serving_requests(args.serve_requests, 1.0, seed=5, steps_lo=args.serve_steps_lo,
                                        steps_hi=args.serve_steps_hi, precision=args.precision)
     work = np.mean([r["nx"] * r["ny"] * r["steps"] for r in probe])
     capacity = args.capacity_mlups * 1e6 / work  # requests / s the batch can sustain
     for load in (0.5, 1.2):
-        reqs = workloads.serving_requests(args.instances, load * capacity, seed=5, steps_lo=args.serve_steps_lo,
+        reqs = workloads.serving_requests(args.serve_requests, load * capacity, seed=5, steps_lo=args.serve_steps_lo,
                                           steps_hi=args.serve_steps_hi, precision=args.precision)
         pool = sum(serve.state_bytes(r, args.precision) + 4096 for r in reqs)
         nbeads = sum(r["n_beads"] * r["n_fibers"] for r in reqs)
@@ -419,7 +419,7 @@ def run_serve(args, rank: int, world: int):
         "metric": "serving: p50/p99 time-to-result and aggregate MLUPS under Poisson arrivals",
         "value": round(out[0]["aggregate_mlups"], 1), "unit": "MLUPS", "n_gpus": 1,
         "higher_is_better": True, "dtype": {0: "f64", 1: "f32", 2: "f32"}[args.precision], "data": "synthetic",
-        "config": {"workload": "serving", "requests": args.instances,
+        "config": {"workload": "serving", "requests": args.serve_requests,
                    "steps_per_request": [args.serve_steps_lo, args.serve_steps_hi], "chunk": args.chunk,
                    "cap_bytes": args.cap_bytes, "capacity_mlups_assumed": args.capacity_mlups},
         "loads": out,
@@ -440,8 +440,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="two_fiber", choices=["two_fiber", "sweep", "serve"])
     ap.add_argument("--instances", type=int, default=512)
-    ap.add_argument("--serve-steps-lo", type=int, default=5000)
-    ap.add_argument("--serve-steps-hi", type=int, default=50000)
+    ap.add_argument("--serve-steps-lo", type=int, default=50000)
+    ap.add_argument("--serve-steps-hi", type=int, default=500000)
+    ap.add_argument("--serve-requests", type=int, default=128)
     ap.add_argument("--capacity-mlups", type=float, default=40000.0)
     ap.add_argument("--cap-bytes", type=int, default=150 << 30)
     ap.add_argument("--max-slots", type=int, default=512)
