@@ -112,6 +112,10 @@ struct fpd_batch {
     double cell_updates = 0.0;
     bool dirty = true;
     int variant = 0;  // lattice sweep variant
+    // captured chunks of kGraphSteps steps, one per starting mask buffer
+    // (global step mod kMaskBufs); valid until the next rebuild or tuning change
+    cudaGraphExec_t graph[fpd::kMaskBufs] = {};
+    cudaStream_t cap_stream = nullptr;
     double *scratch = nullptr;
     size_t scratch_bytes = 0;
     std::string err;
@@ -133,7 +137,22 @@ int bcuda(fpd_batch *b, cudaError_t e, const char *what) {
     return bfail(b, FPD_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
+// Destroys the captured step chunks (after the stream has drained them).
+void drop_bgraphs(fpd_batch *b) {
+    bool any = false;
+    for (auto g : b->graph) any = any || g;
+    if (!any) return;
+    cudaStreamSynchronize(b->stream);
+    for (auto &g : b->graph)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+}
+
 void free_batch(fpd_batch *b) {
+    drop_bgraphs(b);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     cudaFree(b->pool);
     cudaFree(b->tabmem);
     cudaFree(b->insts_d);
@@ -162,6 +181,8 @@ int ensure_bscratch(fpd_batch *b, size_t bytes) {
 // bead tables of newly admitted instances.
 int rebuild(fpd_batch *b) {
     cudaError_t e;
+    // launch sizes and buffers change: captured chunks are stale
+    drop_bgraphs(b);
     std::vector<int2> tiles;
     const int gp = (int)(b->gstep & 1);
     // words per tile mask: enough for the largest resident instance
@@ -373,6 +394,65 @@ int fpd_batch_add(fpd_batch *b, const fpd_params *p, int64_t n_steps, int32_t *s
     return FPD_OK;
 }
 
+namespace {
+
+// The launches of global step gstep on stream st: the bead phase (all beads,
+// or those of instances past their first step) and the batched sweep.
+int enqueue_bstep(fpd_batch *b, cudaStream_t st, int64_t gstep, bool any_first) {
+    const int gp = (int)(gstep & 1);
+    const int2 *blist = any_first ? b->beads_old_d : b->beads_all_d;
+    const int nbl = any_first ? b->n_old : b->n_all;
+    constexpr int M = fpd::kMaskBufs;
+    const size_t mstride = (size_t)b->tiles_cap * b->mask_words;
+    unsigned *mw = b->masks + (size_t)(gstep % M) * mstride;
+    // the previous buffer holds the previous bead phase's marks unless the
+    // masks were reset before this step
+    const fpd::SweepMasks mk{mw, b->masks + (size_t)((gstep + M - 1) % M) * mstride,
+                             b->masks + (size_t)((gstep + 1) % M) * mstride, gstep > b->rebuild_gstep ? 1 : 0};
+    cudaError_t e;
+    if (nbl > 0) {
+        e = fpd::launch_beads(b->precision, b->insts_d, blist, nbl, b->pool, b->tab[0], b->tab[1], mw, gp, 1,
+                              b->counters, 1, st);
+        if (e != cudaSuccess) return bcuda(b, e, "batched bead phase");
+    }
+    e = fpd::launch_lattice_batch(b->precision, b->insts_d, b->tiles_d, b->ntiles, b->pool, b->tab[0], b->tab[1], mk,
+                                  gp, nbl > 0 ? 1 : 0, b->variant, st);
+    if (e != cudaSuccess) return bcuda(b, e, "batched lattice sweep");
+    return FPD_OK;
+}
+
+// Capture kGraphSteps steps starting at a global step g > rebuild_gstep with
+// g % kMaskBufs == p (every instance past its first step) on a private
+// stream; the graph replays on the batch's stream.
+int capture_bchunk(fpd_batch *b, int p) {
+    cudaError_t e;
+    if (!b->cap_stream && (e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+        return bcuda(b, e, "capture stream");
+    // a start step with the same mask buffer and parity, past the last reset
+    int64_t g0 = b->rebuild_gstep + 1;
+    g0 += ((p - g0 % fpd::kMaskBufs) % fpd::kMaskBufs + fpd::kMaskBufs) % fpd::kMaskBufs;
+    if ((e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+        return bcuda(b, e, "begin capture");
+    int rc = FPD_OK;
+    for (int i = 0; i < fpd::kGraphSteps && rc == FPD_OK; ++i) rc = enqueue_bstep(b, b->cap_stream, g0 + i, false);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(b->cap_stream, &g);
+    if (rc != FPD_OK) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return bcuda(b, e, "end capture");
+    e = cudaGraphInstantiate(&b->graph[p], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        b->graph[p] = nullptr;
+        return bcuda(b, e, "graph instantiate");
+    }
+    return FPD_OK;
+}
+
+}  // namespace
+
 int fpd_batch_run(fpd_batch *b, int64_t max_steps, int64_t *steps_done) {
     if (!b) return FPD_EINVAL;
     if (steps_done) *steps_done = 0;
@@ -389,31 +469,25 @@ int fpd_batch_run(fpd_batch *b, int64_t max_steps, int64_t *steps_done) {
     if (nactive == 0 || chunk <= 0) return FPD_OK;
     int rc;
     if (b->dirty && (rc = rebuild(b)) != FPD_OK) return rc;
-    cudaError_t e;
-    for (int64_t t = 0; t < chunk; ++t) {
-        const int gp = (int)(b->gstep & 1);
+    for (int64_t t = 0; t < chunk;) {
         // on the first step after admissions the new instances skip the
         // bead advance (their table is the initial one)
         const bool any_first = b->n_old != b->n_all;
-        const int2 *blist = any_first ? b->beads_old_d : b->beads_all_d;
-        const int nbl = any_first ? b->n_old : b->n_all;
-        constexpr int M = fpd::kMaskBufs;
-        const size_t mstride = (size_t)b->tiles_cap * b->mask_words;
-        unsigned *mw = b->masks + (size_t)(b->gstep % M) * mstride;
-        // the previous buffer holds the previous bead phase's marks unless
-        // the masks were reset before this step
-        const fpd::SweepMasks mk{mw, b->masks + (size_t)((b->gstep + M - 1) % M) * mstride,
-                                 b->masks + (size_t)((b->gstep + 1) % M) * mstride,
-                                 b->gstep > b->rebuild_gstep ? 1 : 0};
-        if (nbl > 0) {
-            e = fpd::launch_beads(b->precision, b->insts_d, blist, nbl, b->pool, b->tab[0], b->tab[1], mw, gp, 1,
-                                  b->counters, 1, b->stream);
-            if (e != cudaSuccess) return bcuda(b, e, "batched bead phase");
+        // whole chunks of steps with every instance past its first step and
+        // the masks carried over from the previous step replay a captured
+        // graph (launch sizes and pointers fixed until the next rebuild)
+        if (!any_first && b->gstep > b->rebuild_gstep && chunk - t >= fpd::kGraphSteps) {
+            const int p = (int)(b->gstep % fpd::kMaskBufs);
+            if (!b->graph[p] && (rc = capture_bchunk(b, p)) != FPD_OK) return rc;
+            cudaError_t e = cudaGraphLaunch(b->graph[p], b->stream);
+            if (e != cudaSuccess) return bcuda(b, e, "batched step graph");
+            b->gstep += fpd::kGraphSteps;
+            t += fpd::kGraphSteps;
+            continue;
         }
-        e = fpd::launch_lattice_batch(b->precision, b->insts_d, b->tiles_d, b->ntiles, b->pool, b->tab[0], b->tab[1],
-                                      mk, gp, nbl > 0 ? 1 : 0, b->variant, b->stream);
-        if (e != cudaSuccess) return bcuda(b, e, "batched lattice sweep");
+        if ((rc = enqueue_bstep(b, b->stream, b->gstep, any_first)) != FPD_OK) return rc;
         b->gstep++;
+        ++t;
         if (any_first) {
             for (auto &sl : b->slots)
                 if (sl.state == kActive) sl.first = false;
@@ -437,7 +511,10 @@ int fpd_batch_set_tuning(fpd_batch *b, int32_t variant) {
     if (!b) return FPD_EINVAL;
     if (variant < 0 || variant >= fpd::kLatticeVariants)
         return bfail(b, FPD_EINVAL, "tuning variant must be in [0, %d)", fpd::kLatticeVariants);
-    b->variant = variant;
+    if (variant != b->variant) {
+        drop_bgraphs(b);
+        b->variant = variant;
+    }
     return FPD_OK;
 }
 

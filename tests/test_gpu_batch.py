@@ -92,6 +92,24 @@ def test_batch_longer_than_the_sms_equals_alone(fpd, precision):
     b.close()
 
 
+@pytest.mark.parametrize("precision", [1, 2])
+def test_batch_graph_chunks_equal_alone(fpd, precision):
+    # runs long enough that whole 32-step chunks replay captured graphs
+    # (started at different mask buffers, across an admission that forces a
+    # recapture); every instance still agrees bit for bit
+    cases = _cases(precision)
+    b = fpd.Batch(precision, max_slots=8, pool_bytes=64 << 20, max_beads=256)
+    s0 = b.add(cases[0], 140)
+    s1 = b.add(cases[1], 101)
+    assert b.run(69) == 69
+    s3 = b.add(cases[3], 75)                 # joins at global step 69: recapture
+    while b.run(1000):
+        pass
+    for c, n, s in [(cases[0], 140, s0), (cases[1], 101, s1), (cases[3], 75, s3)]:
+        _same((b.populations(s), b.beads(s)), _alone(fpd, c, n))
+    b.close()
+
+
 @pytest.mark.parametrize("precision,tol", [(0, 1e-13), (1, 1e-5), (2, 1e-2)])
 def test_batch_vector_variant(fpd, precision, tol):
     # variant 2 in a batch: instances whose nx is a multiple of the vector
