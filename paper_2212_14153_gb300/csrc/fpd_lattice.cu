@@ -125,8 +125,7 @@ __device__ __forceinline__ bool tile_cold_early(const unsigned *__restrict__ pre
 // One tile of the sweep: tile (bx, by) of instance I at the instance's step
 // parity, on kTileX x (kTileY / CY) threads; thread (tx, ty) owns the CY
 // cells (x, y0 + ty + k kTileY / CY), k < CY, of its column.  kInner: tiles
-// away from walls and periodic edges use the precomputed pull offsets (the
-// batched sweep keeps the general form, which fits it in 32 registers).
+// away from walls and periodic edges use the precomputed pull offsets.
 template <class S, int CY, bool kInner>
 __device__ __forceinline__ void lattice_tile(const Inst &I, S *__restrict__ pool, const BeadTab &tab,
                                              const unsigned *__restrict__ mask_read,
@@ -199,8 +198,20 @@ __global__ void __launch_bounds__(kTileX *kTileY / CY)
 // Batched sweep over a packed tile list: tiles[t] = (instance slot,
 // by << 16 | bx).  Each instance reads table and layout of its own parity
 // (global parity ^ par_xor); the record is copied to shared memory per CTA.
+// Resident CTAs per SM the batched sweep is compiled for: one cell per
+// thread in the reduced-precision paths fits the precomputed pull offsets in
+// 32 registers (8 CTAs of 256 threads); the other shapes keep the register
+// counts they had without a bound.
+template <class S, int CY> struct BatchMinBlocks {
+    static constexpr int value = std::is_same<S, double>::value ? 4 : (CY == 1 ? 8 : 7);
+};
+// Which batched shapes use the precomputed pull offsets.
+template <class S, int CY> struct BatchInner {
+    static constexpr bool value = CY == 1 && !std::is_same<S, double>::value;
+};
+
 template <class S, int CY>
-__global__ void __launch_bounds__(kTileX *kTileY / CY)
+__global__ void __launch_bounds__(kTileX *kTileY / CY, BatchMinBlocks<S, CY>::value)
     k_lattice_batch(const Inst *__restrict__ insts, const int2 *__restrict__ tiles, S *__restrict__ pool,
                     const BeadTab tab0, const BeadTab tab1, const unsigned *__restrict__ mask_read,
                     const unsigned *__restrict__ mask_prev, unsigned *__restrict__ mask_clear, const int gparity,
@@ -215,8 +226,9 @@ __global__ void __launch_bounds__(kTileX *kTileY / CY)
     }
     __syncthreads();
     const int parity = gparity ^ sI.par_xor;
-    lattice_tile<S, CY, false>(sI, pool, parity ? tab1 : tab0, mask_read, mask_prev, mask_clear, t.y & 0xffff,
-                               t.y >> 16, parity, early_load, early_cold, blockIdx.x == 0, threadIdx.x, threadIdx.y);
+    lattice_tile<S, CY, BatchInner<S, CY>::value>(sI, pool, parity ? tab1 : tab0, mask_read, mask_prev, mask_clear,
+                                                  t.y & 0xffff, t.y >> 16, parity, early_load, early_cold,
+                                                  blockIdx.x == 0, threadIdx.x, threadIdx.y);
 }
 
 // ------------------------------------------------ vectorised sweep (variant 2)
