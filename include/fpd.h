@@ -159,6 +159,23 @@ int fpd_read_fields(fpd_sim *s, double *ux, double *uy, double *rho);
  * Synchronises. */
 int fpd_read_beads(fpd_sim *s, double *pos, double *vel, double *force, double *support);
 
+/* Stream-ordered bead read for callers that keep the device busy while they
+ * consume results: enqueue, after the steps queued so far, a copy of the
+ * current bead table (the table fpd_read_beads would read after those steps)
+ * into the caller-owned host array dst of 7 * n_fibers * n_beads doubles --
+ * the arrays R_x, R_y, V_x, V_y, F_x, F_y, S one after another, each in bead
+ * order -- and return without waiting.  Steps queued afterwards run while
+ * the copy is in flight.  dst holds the values once fpd_wait_read(s, *ticket)
+ * has returned FPD_OK and must stay valid until then; page-locked (pinned)
+ * host memory keeps the copy asynchronous, pageable memory may make this call
+ * block.  FPD_EINVAL for a NULL dst or ticket. */
+int fpd_read_beads_async(fpd_sim *s, double *dst, uint64_t *ticket);
+
+/* Block until the read with this ticket, and every read before it, has
+ * completed; report device-side errors.  FPD_EINVAL for a ticket this handle
+ * has not issued. */
+int fpd_wait_read(fpd_sim *s, uint64_t ticket);
+
 /* Copy the populations f_k (not the stored deviations) of the current time
  * into a caller-owned host array of 9*ny*nx doubles, layout [k][j][i] with
  * the velocity order (0,0) (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1) (-1,-1)

@@ -240,6 +240,11 @@ void free_all(fpd_sim *s) {
     drop_graphs(s);
     if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
     for (auto e : s->ev_pool) cudaEventDestroy(e);
+    for (auto &e : s->read_ev)
+        if (e) {
+            cudaEventDestroy(e);
+            e = nullptr;
+        }
     for (auto &r : s->recs) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
@@ -696,6 +701,38 @@ int fpd_read_beads(fpd_sim *s, double *pos, double *vel, double *force, double *
     pair(force, 4);
     if (support) std::memcpy(support, h + 6 * (size_t)nb, nb * sizeof(double));
     return FPD_OK;
+}
+
+int fpd_read_beads_async(fpd_sim *s, double *dst, uint64_t *ticket) {
+    if (!s) return fail(nullptr, FPD_EINVAL, "fpd_read_beads_async: NULL handle");
+    if (!dst || !ticket) return fail(s, FPD_EINVAL, "fpd_read_beads_async: NULL destination or ticket");
+    const int k = (int)(s->read_seq % fpd_sim::kReadTickets);
+    cudaError_t e;
+    if (!s->read_ev[k] && (e = cudaEventCreateWithFlags(&s->read_ev[k], cudaEventDisableTiming)) != cudaSuccess) {
+        s->read_ev[k] = nullptr;
+        return cuda_fail(s, e, "read event");
+    }
+    const int nb = s->inst.nb;
+    if (nb > 0) {
+        // R, V, F, S of a table are seven consecutive arrays of nb doubles
+        const fpd::BeadTab &t = s->tab[cur_tab(s)];
+        if ((e = cudaMemcpyAsync(dst, t.Rx, 7 * (size_t)nb * sizeof(double), cudaMemcpyDeviceToHost, s->stream)) !=
+            cudaSuccess)
+            return cuda_fail(s, e, "copy beads");
+    }
+    if ((e = cudaEventRecord(s->read_ev[k], s->stream)) != cudaSuccess) return cuda_fail(s, e, "record read");
+    *ticket = s->read_seq++;
+    return FPD_OK;
+}
+
+int fpd_wait_read(fpd_sim *s, uint64_t ticket) {
+    if (!s) return fail(nullptr, FPD_EINVAL, "fpd_wait_read: NULL handle");
+    if (ticket >= s->read_seq) return fail(s, FPD_EINVAL, "fpd_wait_read: ticket %llu was not issued",
+                                           (unsigned long long)ticket);
+    // the slot holds this read or a later one on the same stream; either
+    // completing means this read has completed
+    const cudaError_t e = cudaEventSynchronize(s->read_ev[ticket % fpd_sim::kReadTickets]);
+    return e == cudaSuccess ? FPD_OK : cuda_fail(s, e, "bead read");
 }
 
 namespace {

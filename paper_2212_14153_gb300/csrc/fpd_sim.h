@@ -41,6 +41,10 @@ struct fpd_sim {
     // captured step chunks, one per starting parity (see fpd_step)
     bool use_graphs = true;
     double *host_stage = nullptr;  // pinned staging for bead reads (7 nb doubles)
+    // completion events of stream-ordered bead reads, by ticket % kReadTickets
+    static constexpr int kReadTickets = 8;
+    cudaEvent_t read_ev[kReadTickets] = {};
+    uint64_t read_seq = 0;  // tickets issued so far
     bool early_cold = true;  // unmarked tiles update before the bead phase ends (same results)
     int variant = 0;  // lattice sweep variant (see launch_lattice)
     cudaStream_t cap_stream = nullptr;

@@ -70,6 +70,8 @@ SIGNATURES = {
     "fpd_load": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p]),
     "fpd_batch_internal_flow": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, _DP]),
     "fpd_read_beads": (ctypes.c_int, [ctypes.c_void_p, _DP, _DP, _DP, _DP]),
+    "fpd_read_beads_async": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)]),
+    "fpd_wait_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64]),
     "fpd_read_populations": (ctypes.c_int, [ctypes.c_void_p, _DP]),
     "fpd_write_populations": (ctypes.c_int, [ctypes.c_void_p, _DP]),
     "fpd_diag": (ctypes.c_int, [ctypes.c_void_p, _DP]),
@@ -194,6 +196,18 @@ def fpd_batch_internal_flow(b, slot: int, eps) -> None:
 
 def fpd_read_beads(h, pos, vel, force, support=None) -> None:
     _check(load_library().fpd_read_beads(h, _ptr(pos), _ptr(vel), _ptr(force), _ptr(support)), h)
+
+
+def fpd_read_beads_async(h, dst_ptr: int) -> int:
+    """dst_ptr: address of a host buffer of 7 * nb doubles (pinned for an
+    asynchronous copy); returns the read's ticket."""
+    t = ctypes.c_uint64(0)
+    _check(load_library().fpd_read_beads_async(h, ctypes.c_void_p(dst_ptr), ctypes.byref(t)), h)
+    return t.value
+
+
+def fpd_wait_read(h, ticket: int) -> None:
+    _check(load_library().fpd_wait_read(h, ctypes.c_uint64(ticket)), h)
 
 
 def fpd_read_populations(h, f) -> None:
@@ -339,6 +353,23 @@ class Simulation:
         fpd_read_beads(self.h, R, V, F, S)
         k = self.nb
         return R[:k], V[:k], F[:k], S[:k]
+
+    def read_beads_async(self, buf) -> int:
+        """Queue a copy of the current bead table into buf (a C-contiguous
+        float64 host array or tensor of 7 * nb values: R_x, R_y, V_x, V_y,
+        F_x, F_y, S, each nb long) and return a ticket for wait_read; buf
+        must stay alive until then."""
+        if isinstance(buf, np.ndarray):
+            assert buf.dtype == np.float64 and buf.flags["C_CONTIGUOUS"] and buf.size >= 7 * self.nb
+            ptr = buf.ctypes.data
+        else:  # a torch tensor (pinned host memory keeps the copy asynchronous)
+            assert buf.dtype.is_floating_point and buf.element_size() == 8 and buf.is_contiguous()
+            assert not buf.is_cuda and buf.numel() >= 7 * self.nb
+            ptr = buf.data_ptr()
+        return fpd_read_beads_async(self.h, ptr)
+
+    def wait_read(self, ticket: int) -> None:
+        fpd_wait_read(self.h, ticket)
 
     def save(self, path: str):
         """Checkpoint the whole device state to a file."""

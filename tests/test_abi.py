@@ -126,3 +126,12 @@ def test_workspace_bytes_without_a_device(lib):
     with pytest.raises(fpd.FpdError) as e:
         fpd.fpd_workspace_bytes(p)
     assert e.value.code == fpd.FPD_EINVAL
+
+
+def test_async_bead_reads_reject_a_null_handle(lib):
+    # host-only argument checks of the stream-ordered bead read
+    t = ctypes.c_uint64(0)
+    buf = (ctypes.c_double * 7)()
+    from paper_2212_14153_gb300 import fpd
+    assert lib.fpd_read_beads_async(None, ctypes.cast(buf, ctypes.c_void_p), ctypes.byref(t)) == fpd.FPD_EINVAL
+    assert lib.fpd_wait_read(None, ctypes.c_uint64(0)) == fpd.FPD_EINVAL

@@ -556,3 +556,40 @@ def test_caller_workspace_gives_identical_results():
         with pytest.raises(fpd.FpdError) as e:
             fpd.Simulation(cfg, workspace=bad)
         assert e.value.code == fpd.FPD_EINVAL
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_async_bead_reads_equal_sync_reads(precision):
+    # a caller that keeps the next step queued while it consumes the last
+    # one's beads (double-buffered pinned reads) sees exactly what the
+    # synchronous read returns after the same steps; tickets older than the
+    # handle's event ring still wait correctly
+    import torch
+    rng = np.random.default_rng(91)
+    cfg = wl.random_fiber(rng, 96, 40, n_beads=6, a=2.0, xi=1.0, n_fibers=2, precision=precision)
+    a, b = gpu_sim(cfg), gpu_sim(cfg)
+    nb = a.nb
+    bufs = [torch.zeros(7 * nb, dtype=torch.float64, pin_memory=True) for _ in range(2)]
+    got, want, prev = [], [], None
+    for i in range(20):
+        a.step(1)
+        t = a.read_beads_async(bufs[i % 2])
+        if prev is not None:
+            a.wait_read(prev)
+            got.append(bufs[(i - 1) % 2].numpy().copy())
+        prev = t
+        b.step(1)
+        R, V, F, S = b.beads()
+        want.append(np.concatenate([R[:, 0], R[:, 1], V[:, 0], V[:, 1], F[:, 0], F[:, 1], S]))
+    a.wait_read(prev)
+    got.append(bufs[19 % 2].numpy().copy())
+    for g, w in zip(got, want):
+        assert np.array_equal(g, w)
+    a.wait_read(0)                        # issued 20 reads ago: already complete
+    page = np.zeros(7 * nb)               # pageable host memory works too
+    a.wait_read(a.read_beads_async(page))
+    assert np.array_equal(page, want[-1])
+    from paper_2212_14153_gb300 import fpd
+    with pytest.raises(fpd.FpdError) as e:
+        a.wait_read(10 ** 6)
+    assert e.value.code == fpd.FPD_EINVAL
