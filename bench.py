@@ -195,20 +195,24 @@ def run_gpu(args, rank: int, world: int):
     sim = fpd.Simulation(cfg, stream=stream.cuda_stream)
     sim.set_tuning(variant)
     nb = sim.nb
-    # every step's bead table comes back to the host: two pinned buffers, so
-    # that step t + 1 is queued while the host takes step t's result
-    bufs = [torch.empty(7 * max(nb, 1), dtype=torch.float64, pin_memory=True) for _ in range(2)]
-    prev = None
+    # every step's bead table comes back to the host: the bead phase writes it
+    # into a host ring itself (no copy between the kernels of the step
+    # chain), and the host takes step n while step n + 1 runs
+    sim.export_beads(4)
+    dst = np.empty(7 * max(nb, 1))
     taken = 0.0
     for i in range(e2e_steps):
         sim.step(1)
-        tk = sim.read_beads_async(bufs[i % 2])
-        if prev is not None:
-            sim.wait_read(prev)
-            taken += float(bufs[(i - 1) % 2][0])  # the host consumes R_x of bead 0
-        prev = tk
-    sim.wait_read(prev)
-    taken += float(bufs[(e2e_steps - 1) % 2][0])
+        n = i + 1
+        if n == 1:
+            R, V, F, S = sim.beads()          # step 1 has no bead phase: the initial table
+            taken += R[0, 0] if nb else 0.0
+        elif n >= 3:
+            sim.take_beads(n - 1, dst)
+            taken += dst[0]
+    if e2e_steps >= 2:
+        sim.take_beads(e2e_steps, dst)
+        taken += dst[0]
     ux, uy, rho = sim.fields()
     sim.close()
     e2e_s = time.perf_counter() - t0
@@ -257,8 +261,8 @@ def run_gpu(args, rank: int, world: int):
             "gpu_launches": gpu_launches,
             "e2e": {"value": round(e2e_mlups, 1), "unit": "MLUPS", "h2d_bytes_per_step": h2d_total / e2e_steps,
                     "d2h_bytes_per_step": d2h_total / e2e_steps, "steps": e2e_steps,
-                    "api": "fpd_create, per step fpd_step(1) + fpd_read_beads_async into one of two pinned buffers "
-                           "+ fpd_wait_read of the previous step's read, fpd_read_fields, fpd_destroy"},
+                    "api": "fpd_create, fpd_export_beads(4), per step fpd_step(1) + fpd_take_beads of the previous "
+                           "step (the bead phase writes each table into a host ring), fpd_read_fields, fpd_destroy"},
             "clocks": clocks,
             "mass_after": diag[0],
         }

@@ -176,6 +176,27 @@ int fpd_read_beads_async(fpd_sim *s, double *dst, uint64_t *ticket);
  * has not issued. */
 int fpd_wait_read(fpd_sim *s, uint64_t ticket);
 
+/* Per-step bead export, for callers that take every step's beads while the
+ * steps keep running: from the next step on, the bead phase of each step
+ * also writes its finished table into a ring of `slots` (>= 2) entries of
+ * page-locked host memory owned by the handle, from the device itself, so
+ * that no copy is queued between the kernels of the step chain.
+ * fpd_take_beads then hands over the table after a given step.  slots = 0
+ * turns the export off.  Synchronises and drops captured step graphs.
+ * FPD_EINVAL for slots < 0 or slots == 1; FPD_ENOMEM if the ring cannot be
+ * allocated. */
+int fpd_export_beads(fpd_sim *s, int32_t slots);
+
+/* Copy the bead table after n completed steps (the layout of
+ * fpd_read_beads_async: R_x, R_y, V_x, V_y, F_x, F_y, S, 7 * n_fibers *
+ * n_beads doubles) from the export ring to dst, waiting until the device has
+ * written it.  n counts the steps since fpd_create; the first exported n is
+ * the step count at fpd_export_beads plus one (two if that count was 0: the
+ * first step has no bead phase).  FPD_EBUSY if the ring has already reused
+ * that entry (the caller fell `slots` or more steps behind); FPD_EINVAL if
+ * export is off, n was not exported or not enqueued yet. */
+int fpd_take_beads(fpd_sim *s, int64_t n, double *dst);
+
 /* Copy the populations f_k (not the stored deviations) of the current time
  * into a caller-owned host array of 9*ny*nx doubles, layout [k][j][i] with
  * the velocity order (0,0) (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1) (-1,-1)

@@ -7,6 +7,7 @@
 #include <cstdlib>
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -237,6 +238,9 @@ void free_all(fpd_sim *s) {
     for (auto &m : s->masks) m = nullptr;
     if (s->host_stage) cudaFreeHost(s->host_stage);
     s->host_stage = nullptr;
+    if (s->ex_ring) cudaFreeHost(s->ex_ring);
+    s->ex_ring = s->ex_ring_d = nullptr;
+    s->ex_slots = 0;
     drop_graphs(s);
     if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
     for (auto e : s->ev_pool) cudaEventDestroy(e);
@@ -309,7 +313,8 @@ int enqueue_step(fpd_sim *s, cudaStream_t st, int64_t t, bool profiled) {
             cudaEventRecord(a, st);
         }
         e = fpd::launch_beads(s->precision, s->inst_d, nullptr, I.nb, s->pool, s->tab[0], s->tab[1],
-                              s->masks[t % fpd::kMaskBufs], parity, 1, s->counters, profiled ? 0 : 1, st);
+                              s->masks[t % fpd::kMaskBufs], parity, 1, s->counters, profiled ? 0 : 1, st,
+                              fpd::BeadExport{s->ex_ring_d, s->ex_count, s->ex_slots, s->ex_stride});
         if (e != cudaSuccess) return cuda_fail(s, e, "bead kernel launch");
         if (profiled) {
             cudaEventRecord(b, st);
@@ -451,7 +456,7 @@ StateLayout state_layout(const fpd::Inst &I, size_t elem) {
     L.tab = up(L.pool + L.pool_bytes);
     L.masks = up(L.tab + L.tab_bytes);
     L.counters = up(L.masks + L.mask_bytes);
-    L.inst = up(L.counters + sizeof(unsigned));
+    L.inst = up(L.counters + 16);  // last-block counter, then the 64-bit export counter at +8
     L.total = up(L.inst + sizeof(fpd::Inst));
     return L;
 }
@@ -547,6 +552,7 @@ int create_impl(const fpd_params *p, void *stream, void *workspace, uint64_t wor
     for (int m = 1; m < fpd::kMaskBufs; ++m) s->masks[m] = s->masks[0] + m * L.mask_words;
     s->mask_bytes = L.mask_bytes;
     s->counters = (unsigned *)(base + L.counters);
+    s->ex_count = (unsigned long long *)(base + L.counters + 8);
     s->inst_d = (fpd::Inst *)(base + L.inst);
     FPD_TRY(cudaMemcpyAsync(s->inst_d, &I, sizeof I, cudaMemcpyHostToDevice, s->stream), "copy instance");
     FPD_TRY(fpd::launch_init(s->precision, s->inst_d, I, s->pool, p->init_couette, s->stream), "init kernel");
@@ -725,6 +731,78 @@ int fpd_read_beads_async(fpd_sim *s, double *dst, uint64_t *ticket) {
     return FPD_OK;
 }
 
+int fpd_export_beads(fpd_sim *s, int32_t slots) {
+    if (!s) return fail(nullptr, FPD_EINVAL, "fpd_export_beads: NULL handle");
+    if (slots < 0 || slots == 1) return fail(s, FPD_EINVAL, "fpd_export_beads: slots must be 0 or >= 2");
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "fpd_export_beads");
+    drop_graphs(s);
+    if (s->ex_ring) cudaFreeHost(s->ex_ring);
+    s->ex_ring = s->ex_ring_d = nullptr;
+    s->ex_slots = 0;
+    if (slots == 0 || s->inst.nb == 0) return FPD_OK;
+    const int stride = fpd::kExportHeader + 7 * s->inst.nb;
+    const size_t bytes = (size_t)slots * stride * sizeof(double);
+    void *h = nullptr, *d = nullptr;
+    if ((e = cudaHostAlloc(&h, bytes, cudaHostAllocMapped)) != cudaSuccess)
+        return fail(s, FPD_ENOMEM, "fpd_export_beads: page-locked ring of %zu bytes: %s", bytes,
+                    cudaGetErrorString(e));
+    if ((e = cudaHostGetDevicePointer(&d, h, 0)) != cudaSuccess) {
+        cudaFreeHost(h);
+        return cuda_fail(s, e, "fpd_export_beads: device address of the ring");
+    }
+    std::memset(h, 0, bytes);
+    if ((e = cudaMemsetAsync(s->ex_count, 0, sizeof(unsigned long long), s->stream)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s->stream)) != cudaSuccess) {
+        cudaFreeHost(h);
+        return cuda_fail(s, e, "fpd_export_beads: reset counter");
+    }
+    s->ex_ring = (double *)h;
+    s->ex_ring_d = (double *)d;
+    s->ex_slots = slots;
+    s->ex_stride = stride;
+    // the bead phase of step index t (t >= 1) finishes the table after t + 1 steps
+    s->ex_first = std::max<int64_t>(s->nstep, 1) + 1;
+    return FPD_OK;
+}
+
+int fpd_take_beads(fpd_sim *s, int64_t n, double *dst) {
+    if (!s) return fail(nullptr, FPD_EINVAL, "fpd_take_beads: NULL handle");
+    if (!dst) return fail(s, FPD_EINVAL, "fpd_take_beads: NULL destination");
+    if (!s->ex_ring) return fail(s, FPD_EINVAL, "fpd_take_beads: bead export is off");
+    if (n < s->ex_first || n > s->nstep)
+        return fail(s, FPD_EINVAL, "fpd_take_beads: step %lld was not exported or not enqueued (exported from %lld, "
+                    "%lld enqueued)", (long long)n, (long long)s->ex_first, (long long)s->nstep);
+    const unsigned long long want = (unsigned long long)(n - s->ex_first) + 1ull;
+    const double *slot = s->ex_ring + (size_t)((want - 1) % (unsigned long long)s->ex_slots) * s->ex_stride;
+    const auto *hdr = reinterpret_cast<const unsigned long long *>(slot);
+    const size_t count = 7 * (size_t)s->inst.nb;
+    for (long spin = 0;; ++spin) {
+        const unsigned long long h = __atomic_load_n(hdr, __ATOMIC_ACQUIRE);
+        if (h > want) return fail(s, FPD_EBUSY, "fpd_take_beads: the ring has reused the entry of step %lld",
+                                  (long long)n);
+        if (h == want) {
+            std::memcpy(dst, slot + fpd::kExportHeader, count * sizeof(double));
+            // the entry must not have been rewritten while it was copied
+            if (__atomic_load_n(hdr, __ATOMIC_ACQUIRE) != want)
+                return fail(s, FPD_EBUSY, "fpd_take_beads: the ring reused the entry of step %lld during the copy",
+                            (long long)n);
+            return FPD_OK;
+        }
+        if ((spin & 1023) == 1023) {
+            // the device has not written it yet: stop if the stream has run
+            // dry (the step's bead phase cannot come) or failed
+            const cudaError_t q = cudaStreamQuery(s->stream);
+            if (q == cudaSuccess) {
+                if (__atomic_load_n(hdr, __ATOMIC_ACQUIRE) == want) continue;
+                return fail(s, FPD_EINVAL, "fpd_take_beads: the stream is idle and step %lld was not exported",
+                            (long long)n);
+            }
+            if (q != cudaErrorNotReady) return cuda_fail(s, q, "fpd_take_beads");
+        }
+    }
+}
+
 int fpd_wait_read(fpd_sim *s, uint64_t ticket) {
     if (!s) return fail(nullptr, FPD_EINVAL, "fpd_wait_read: NULL handle");
     if (ticket >= s->read_seq) return fail(s, FPD_EINVAL, "fpd_wait_read: ticket %llu was not issued",
@@ -816,6 +894,8 @@ int fpd_load(fpd_sim *s, const char *path) {
     if (e == cudaSuccess) e = cudaMemcpy(s->masks[0], masks.data(), masks.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(s, e, "fpd_load");
     s->nstep = h.nstep;
+    // an active bead export restarts from the restored step count
+    if (s->ex_ring) return fpd_export_beads(s, s->ex_slots);
     return FPD_OK;
 }
 

@@ -339,7 +339,7 @@ template <class S, int NT>
 __global__ void __launch_bounds__(NT, BeadMinBlocks<S, NT>::value)
     k_beads(const Inst *__restrict__ insts, const int2 *__restrict__ blist, const int nb_total,
             const S *__restrict__ pool, const BeadTab tab0, const BeadTab tab1, unsigned *__restrict__ mask_write,
-            int gparity, int advance, unsigned *__restrict__ counters) {
+            int gparity, int advance, unsigned *__restrict__ counters, BeadExport ex) {
     constexpr bool kF64 = std::is_same<S, double>::value;
     __shared__ Inst sI;
     // neighbour beads: old-table position (FP64 path), offset R_b - R_q and
@@ -662,6 +662,8 @@ __global__ void __launch_bounds__(NT, BeadMinBlocks<S, NT>::value)
     __syncthreads();
     if (s_last) {
     __threadfence();
+    // this phase's export number (the previous phase wrote the counter)
+    const unsigned long long ex_k = ex.ring ? *(volatile unsigned long long *)ex.count : 0ull;
     // stage the instance's new positions and support sums (written by every
     // CTA; the L2-coherent loads see them), then every segment once
     for (int q = tid; q < I.nb; q += blockDim.x) {
@@ -732,6 +734,29 @@ __global__ void __launch_bounds__(NT, BeadMinBlocks<S, NT>::value)
         tnew.yl[gq] = (float)(yw - (double)yh);
         tnew.gxf[gq] = (float)Gx;
         tnew.gyf[gq] = (float)Gy;
+        if (ex.ring) {
+            // export: R, V, F, S of bead q into the ring slot of this phase
+            double *d = ex.ring + (size_t)(ex_k % (unsigned long long)ex.slots) * ex.stride + kExportHeader;
+            const int nbq = I.nb;
+            d[q] = s_rx[q];
+            d[nbq + q] = s_ry[q];
+            d[2 * nbq + q] = __ldcg(tnew.Vx + gq);
+            d[3 * nbq + q] = __ldcg(tnew.Vy + gq);
+            d[4 * nbq + q] = Fx;
+            d[5 * nbq + q] = Fy;
+            d[6 * nbq + q] = s_gx[q];
+        }
+    }
+    if (ex.ring) {
+        // the table is in host memory before its slot header says so
+        __threadfence_system();
+        __syncthreads();
+        if (tid == 0) {
+            unsigned long long *hdr =
+                (unsigned long long *)(ex.ring + (size_t)(ex_k % (unsigned long long)ex.slots) * ex.stride);
+            asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(hdr), "l"(ex_k + 1ull) : "memory");
+            *ex.count = ex_k + 1ull;
+        }
     }
     if (tid == 0) counters[ii] = 0u;
     }  // last bead of the instance
@@ -756,20 +781,20 @@ int sm_count() {
 template <class S>
 cudaError_t launch_beads_t(cudaLaunchConfig_t &cfg, bool few, const Inst *inst_d, const int2 *blist, int nb_total,
                            const void *pool, BeadTab tab0, BeadTab tab1, unsigned *mask_write, int gparity,
-                           int advance, unsigned *counters) {
+                           int advance, unsigned *counters, BeadExport ex) {
     cfg.blockDim = dim3(few ? kBeadThreadsFew : kBeadThreads);
     if (few)
         return cudaLaunchKernelEx(&cfg, k_beads<S, kBeadThreadsFew>, inst_d, blist, nb_total, (const S *)pool, tab0,
-                                  tab1, mask_write, gparity, advance, counters);
+                                  tab1, mask_write, gparity, advance, counters, ex);
     return cudaLaunchKernelEx(&cfg, k_beads<S, kBeadThreads>, inst_d, blist, nb_total, (const S *)pool, tab0, tab1,
-                              mask_write, gparity, advance, counters);
+                              mask_write, gparity, advance, counters, ex);
 }
 
 }  // namespace
 
 cudaError_t launch_beads(int precision, const Inst *inst_d, const int2 *blist, int nb_total, const void *pool,
                          BeadTab tab0, BeadTab tab1, unsigned *mask_write, int gparity, int advance,
-                         unsigned *counters, int pdl, cudaStream_t st) {
+                         unsigned *counters, int pdl, cudaStream_t st, BeadExport ex) {
     if (nb_total <= 0) return cudaSuccess;
     // one CTA per bead: a grid capped at the resident CTAs (persistent) keeps
     // the bead CTAs on the SMs at once and leaves the sweep that follows
@@ -788,13 +813,13 @@ cudaError_t launch_beads(int precision, const Inst *inst_d, const int2 *blist, i
     switch (precision) {
         case 0:
             return launch_beads_t<double>(cfg, few, inst_d, blist, nb_total, pool, tab0, tab1, mask_write, gparity,
-                                          advance, counters);
+                                          advance, counters, ex);
         case 1:
             return launch_beads_t<float>(cfg, few, inst_d, blist, nb_total, pool, tab0, tab1, mask_write, gparity,
-                                         advance, counters);
+                                         advance, counters, ex);
         case 2:
             return launch_beads_t<__half>(cfg, few, inst_d, blist, nb_total, pool, tab0, tab1, mask_write, gparity,
-                                          advance, counters);
+                                          advance, counters, ex);
     }
     return cudaErrorInvalidValue;
 }

@@ -61,9 +61,22 @@ cudaError_t launch_lattice(int precision, const Inst *inst_d, const Inst &inst_h
 // pdl = 1 launches the bead phase as a programmatic dependent of the
 // previous sweep: it waits for that sweep first thing and releases the next
 // sweep at once, so the next sweep's unmarked tiles overlap the whole phase.
+// Per-step export of a single instance's finished bead table to host
+// memory (ring == nullptr: none): the instance's last CTA writes R_x, R_y,
+// V_x, V_y, F_x, F_y, S (nb doubles each) after kExportHeader doubles into
+// slot k % slots of the ring (stride doubles a slot, device address of
+// mapped page-locked memory), then k + 1 into the slot's first 64-bit word,
+// and increments *count (k: the exports before this one).
+constexpr int kExportHeader = 8;
+struct BeadExport {
+    double *ring = nullptr;
+    unsigned long long *count = nullptr;
+    int slots = 0;
+    int stride = 0;
+};
 cudaError_t launch_beads(int precision, const Inst *inst_d, const int2 *blist, int nb_total,
                          const void *pool, BeadTab tab0, BeadTab tab1, unsigned *mask_write, int gparity,
-                         int advance, unsigned *counters, int pdl, cudaStream_t st);
+                         int advance, unsigned *counters, int pdl, cudaStream_t st, BeadExport ex = BeadExport{});
 
 // Batched sweep over a packed tile list of many instances (tiles[t] =
 // (slot, by << 16 | bx)); each instance at its own parity.  Under variant 2

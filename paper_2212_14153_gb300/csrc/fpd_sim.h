@@ -45,6 +45,13 @@ struct fpd_sim {
     static constexpr int kReadTickets = 8;
     cudaEvent_t read_ev[kReadTickets] = {};
     uint64_t read_seq = 0;  // tickets issued so far
+    // per-step bead export (fpd_export_beads): mapped page-locked ring, its
+    // device alias, slot count and stride (doubles), the device-side export
+    // counter (in the state block) and the step count of export 0
+    double *ex_ring = nullptr, *ex_ring_d = nullptr;
+    int ex_slots = 0, ex_stride = 0;
+    unsigned long long *ex_count = nullptr;
+    int64_t ex_first = 0;
     bool early_cold = true;  // unmarked tiles update before the bead phase ends (same results)
     int variant = 0;  // lattice sweep variant (see launch_lattice)
     cudaStream_t cap_stream = nullptr;

@@ -72,6 +72,8 @@ SIGNATURES = {
     "fpd_read_beads": (ctypes.c_int, [ctypes.c_void_p, _DP, _DP, _DP, _DP]),
     "fpd_read_beads_async": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)]),
     "fpd_wait_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64]),
+    "fpd_export_beads": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "fpd_take_beads": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, _DP]),
     "fpd_read_populations": (ctypes.c_int, [ctypes.c_void_p, _DP]),
     "fpd_write_populations": (ctypes.c_int, [ctypes.c_void_p, _DP]),
     "fpd_diag": (ctypes.c_int, [ctypes.c_void_p, _DP]),
@@ -208,6 +210,14 @@ def fpd_read_beads_async(h, dst_ptr: int) -> int:
 
 def fpd_wait_read(h, ticket: int) -> None:
     _check(load_library().fpd_wait_read(h, ctypes.c_uint64(ticket)), h)
+
+
+def fpd_export_beads(h, slots: int) -> None:
+    _check(load_library().fpd_export_beads(h, slots), h)
+
+
+def fpd_take_beads(h, n: int, dst) -> None:
+    _check(load_library().fpd_take_beads(h, n, _ptr(dst)), h)
 
 
 def fpd_read_populations(h, f) -> None:
@@ -370,6 +380,19 @@ class Simulation:
 
     def wait_read(self, ticket: int) -> None:
         fpd_wait_read(self.h, ticket)
+
+    def export_beads(self, slots: int) -> None:
+        """Have every following step's bead phase write its table into a
+        host ring of `slots` entries (0: off); take it with take_beads."""
+        fpd_export_beads(self.h, slots)
+
+    def take_beads(self, n: int, dst: np.ndarray | None = None) -> np.ndarray:
+        """The bead table after n completed steps from the export ring
+        (7 * nb doubles: R_x, R_y, V_x, V_y, F_x, F_y, S)."""
+        if dst is None:
+            dst = np.empty(7 * self.nb)
+        fpd_take_beads(self.h, n, dst)
+        return dst
 
     def save(self, path: str):
         """Checkpoint the whole device state to a file."""

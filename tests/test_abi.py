@@ -135,3 +135,10 @@ def test_async_bead_reads_reject_a_null_handle(lib):
     from paper_2212_14153_gb300 import fpd
     assert lib.fpd_read_beads_async(None, ctypes.cast(buf, ctypes.c_void_p), ctypes.byref(t)) == fpd.FPD_EINVAL
     assert lib.fpd_wait_read(None, ctypes.c_uint64(0)) == fpd.FPD_EINVAL
+
+
+def test_bead_export_rejects_a_null_handle(lib):
+    from paper_2212_14153_gb300 import fpd
+    buf = (ctypes.c_double * 7)()
+    assert lib.fpd_export_beads(None, 4) == fpd.FPD_EINVAL
+    assert lib.fpd_take_beads(None, 2, ctypes.cast(buf, fpd._DP)) == fpd.FPD_EINVAL

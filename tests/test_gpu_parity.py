@@ -593,3 +593,44 @@ def test_async_bead_reads_equal_sync_reads(precision):
     with pytest.raises(fpd.FpdError) as e:
         a.wait_read(10 ** 6)
     assert e.value.code == fpd.FPD_EINVAL
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_bead_export_equals_sync_reads(precision):
+    # the bead phase writes every step's finished table into the host ring;
+    # taking step n from the ring gives exactly what the synchronous read
+    # returns after n steps, for single steps and for graph-replayed chunks
+    from paper_2212_14153_gb300 import fpd
+    rng = np.random.default_rng(92)
+    cfg = wl.random_fiber(rng, 96, 40, n_beads=6, a=2.0, xi=1.0, n_fibers=2, precision=precision)
+    a, b = gpu_sim(cfg), gpu_sim(cfg)
+
+    def table(sim):
+        R, V, F, S = sim.beads()
+        return np.concatenate([R[:, 0], R[:, 1], V[:, 0], V[:, 1], F[:, 0], F[:, 1], S])
+
+    a.export_beads(4)                     # at step 0: the first bead phase finishes step 2
+    with pytest.raises(fpd.FpdError) as e:
+        a.take_beads(1)
+    assert e.value.code == fpd.FPD_EINVAL
+    want = {}
+    for n in range(1, 25):
+        a.step(1)
+        b.step(1)
+        want[n] = table(b)
+        if n >= 3:                        # take the previous step while this one runs
+            assert np.array_equal(a.take_beads(n - 1), want[n - 1])
+    assert np.array_equal(a.take_beads(24), want[24])
+    a.step(64)                            # two captured 32-step chunks
+    b.step(64)
+    assert np.array_equal(a.take_beads(88), table(b))
+    with pytest.raises(fpd.FpdError) as e:  # four slots: step 80 was overwritten
+        a.take_beads(80)
+    assert e.value.code == fpd.FPD_EBUSY
+    with pytest.raises(fpd.FpdError) as e:  # not enqueued
+        a.take_beads(89)
+    assert e.value.code == fpd.FPD_EINVAL
+    a.export_beads(0)
+    with pytest.raises(fpd.FpdError) as e:
+        a.take_beads(88)
+    assert e.value.code == fpd.FPD_EINVAL
