@@ -221,6 +221,24 @@ def run_gpu(args, rank: int, world: int):
     d2h_step = 8 * 7 * nb                                        # R, V, F, S every step
     d2h_total = d2h_step * e2e_steps + 3 * 8 * cells             # + final u_x, u_y, rho
 
+    # accuracy beside the throughput: the same workload in FP64 storage (the
+    # path the parity tests pin to the oracle at 1e-12) against this
+    # precision, after a short run
+    accuracy = None
+    if rank == 0 and args.precision != 0 and args.accuracy_steps > 0:
+        runs = []
+        for prec in (0, args.precision):
+            s2 = fpd.Simulation(dict(cfg, precision=prec), stream=stream.cuda_stream)
+            s2.step(args.accuracy_steps)
+            ux, uy, _ = s2.fields()
+            R = s2.beads()[0]
+            s2.close()
+            runs.append((np.concatenate([ux.ravel(), uy.ravel()]), R))
+        (u64, R64), (u, R) = runs
+        accuracy = {"vs": "FP64 storage on this GPU (pinned to the oracle at 1e-12)", "steps": args.accuracy_steps,
+                    "u_rel_l2": float(np.linalg.norm(u - u64) / np.linalg.norm(u64)),
+                    "bead_max_dR": float(np.abs(R - R64).max())}
+
     if rank == 0:
         peaks = measured_peaks()
         bpc = 18 * STORE_BYTES[args.precision]
@@ -265,6 +283,7 @@ def run_gpu(args, rank: int, world: int):
                            "step (the bead phase writes each table into a host ring), fpd_read_fields, fpd_destroy"},
             "clocks": clocks,
             "mass_after": diag[0],
+            "accuracy": accuracy,
         }
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(cfg, budget_s=args.cpu_seconds)
@@ -451,6 +470,7 @@ def main():
     ap.add_argument("--precision", type=int, default=1, choices=[0, 1, 2])
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=10000)
+    ap.add_argument("--accuracy-steps", type=int, default=200)
     ap.add_argument("--ref-steps", type=int, default=20)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
