@@ -308,8 +308,20 @@ def cpu_baseline(cfg: dict, budget_s: float = 12.0, steps: int | None = None) ->
         el = time.perf_counter() - t0
         if (steps is not None and n >= steps) or (steps is None and (el >= budget_s or n >= 1000)):
             break
-    return {"value": round(cells * n / el / 1e6, 3), "unit": "MLUPS", "cores": cores, "kind": "oracle",
-            "sample": f"{n} full steps of {cfg['name']} ({cells} cells) in {el:.1f} s"}
+    out = {"value": round(cells * n / el / 1e6, 3), "unit": "MLUPS", "cores": cores, "kind": "oracle",
+           "sample": f"{n} full steps of {cfg['name']} ({cells} cells) in {el:.1f} s"}
+    # the same oracle on one thread (the canonical single-core baseline), a
+    # shorter sample
+    o1 = oracle.Sim(dict(cfg, threads=1))
+    t0 = time.perf_counter()
+    n1 = 0
+    while n1 < 1000 and time.perf_counter() - t0 < budget_s / 2:
+        o1.step(1)
+        n1 += 1
+    el1 = time.perf_counter() - t0
+    out["single_thread"] = {"value": round(cells * n1 / el1 / 1e6, 3), "unit": "MLUPS", "cores": 1,
+                            "sample": f"{n1} full steps in {el1:.1f} s"}
+    return out
 
 
 def run_reference(args, rank: int, world: int):
