@@ -45,7 +45,7 @@ typedef enum {
     FPD_EINVAL = -1,   /* invalid argument or parameter set                 */
     FPD_ENOMEM = -2,   /* device or host allocation failed                  */
     FPD_ECUDA = -3,    /* a CUDA call failed (message has the CUDA error)   */
-    FPD_ETIMEOUT = -4, /* a bounded device-side wait gave up                */
+    FPD_ETIMEOUT = -4, /* a bounded wait gave up                            */
     FPD_ENAN = -5,     /* a non-finite value was found in the state         */
     FPD_EBUSY = -6     /* no free slot or memory for the request            */
 } fpd_status;
@@ -194,7 +194,8 @@ int fpd_export_beads(fpd_sim *s, int32_t slots);
  * the step count at fpd_export_beads plus one (two if that count was 0: the
  * first step has no bead phase).  FPD_EBUSY if the ring has already reused
  * that entry (the caller fell `slots` or more steps behind); FPD_EINVAL if
- * export is off, n was not exported or not enqueued yet. */
+ * export is off, n was not exported or not enqueued yet; FPD_ETIMEOUT if the
+ * entry has not arrived within 60 s while the stream is still busy. */
 int fpd_take_beads(fpd_sim *s, int64_t n, double *dst);
 
 /* Copy the populations f_k (not the stored deviations) of the current time

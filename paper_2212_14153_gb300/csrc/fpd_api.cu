@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <algorithm>
+#include <chrono>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -777,6 +778,8 @@ int fpd_take_beads(fpd_sim *s, int64_t n, double *dst) {
     const double *slot = s->ex_ring + (size_t)((want - 1) % (unsigned long long)s->ex_slots) * s->ex_stride;
     const auto *hdr = reinterpret_cast<const unsigned long long *>(slot);
     const size_t count = 7 * (size_t)s->inst.nb;
+    constexpr int kTakeTimeoutS = 60;
+    std::chrono::steady_clock::time_point t_start{};
     for (long spin = 0;; ++spin) {
         const unsigned long long h = __atomic_load_n(hdr, __ATOMIC_ACQUIRE);
         if (h > want) return fail(s, FPD_EBUSY, "fpd_take_beads: the ring has reused the entry of step %lld",
@@ -791,7 +794,12 @@ int fpd_take_beads(fpd_sim *s, int64_t n, double *dst) {
         }
         if ((spin & 1023) == 1023) {
             // the device has not written it yet: stop if the stream has run
-            // dry (the step's bead phase cannot come) or failed
+            // dry (the step's bead phase cannot come), failed, or made no
+            // progress for kTakeTimeoutS seconds
+            if (spin == 1023) t_start = std::chrono::steady_clock::now();
+            else if (std::chrono::steady_clock::now() - t_start > std::chrono::seconds(kTakeTimeoutS))
+                return fail(s, FPD_ETIMEOUT, "fpd_take_beads: step %lld not written within %d s", (long long)n,
+                            kTakeTimeoutS);
             const cudaError_t q = cudaStreamQuery(s->stream);
             if (q == cudaSuccess) {
                 if (__atomic_load_n(hdr, __ATOMIC_ACQUIRE) == want) continue;
