@@ -69,10 +69,13 @@ def test_classifier_regimes():
     assert tb.classify(t, th_stuck, np.full_like(t, 0.8), g) == "s-stuck"
 
 
-@pytest.mark.parametrize("x_cr,beta,T0", [(2.2, 0.5, 30.6), (0.7, 0.5, 29.5), (5.6, 0.3, 11.9), (0.8, 0.6, 7.3)])
-def test_critical_fit_recovers_the_divergence_law(x_cr, beta, T0):
+@pytest.mark.parametrize("law", ["rigid_re", "rigid_c", "flex_re", "flex_c"])
+def test_critical_fit_recovers_the_divergence_law(law):
     # gamma_dot T = T0 (1 - x / x_cr)^-beta, sampled below x_cr (the four
-    # laws reported in Secs. 4.2-4.3)
+    # laws the paper reports, tests/golden)
+    from conftest import paper_value
+    v = paper_value(law)
+    x_cr, beta, T0 = v["x_cr"], v["beta"], v["gT0"]
     x = np.linspace(0.1, 0.9, 7) * x_cr
     T = T0 * (1 - x / x_cr) ** (-beta)
     xc, t0, rms = tb.critical_fit(x, T, beta)
