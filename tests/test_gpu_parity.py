@@ -634,3 +634,31 @@ def test_bead_export_equals_sync_reads(precision):
     with pytest.raises(fpd.FpdError) as e:
         a.take_beads(88)
     assert e.value.code == fpd.FPD_EINVAL
+
+
+def test_bead_export_restarts_after_a_checkpoint_load(tmp_path):
+    # a load rewinds the step count; an active export restarts from it and
+    # hands over the same tables as an uninterrupted run
+    from paper_2212_14153_gb300 import fpd
+    rng = np.random.default_rng(93)
+    cfg = wl.random_fiber(rng, 80, 40, n_beads=5, a=2.0, xi=1.0, n_fibers=2, precision=1)
+    ref = gpu_sim(cfg)
+    want = {}
+    for n in range(1, 12):
+        ref.step(1)
+        R, V, F, S = ref.beads()
+        want[n] = np.concatenate([R[:, 0], R[:, 1], V[:, 0], V[:, 1], F[:, 0], F[:, 1], S])
+    a = gpu_sim(cfg)
+    a.step(5)
+    path = str(tmp_path / "ck.fpd")
+    a.save(path)
+    a.export_beads(3)
+    a.step(4)
+    assert np.array_equal(a.take_beads(9), want[9])
+    a.load(path)                          # back at step 5: the export restarts at step 6
+    with pytest.raises(fpd.FpdError) as e:
+        a.take_beads(9)                   # not enqueued since the load
+    assert e.value.code == fpd.FPD_EINVAL
+    a.step(6)
+    for n in (9, 10, 11):
+        assert np.array_equal(a.take_beads(n), want[n])
