@@ -316,10 +316,16 @@ def workspace_bytes(cfg: dict) -> int:
 class Simulation:
     """One FPD instance on the GPU, driven through the C ABI."""
 
-    def __init__(self, cfg: dict, stream=None, workspace=None):
+    def __init__(self, cfg: dict, stream=None, workspace=None, tuning=None):
         """workspace: optional CUDA tensor (any dtype, contiguous, at least
         workspace_bytes(cfg) bytes, 256-byte aligned) that holds the state;
-        it is kept referenced for the handle's lifetime."""
+        it is kept referenced for the handle's lifetime.
+
+        tuning: sweep launch shape.  None keeps variant 0, the shape a
+        Batch also starts with, so a lone run and the same instance in a
+        batch agree bit for bit; an int sets that variant; "auto" takes
+        the fastest variant the autotuner measured for this workload
+        (timed once on a scratch instance, then cached)."""
         if stream is None:
             import torch
             if not torch.cuda.is_available():
@@ -334,6 +340,11 @@ class Simulation:
             self.h = fpd_create(p, stream)
         self.nx, self.ny = p.nx, p.ny
         self.nb = p.n_beads * p.n_fibers
+        if tuning == "auto":
+            from . import autotune
+            tuning = autotune.tune(self.cfg)
+        if tuning is not None:
+            self.set_tuning(int(tuning))
 
     def close(self):
         if getattr(self, "h", None) is not None:

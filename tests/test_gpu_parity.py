@@ -30,9 +30,9 @@ def _built():
     build.build()
 
 
-def gpu_sim(cfg):
+def gpu_sim(cfg, **kw):
     from paper_2212_14153_gb300 import fpd
-    return fpd.Simulation(cfg)
+    return fpd.Simulation(cfg, **kw)
 
 
 def orc_sim(cfg):
@@ -317,6 +317,28 @@ def test_sweep_variants_agree(precision, tol, variant):
     print(f"variant {variant} vs 0, precision {precision}: rel L2 of f - w {e:.2e}")
     assert e < tol
     assert rel_l2(b.beads()[0], a.beads()[0]) < tol * 1e-3
+
+
+def test_auto_tuning_picks_a_measured_variant_and_caches_it(tmp_path, monkeypatch):
+    # Simulation(cfg, tuning="auto") times every launch shape once, keeps the
+    # fastest, and a second handle of the same workload reads the cache
+    import json
+    monkeypatch.setenv("FPD_TUNING_CACHE", str(tmp_path / "tuning.json"))
+    rng = np.random.default_rng(79)
+    cfg = wl.random_fiber(rng, 96, 48, n_beads=6, a=2.0, xi=1.0, n_fibers=2, precision=1)
+    s = gpu_sim(cfg, tuning="auto")
+    v, n = s.tuning()
+    d = json.load(open(tmp_path / "tuning.json"))
+    (entry,) = d.values()
+    assert len(entry["ms_per_step"]) == n and entry["variant"] == v
+    assert entry["ms_per_step"][v] == min(entry["ms_per_step"])
+    assert gpu_sim(cfg, tuning="auto").tuning() == (v, n)
+    plain = gpu_sim(cfg)
+    assert plain.tuning() == (0, n)
+    s.step(40)
+    plain.step(40)
+    w = oracle.feq(1.0, 0.0, 0.0)[:, None, None]
+    assert rel_l2(s.populations() - w, plain.populations() - w) < 1e-5
 
 
 @pytest.mark.parametrize("seed,nx,ny,N,NF,a,xi,coll", [
