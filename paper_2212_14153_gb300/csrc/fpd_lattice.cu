@@ -124,16 +124,21 @@ __device__ __forceinline__ bool tile_cold_early(const unsigned *__restrict__ pre
 
 // One tile of the sweep: tile (bx, by) of instance I at the instance's step
 // parity, on kTileX x (kTileY / CY) threads; thread (tx, ty) owns the CY
-// cells (x, y0 + ty + k kTileY / CY), k < CY, of its column.  kInner: tiles
-// away from walls and periodic edges use the precomputed pull offsets.
-template <class S, int CY, bool kInner>
+// cells (x, y0 + ty + k kTileY / CY), k < CY, of its column.  kAlongX: on
+// (kTileX / CY) x kTileY threads instead, thread (tx, ty) owns the CY cells
+// (x0 + tx + k kTileX / CY, y0 + ty) of its row, whose elements in every
+// plane lie a constant distance apart, so that one address serves all of
+// them (immediate offsets).  kInner: tiles away from walls and periodic
+// edges use the precomputed pull offsets.
+template <class S, int CY, bool kInner, bool kAlongX = false>
 __device__ __forceinline__ void lattice_tile(const Inst &I, S *__restrict__ pool, const BeadTab &tab,
                                              const unsigned *__restrict__ mask_read,
                                              const unsigned *__restrict__ mask_prev, unsigned *__restrict__ mask_clear,
                                              const int bx, const int by, const int parity, const int early_load,
                                              const int early_cold, const bool lead, const int tx, const int ty) {
     using R = typename Real<S>::type;
-    constexpr int RY = kTileY / CY;
+    constexpr int RY = kAlongX ? 0 : kTileY / CY;
+    constexpr int RX = kAlongX ? kTileX / CY : 0;
     const int x = bx * kTileX + tx;
     const int tile = I.tile_base + by * I.ntx + bx;
     const int W = I.mask_words;
@@ -148,18 +153,18 @@ __device__ __forceinline__ void lattice_tile(const Inst &I, S *__restrict__ pool
 #pragma unroll
     for (int k = 0; k < CY; ++k) {
         y[k] = by * kTileY + ty + k * RY;
-        valid[k] = x < I.nx && y[k] < I.ny;
-        if constexpr (!kInner) C[k] = make_cell(I, x, valid[k] ? y[k] : 0);
+        valid[k] = x + k * RX < I.nx && y[k] < I.ny;
+        if constexpr (!kInner) C[k] = make_cell(I, x + k * RX, valid[k] ? y[k] : 0);
     }
     auto pull = [&]() {
         if (inner) {
             const S *p = Asrc + (y[0] * I.pitch + x);
 #pragma unroll
-            for (int k = 0; k < CY; ++k) pull_inner<S, R>(p + k * RY * I.pitch, I, g[k]);
+            for (int k = 0; k < CY; ++k) pull_inner<S, R>(p + (k * RY * I.pitch + k * RX), I, g[k]);
         } else {
 #pragma unroll
             for (int k = 0; k < CY; ++k)
-                if (valid[k]) pull_pops<S, R>(Asrc, I, kInner ? make_cell(I, x, y[k]) : C[k], g[k]);
+                if (valid[k]) pull_pops<S, R>(Asrc, I, kInner ? make_cell(I, x + k * RX, y[k]) : C[k], g[k]);
         }
     };
     // populations come from the previous sweep; when the bead phase runs
@@ -170,7 +175,7 @@ __device__ __forceinline__ void lattice_tile(const Inst &I, S *__restrict__ pool
     pdl_trigger();
     if (tx == 0 && ty == 0)  // a mask of two steps back, for the next bead phase
         for (int w = 0; w < W; ++w) mask_clear[tile * W + w] = 0u;
-    if (!valid[0]) return;  // cells further down the column are invalid too
+    if (!valid[0]) return;  // the thread's other cells (further along its column or row) are invalid too
     if (!early_load) pull();
     const unsigned *m = mask_read + tile * W;
     unsigned any = 0u;
@@ -180,18 +185,18 @@ __device__ __forceinline__ void lattice_tile(const Inst &I, S *__restrict__ pool
     for (int k = 0; k < CY; ++k) {
         if (!valid[k]) continue;
         R Fx, Fy, s_nu, s_e, s_eps, s_q;
-        cell_overlay<R>(I, tab, m, W, any, x, y[k], Fx, Fy, s_nu, s_e, s_eps, s_q);
+        cell_overlay<R>(I, tab, m, W, any, x + k * RX, y[k], Fx, Fy, s_nu, s_e, s_eps, s_q);
         collide<R>(g[k], Fx, Fy, s_nu, s_e, s_eps, s_q);
-        put_at<S, R>(Adst + (kInner ? y[k] * I.pitch + x : C[k].r0 + C[k].x), I, g[k]);
+        put_at<S, R>(Adst + (kInner ? y[k] * I.pitch + x + k * RX : C[k].r0 + C[k].x), I, g[k]);
     }
 }
 
-template <class S, int CY>
+template <class S, int CY, bool kAlongX = false>
 __global__ void __launch_bounds__(kTileX *kTileY / CY)
     k_lattice(const Inst I, S *__restrict__ pool, const BeadTab tab, const unsigned *__restrict__ mask_read,
               const unsigned *__restrict__ mask_prev, unsigned *__restrict__ mask_clear, const int parity,
               const int early_load, const int early_cold) {
-    lattice_tile<S, CY, true>(I, pool, tab, mask_read, mask_prev, mask_clear, blockIdx.x, blockIdx.y, parity,
+    lattice_tile<S, CY, true, kAlongX>(I, pool, tab, mask_read, mask_prev, mask_clear, blockIdx.x, blockIdx.y, parity,
                               early_load, early_cold, (blockIdx.x | blockIdx.y) == 0, threadIdx.x, threadIdx.y);
 }
 
@@ -206,11 +211,11 @@ template <class S, int CY> struct BatchMinBlocks {
     static constexpr int value = std::is_same<S, double>::value ? 4 : (CY == 1 ? 8 : 7);
 };
 // Which batched shapes use the precomputed pull offsets.
-template <class S, int CY> struct BatchInner {
-    static constexpr bool value = CY == 1 && !std::is_same<S, double>::value;
+template <class S, int CY, bool kAlongX> struct BatchInner {
+    static constexpr bool value = (CY == 1 || kAlongX) && !std::is_same<S, double>::value;
 };
 
-template <class S, int CY>
+template <class S, int CY, bool kAlongX = false>
 __global__ void __launch_bounds__(kTileX *kTileY / CY, BatchMinBlocks<S, CY>::value)
     k_lattice_batch(const Inst *__restrict__ insts, const int2 *__restrict__ tiles, S *__restrict__ pool,
                     const BeadTab tab0, const BeadTab tab1, const unsigned *__restrict__ mask_read,
@@ -221,12 +226,12 @@ __global__ void __launch_bounds__(kTileX *kTileY / CY, BatchMinBlocks<S, CY>::va
     {
         const unsigned *src = (const unsigned *)(insts + t.x);
         unsigned *dst = (unsigned *)&sI;
-        const int tid = threadIdx.y * kTileX + threadIdx.x;
+        const int tid = threadIdx.y * blockDim.x + threadIdx.x;
         for (int wd = tid; wd < (int)(sizeof(Inst) / 4); wd += kTileX * kTileY / CY) dst[wd] = src[wd];
     }
     __syncthreads();
     const int parity = gparity ^ sI.par_xor;
-    lattice_tile<S, CY, BatchInner<S, CY>::value>(sI, pool, parity ? tab1 : tab0, mask_read, mask_prev, mask_clear,
+    lattice_tile<S, CY, BatchInner<S, CY, kAlongX>::value, kAlongX>(sI, pool, parity ? tab1 : tab0, mask_read, mask_prev, mask_clear,
                                                   t.y & 0xffff, t.y >> 16, parity, early_load, early_cold,
                                                   blockIdx.x == 0, threadIdx.x, threadIdx.y);
 }
@@ -684,9 +689,9 @@ static cudaError_t lattice_v(int variant, const Inst &I, void *pool, BeadTab tab
                                   after_beads, ec);
     }
     if (variant == 1) {
-        const cudaLaunchConfig_t cfg = sweep_config(grid, dim3(kTileX, kTileY / 2), after_beads, st, attr);
-        return cudaLaunchKernelEx(&cfg, k_lattice<S, 2>, I, (S *)pool, tab, mk.read, mk.prev, mk.clear, parity,
-                                  after_beads, ec);
+        const cudaLaunchConfig_t cfg = sweep_config(grid, dim3(kTileX / 2, kTileY), after_beads, st, attr);
+        return cudaLaunchKernelEx(&cfg, k_lattice<S, 2, true>, I, (S *)pool, tab, mk.read, mk.prev, mk.clear,
+                                  parity, after_beads, ec);
     }
     const cudaLaunchConfig_t cfg = sweep_config(grid, dim3(kTileX, kTileY), after_beads, st, attr);
     return cudaLaunchKernelEx(&cfg, k_lattice<S, 1>, I, (S *)pool, tab, mk.read, mk.prev, mk.clear, parity,
@@ -717,9 +722,9 @@ static cudaError_t lattice_batch_v(int variant, const Inst *insts, const int2 *t
                                   mk.prev, mk.clear, gparity, after_beads, ec);
     }
     if (variant == 1) {
-        const cudaLaunchConfig_t cfg = sweep_config(grid, dim3(kTileX, kTileY / 2), after_beads, st, attr);
-        return cudaLaunchKernelEx(&cfg, k_lattice_batch<S, 2>, insts, tiles, (S *)pool, tab0, tab1, mk.read,
-                                  mk.prev, mk.clear, gparity, after_beads, ec);
+        const cudaLaunchConfig_t cfg = sweep_config(grid, dim3(kTileX / 2, kTileY), after_beads, st, attr);
+        return cudaLaunchKernelEx(&cfg, k_lattice_batch<S, 2, true>, insts, tiles, (S *)pool, tab0, tab1,
+                                  mk.read, mk.prev, mk.clear, gparity, after_beads, ec);
     }
     const cudaLaunchConfig_t cfg = sweep_config(grid, dim3(kTileX, kTileY), after_beads, st, attr);
     return cudaLaunchKernelEx(&cfg, k_lattice_batch<S, 1>, insts, tiles, (S *)pool, tab0, tab1, mk.read, mk.prev,
