@@ -136,6 +136,30 @@ def test_batch_vector_variant(fpd, precision, tol):
     b.close()
 
 
+@pytest.mark.parametrize("precision,tol", [(0, 1e-13), (1, 1e-5), (2, 1e-2)])
+def test_batch_two_cells_along_x(fpd, precision, tol):
+    # variant 1 in a batch (two cells 16 apart along x per thread, precomputed
+    # pull offsets in inner tiles in the reduced precisions): each instance
+    # agrees with the instance alone to rounding
+    cases = _cases(precision) + [wl.couette_only(100, 72, u=0.01, nu=0.2, precision=precision)]
+    steps = [41, 60, 17, 33, 25]
+    b = fpd.Batch(precision, max_slots=8, pool_bytes=64 << 20, max_beads=256)
+    b.set_tuning(1)
+    slots = [b.add(c, n) for c, n in zip(cases, steps)]
+    while b.run(1000):
+        pass
+    w = (np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4))[:, None, None]
+    for c, n, s in zip(cases, steps, slots):
+        fa, ba = b.populations(s), b.beads(s)
+        fb, bb = _alone(fpd, c, n)
+        e = np.sqrt(np.sum((fa - fb) ** 2) / np.sum((fb - w) ** 2))
+        print(f"batch variant 1 vs alone variant 0, precision {precision}, nx {c['nx']}: rel L2 {e:.2e}")
+        assert e < tol
+        if ba[0].size:
+            assert np.abs(ba[0] - bb[0]).max() < tol * 1e-2
+    b.close()
+
+
 def test_staggered_admission_and_slot_reuse(fpd):
     cases = _cases(1)
     b = fpd.Batch(1, max_slots=3, pool_bytes=64 << 20, max_beads=128)

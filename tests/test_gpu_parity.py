@@ -299,8 +299,8 @@ def test_graph_chunks_equal_direct_steps(precision):
 @pytest.mark.parametrize("variant", [1, 2])
 @pytest.mark.parametrize("precision,tol", [(0, 1e-13), (1, 1e-5), (2, 1e-2)])
 def test_sweep_variants_agree(precision, tol, variant):
-    # the autotuner's launch shapes (1 or 2 cells per thread along y, or a
-    # vector of cells along x) compute the same arithmetic; the compiler may
+    # the autotuner's launch shapes (1 cell per thread, 2 cells 16 apart
+    # along x, or a vector of cells along x) compute the same arithmetic; the compiler may
     # contract multiply-adds differently in each instantiation, so they
     # agree to rounding, not bit for bit.  nx = 76: a multiple of the vector
     # width whose last tile is 12 cells wide; ny = 45: ragged rows too
@@ -353,6 +353,26 @@ def test_vector_sweep_fp64_parity(seed, nx, ny, N, NF, a, xi, coll):
                           gx=float(rng.uniform(-1e-6, 1e-6)))
     g = gpu_sim(cfg)
     g.set_tuning(2)
+    o = orc_sim(cfg)
+    g.step(301)
+    o.step(301)
+    compare_f64(g, o)
+
+
+@pytest.mark.parametrize("seed,nx,ny,N,NF,a,xi,coll", [
+    (41, 90, 37, 5, 1, 2.0, 1.0, 0),    # last tile 26 wide: 10 of its threads hold a second cell
+    (42, 76, 45, 6, 2, 2.0, 0.5, 1),    # last tile 12 wide: no second cell there
+    (43, 20, 17, 3, 1, 2.0, 1.0, 2),    # one tile column: columns 16..19 are second cells, BGK
+    (44, 97, 70, 6, 1, 2.0, 1.0, 0),    # inner tiles (precomputed offsets) beside edge tiles
+    (45, 7, 9, 3, 1, 1.0, 0.5, 0),      # narrower than the 16-column split
+])
+def test_two_cells_along_x_fp64_parity(seed, nx, ny, N, NF, a, xi, coll):
+    # variant 1: each thread owns the cells x and x + 16 of one tile row
+    rng = np.random.default_rng(seed)
+    cfg = wl.random_fiber(rng, nx, ny, n_beads=N, a=a, xi=xi, n_fibers=NF, collision=coll,
+                          gx=float(rng.uniform(-1e-6, 1e-6)))
+    g = gpu_sim(cfg)
+    g.set_tuning(1)
     o = orc_sim(cfg)
     g.step(301)
     o.step(301)
