@@ -3,8 +3,9 @@
 Each sweep variant (see fpd_set_tuning) is timed with CUDA events on a
 scratch instance of the same workload (same parameters, so the same hot
 tiles), after warm-up, and the fastest is returned and cached per GPU,
-precision and lattice size in a JSON file ($FPD_TUNING_CACHE, default
-~/.cache/fpd_gb300/tuning.json).  Variants compute the same arithmetic
+library build, precision and lattice size in a JSON file
+($FPD_TUNING_CACHE, default ~/.cache/fpd_gb300/tuning.json): a rebuilt
+library (changed kernels) is timed afresh.  Variants compute the same arithmetic
 (they differ only in how the compiler contracts multiply-adds, i.e. at the
 rounding level), so the choice only affects speed.
 """
@@ -21,8 +22,20 @@ def _cache_path() -> str:
                           os.path.join(os.path.expanduser("~"), ".cache", "fpd_gb300", "tuning.json"))
 
 
+def _lib_tag() -> str:
+    """Short tag of the built library: its build stamp (a hash of the
+    sources, flags and machine), or "unbuilt"."""
+    from . import build
+    try:
+        with open(os.path.join(build.OUT_DIR, "stamp")) as f:
+            return f.read().strip()[:12] or "unbuilt"
+    except OSError:
+        return "unbuilt"
+
+
 def _key(cfg: dict, gpu: str) -> str:
-    return f"{gpu}|p{cfg.get('precision', 0)}|{cfg['nx']}x{cfg['ny']}|nb{cfg.get('n_beads', 0) * cfg.get('n_fibers', 0)}"
+    return (f"{gpu}|lib{_lib_tag()}|p{cfg.get('precision', 0)}|{cfg['nx']}x{cfg['ny']}"
+            f"|nb{cfg.get('n_beads', 0) * cfg.get('n_fibers', 0)}")
 
 
 def _load() -> dict:

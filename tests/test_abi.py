@@ -142,3 +142,18 @@ def test_bead_export_rejects_a_null_handle(lib):
     buf = (ctypes.c_double * 7)()
     assert lib.fpd_export_beads(None, 4) == fpd.FPD_EINVAL
     assert lib.fpd_take_beads(None, 2, ctypes.cast(buf, fpd._DP)) == fpd.FPD_EINVAL
+
+
+def test_autotune_cache_key_names_the_library_build(tmp_path, monkeypatch):
+    # cached launch-shape timings belong to one build of the kernels: a
+    # rebuilt library (another stamp) must not reuse them
+    from paper_2212_14153_gb300 import autotune, build
+    from paper_2212_14153_gb300 import workloads as wl
+    cfg = wl.couette_only(40, 24, precision=1)
+    monkeypatch.setattr(build, "OUT_DIR", str(tmp_path))
+    assert "|libunbuilt|" in autotune._key(cfg, "GPU")
+    (tmp_path / "stamp").write_text("a" * 64)
+    k1 = autotune._key(cfg, "GPU")
+    (tmp_path / "stamp").write_text("b" * 64)
+    k2 = autotune._key(cfg, "GPU")
+    assert k1 != k2 and "|p1|40x24|" in k1
