@@ -191,13 +191,25 @@ __device__ __forceinline__ void lattice_tile(const Inst &I, S *__restrict__ pool
     }
 }
 
+// Tile order of a single-lattice sweep.  Every other step takes the tiles
+// in reverse order, so that it starts on the tiles the previous sweep wrote
+// last, whose populations are still in L2 (a lattice larger than L2 is
+// otherwise read back in the order it was written, which under LRU evicts
+// each line before it is read again).  Which tile a CTA takes changes
+// nothing in its arithmetic.  The lead CTA (the first dispatched) is
+// blockIdx 0 either way.  The batched sweep keeps its tile list in order
+// (its state is many times the L2: reversing measured no gain there).
+__device__ __forceinline__ int tile_order(int b, int n, int parity) { return (parity & 1) ? n - 1 - b : b; }
+
 template <class S, int CY, bool kAlongX = false>
 __global__ void __launch_bounds__(kTileX *kTileY / CY)
     k_lattice(const Inst I, S *__restrict__ pool, const BeadTab tab, const unsigned *__restrict__ mask_read,
               const unsigned *__restrict__ mask_prev, unsigned *__restrict__ mask_clear, const int parity,
               const int early_load, const int early_cold) {
-    lattice_tile<S, CY, true, kAlongX>(I, pool, tab, mask_read, mask_prev, mask_clear, blockIdx.x, blockIdx.y, parity,
-                              early_load, early_cold, (blockIdx.x | blockIdx.y) == 0, threadIdx.x, threadIdx.y);
+    lattice_tile<S, CY, true, kAlongX>(I, pool, tab, mask_read, mask_prev, mask_clear,
+                                       tile_order(blockIdx.x, gridDim.x, parity),
+                                       tile_order(blockIdx.y, gridDim.y, parity), parity, early_load, early_cold,
+                                       (blockIdx.x | blockIdx.y) == 0, threadIdx.x, threadIdx.y);
 }
 
 // Batched sweep over a packed tile list: tiles[t] = (instance slot,
@@ -438,8 +450,9 @@ __global__ void __launch_bounds__(kTileX / VecWidth<S>::value * kTileY)
     k_lattice_vec(const Inst I, S *__restrict__ pool, const BeadTab tab, const unsigned *__restrict__ mask_read,
                   const unsigned *__restrict__ mask_prev, unsigned *__restrict__ mask_clear, const int parity,
                   const int early_load, const int early_cold) {
-    lattice_tile_vec<S>(I, pool, tab, mask_read, mask_prev, mask_clear, blockIdx.x, blockIdx.y, parity, early_load,
-                        early_cold, (blockIdx.x | blockIdx.y) == 0);
+    lattice_tile_vec<S>(I, pool, tab, mask_read, mask_prev, mask_clear, tile_order(blockIdx.x, gridDim.x, parity),
+                        tile_order(blockIdx.y, gridDim.y, parity), parity, early_load, early_cold,
+                        (blockIdx.x | blockIdx.y) == 0);
 }
 
 // The column form needs more registers than the vector form: cap them at
