@@ -133,6 +133,121 @@ def pick_variant(args, cfg):
 
 
 # ------------------------------------------------------------------ GPU arm
+def gpu_state(fpd, cfg, precision, variant, steps, stream):
+    """(u_x, u_y, R) after `steps` steps of cfg at this precision and sweep
+    variant, run as the timed region runs it (graph chunks)."""
+    s = fpd.Simulation(dict(cfg, precision=precision), stream=stream.cuda_stream)
+    s.set_tuning(variant)
+    s.step(steps)
+    ux, uy, _ = s.fields()
+    R = s.beads()[0]
+    s.close()
+    return ux, uy, R
+
+
+def accuracy_vs_fp64(fpd, cfg, precision, variant, steps, stream):
+    """The timed configuration against FP64 storage (the path pinned to the
+    oracle at 1e-12) after a short run."""
+    ux64, uy64, R64 = gpu_state(fpd, cfg, 0, variant, steps, stream)
+    ux, uy, R = gpu_state(fpd, cfg, precision, variant, steps, stream)
+    u64 = np.concatenate([ux64.ravel(), uy64.ravel()])
+    u = np.concatenate([ux.ravel(), uy.ravel()])
+    return {"vs": "FP64 storage on this GPU (pinned to the oracle at 1e-12)", "steps": steps,
+            "sweep_variant": variant, "u_rel_l2": float(np.linalg.norm(u - u64) / np.linalg.norm(u64)),
+            "bead_max_dR": float(np.abs(R - R64).max())}
+
+
+def batched_leg(fpd, workloads, stream, n_inst: int, steps: int, warm: int = 8) -> dict:
+    """The batched sweep (n_inst instances drawn as the shape-diagram sweep,
+    FP32) against the plain loop that runs the same instances one at a time
+    with the same kernels, and the bit-identity of two instances with their
+    lone runs."""
+    import torch
+    from paper_2212_14153_gb300 import serve
+    inst = workloads.batched_sweep(n=n_inst, seed=4, precision=1)
+    cells = [c["nx"] * c["ny"] for c in inst]
+    pool = sum(serve.state_bytes(c, 1) + 4096 for c in inst)
+    nbeads = sum(c["n_beads"] * c["n_fibers"] for c in inst)
+    b = fpd.Batch(1, len(inst), pool, nbeads, stream=stream.cuda_stream)
+    slots = [b.add(c, warm + steps) for c in inst]
+    b.run(warm)
+    b.sync()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    done = 0
+    while done < steps:
+        d = b.run(steps - done)
+        if d == 0:
+            break
+        done += d
+    e1.record(stream)
+    e1.synchronize()
+    t_batch = e0.elapsed_time(e1) * 1e-3
+    b.poll()
+    check = {}
+    for i in (0, len(inst) // 2):
+        fb, Rb = b.populations(slots[i]), b.beads(slots[i])[0]
+        s1 = fpd.Simulation(inst[i], stream=stream.cuda_stream)
+        s1.step(warm + steps)
+        check[i] = bool(np.array_equal(fb, s1.populations()) and np.array_equal(Rb, s1.beads()[0]))
+        s1.close()
+    b.close()
+    t_plain = 0.0
+    for c in inst:
+        s1 = fpd.Simulation(c, stream=stream.cuda_stream)
+        s1.step(warm)
+        s1.sync()
+        e0.record(stream)
+        s1.step(steps)
+        e1.record(stream)
+        e1.synchronize()
+        t_plain += e0.elapsed_time(e1) * 1e-3
+        s1.close()
+    batched = sum(cells) * steps / t_batch / 1e6
+    plain = sum(cells) * steps / t_plain / 1e6
+    return {"workload": "batched_sweep", "instances": len(inst), "cells": sum(cells), "beads": nbeads,
+            "steps": steps, "storage": "f32", "sweep_variant": 0, "value": round(batched, 1), "unit": "MLUPS",
+            "plain_loop": round(plain, 1), "speedup": round(batched / plain, 2),
+            "ms_per_step": t_batch * 1e3 / steps,
+            "roofline_frac": round(72 * sum(cells) * steps / t_batch / 1e9 / measured_peaks()["hbm_gbs"], 4),
+            "bit_identical_to_alone": check,
+            "accuracy": "every instance bit-identical to its lone run (checked here on two)"}
+
+
+def fp16_leg(args, fpd, workloads, stream, steps: int = 2000) -> dict:
+    """The two-fiber step with FP16 storage (FP32 math): whole-step and
+    sweep-kernel rooflines at 36 B per cell update, and accuracy against FP64
+    storage in the same launch shape."""
+    import torch
+    cfg = workloads.two_fiber_large(seed=3, precision=2)
+    cells = cfg["nx"] * cfg["ny"]
+    variant, variant_ms = pick_variant(args, cfg)
+    sim = fpd.Simulation(cfg, stream=stream.cuda_stream)
+    sim.set_tuning(variant)
+    sim.step(max(args.warmup, 32))
+    sim.sync()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(steps)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    sim.set_profiling(True)
+    sim.step(steps)
+    kt = sim.kernel_times()
+    sim.set_profiling(False)
+    sim.close()
+    peak = measured_peaks()["hbm_gbs"]
+    lat_ms = kt["lattice_ms"] / max(kt["lattice_launches"], 1)
+    return {"workload": cfg["name"], "storage": "f16x2^s", "sweep_variant": variant, "variant_ms_per_step": variant_ms,
+            "steps": steps, "ms_per_step": ms, "value": round(cells / (ms * 1e-3) / 1e6, 1), "unit": "MLUPS",
+            "step_frac": round(36 * cells / (ms * 1e-3) / 1e9 / peak, 4),
+            "kernel_ms": lat_ms, "kernel_frac": round(36 * cells / (lat_ms * 1e-3) / 1e9 / peak, 4),
+            "accuracy": accuracy_vs_fp64(fpd, cfg, 2, variant, args.accuracy_steps, stream)}
+
+
 def run_gpu(args, rank: int, world: int):
     import torch
     from paper_2212_14153_gb300 import build, fpd, replicas, workloads
@@ -201,6 +316,7 @@ def run_gpu(args, rank: int, world: int):
     sim.export_beads(4)
     dst = np.empty(7 * max(nb, 1))
     taken = 0.0
+    t_loop0 = time.perf_counter()
     for i in range(e2e_steps):
         sim.step(1)
         n = i + 1
@@ -213,6 +329,7 @@ def run_gpu(args, rank: int, world: int):
     if e2e_steps >= 2:
         sim.take_beads(e2e_steps, dst)
         taken += dst[0]
+    t_loop = time.perf_counter() - t_loop0
     ux, uy, rho = sim.fields()
     sim.close()
     e2e_s = time.perf_counter() - t0
@@ -226,18 +343,15 @@ def run_gpu(args, rank: int, world: int):
     # precision, after a short run
     accuracy = None
     if rank == 0 and args.precision != 0 and args.accuracy_steps > 0:
-        runs = []
-        for prec in (0, args.precision):
-            s2 = fpd.Simulation(dict(cfg, precision=prec), stream=stream.cuda_stream)
-            s2.step(args.accuracy_steps)
-            ux, uy, _ = s2.fields()
-            R = s2.beads()[0]
-            s2.close()
-            runs.append((np.concatenate([ux.ravel(), uy.ravel()]), R))
-        (u64, R64), (u, R) = runs
-        accuracy = {"vs": "FP64 storage on this GPU (pinned to the oracle at 1e-12)", "steps": args.accuracy_steps,
-                    "u_rel_l2": float(np.linalg.norm(u - u64) / np.linalg.norm(u64)),
-                    "bead_max_dR": float(np.abs(R - R64).max())}
+        accuracy = accuracy_vs_fp64(fpd, cfg, args.precision, variant, args.accuracy_steps, stream)
+
+    # batched sweep against the plain loop, and the FP16-storage step, on
+    # the same GPU (fixed sizes, independent of --steps)
+    batched = fp16 = None
+    if rank == 0 and not args.no_extras:
+        batched = batched_leg(fpd, workloads, stream, args.batched_instances, args.batched_steps)
+        if args.precision != 2:
+            fp16 = fp16_leg(args, fpd, workloads, stream)
 
     if rank == 0:
         peaks = measured_peaks()
@@ -279,23 +393,37 @@ def run_gpu(args, rank: int, world: int):
             "gpu_launches": gpu_launches,
             "e2e": {"value": round(e2e_mlups, 1), "unit": "MLUPS", "h2d_bytes_per_step": h2d_total / e2e_steps,
                     "d2h_bytes_per_step": d2h_total / e2e_steps, "steps": e2e_steps,
+                    # the step loop alone (per step: fpd_step(1) and the host
+                    # taking that step's bead table), without create, the
+                    # final field read and destroy, which a run of e2e_steps
+                    # amortises
+                    "per_step_value": round(cells * e2e_steps / t_loop / 1e6, 1),
+                    "per_step_d2h_bytes": d2h_step,
+                    "create_read_destroy_s": round(e2e_s - t_loop, 4),
                     "api": "fpd_create, fpd_export_beads(4), per step fpd_step(1) + fpd_take_beads of the previous "
                            "step (the bead phase writes each table into a host ring), fpd_read_fields, fpd_destroy"},
             "clocks": clocks,
             "mass_after": diag[0],
             "accuracy": accuracy,
+            "batched": batched,
+            "fp16": fp16,
         }
         if not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(cfg, budget_s=args.cpu_seconds)
+            line["cpu_baseline"] = cpu_baseline(
+                cfg, budget_s=args.cpu_seconds,
+                gpu_run=lambda n: gpu_state(fpd, cfg, args.precision, variant, n, stream))
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
 
 
 # ------------------------------------------------------------------ CPU oracle
-def cpu_baseline(cfg: dict, budget_s: float = 12.0, steps: int | None = None) -> dict:
+def cpu_baseline(cfg: dict, budget_s: float = 12.0, steps: int | None = None, gpu_run=None) -> dict:
     """The FP64 oracle, as it stands, on this host's cores: whole time steps of
-    the same workload until about budget_s seconds (or a fixed step count)."""
+    the same workload until about budget_s seconds (or a fixed step count).
+    gpu_run(n), if given, returns the GPU's (u_x, u_y, R) after n steps of the
+    timed configuration; they are compared with the oracle's state after its
+    timed steps."""
     import oracle
     cores = os.cpu_count() or 1
     o = oracle.Sim(dict(cfg, threads=cores))
@@ -310,6 +438,16 @@ def cpu_baseline(cfg: dict, budget_s: float = 12.0, steps: int | None = None) ->
             break
     out = {"value": round(cells * n / el / 1e6, 3), "unit": "MLUPS", "cores": cores, "kind": "oracle",
            "sample": f"{n} full steps of {cfg['name']} ({cells} cells) in {el:.1f} s"}
+    if gpu_run is not None:
+        ux, uy, R = gpu_run(n)
+        oux, ouy, _ = o.fields()
+        oR = o.beads()[0]
+        ou = np.concatenate([oux.ravel(), ouy.ravel()])
+        out["gpu_vs_oracle"] = {
+            "steps": n, "what": "the timed configuration (precision, sweep variant, graph chunks) on the GPU",
+            "u_rel_l2": float(np.linalg.norm(np.concatenate([ux.ravel(), uy.ravel()]) - ou) / np.linalg.norm(ou)),
+            "R_rel_l2": float(np.linalg.norm(R - oR) / np.linalg.norm(oR)),
+            "bead_max_dR": float(np.abs(R - oR).max())}
     # the same oracle on one thread (the canonical single-core baseline), a
     # shorter sample
     o1 = oracle.Sim(dict(cfg, threads=1))
@@ -437,6 +575,28 @@ def run_sweep(args, rank: int, world: int):
     return batched
 
 
+def measure_capacity(reqs, precision, steps: int = 256, warm: int = 8) -> float:
+    """Aggregate MLUPS of the batched engine with all of reqs resident."""
+    import torch
+    from paper_2212_14153_gb300 import fpd, serve
+    stream = torch.cuda.Stream()
+    pool = sum(serve.state_bytes(r, precision) + 4096 for r in reqs)
+    nbeads = sum(r["n_beads"] * r["n_fibers"] for r in reqs)
+    b = fpd.Batch(precision, len(reqs), pool, nbeads, stream=stream.cuda_stream)
+    for r in reqs:
+        b.add(r, warm + steps)
+    b.run(warm)
+    b.sync()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.run(steps)
+    e1.record(stream)
+    e1.synchronize()
+    b.close()
+    return sum(r["nx"] * r["ny"] for r in reqs) * steps / (e0.elapsed_time(e1) * 1e-3) / 1e6
+
+
 def run_serve(args, rank: int, world: int):
     """Serving: Poisson arrivals of sweep-point requests at 0.5x and 1.2x the
     measured batched capacity; continuous batching under an HBM cap."""
@@ -448,7 +608,12 @@ def run_serve(args, rank: int, world: int):
     probe = workloads.serving_requests(args.serve_requests, 1.0, seed=5, steps_lo=args.serve_steps_lo,
                                        steps_hi=args.serve_steps_hi, precision=args.precision)
     work = np.mean([r["nx"] * r["ny"] * r["steps"] for r in probe])
-    capacity = args.capacity_mlups * 1e6 / work  # requests / s the batch can sustain
+    cap_mlups = args.capacity_mlups
+    cap_how = "given (--capacity-mlups)"
+    if cap_mlups <= 0:
+        cap_mlups = measure_capacity(probe[:args.max_slots], args.precision)
+        cap_how = f"measured: batched rate of the first {min(len(probe), args.max_slots)} requests resident at once"
+    capacity = cap_mlups * 1e6 / work  # requests / s the batch can sustain
     for load in (0.5, 1.2):
         reqs = workloads.serving_requests(args.serve_requests, load * capacity, seed=5, steps_lo=args.serve_steps_lo,
                                           steps_hi=args.serve_steps_hi, precision=args.precision)
@@ -468,7 +633,9 @@ def run_serve(args, rank: int, world: int):
         "higher_is_better": True, "dtype": {0: "f64", 1: "f32", 2: "f32"}[args.precision], "data": "synthetic",
         "config": {"workload": "serving", "requests": args.serve_requests,
                    "steps_per_request": [args.serve_steps_lo, args.serve_steps_hi], "chunk": args.chunk,
-                   "cap_bytes": args.cap_bytes, "capacity_mlups_assumed": args.capacity_mlups},
+                   "cap_bytes": args.cap_bytes, "capacity_mlups": round(cap_mlups, 1), "capacity": cap_how,
+                   "latency": "arrival to result on the host; admission happens at chunk boundaries, so it "
+                              "includes up to one chunk of waiting"},
         "loads": out,
     }
     print(json.dumps(line), flush=True)
@@ -491,11 +658,15 @@ def main():
     ap.add_argument("--serve-steps-lo", type=int, default=50000)
     ap.add_argument("--serve-steps-hi", type=int, default=500000)
     ap.add_argument("--serve-requests", type=int, default=128)
-    ap.add_argument("--capacity-mlups", type=float, default=40000.0)
     ap.add_argument("--cap-bytes", type=int, default=150 << 30)
     ap.add_argument("--max-slots", type=int, default=512)
     ap.add_argument("--chunk", type=int, default=500)
     ap.add_argument("--variant", default="auto", choices=["auto", "0", "1", "2"])
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched and FP16 sub-measurements")
+    ap.add_argument("--batched-instances", type=int, default=128)
+    ap.add_argument("--batched-steps", type=int, default=64)
+    ap.add_argument("--capacity-mlups", type=float, default=0.0,
+                    help="serving capacity; 0 = measure the batched rate of the same requests first")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define FPD_ABI_VERSION 2
+#define FPD_ABI_VERSION 3
 
 typedef enum {
     FPD_OK = 0,
@@ -141,8 +141,31 @@ int fpd_create_ex(const fpd_params *p, void *stream, void *workspace, uint64_t w
  * returns launch errors only. */
 int fpd_step(fpd_sim *s, int64_t n_steps);
 
-/* Block until all work of s has finished; report device-side errors. */
+/* Block until all work of s has finished; report device-side errors:
+ * FPD_ECUDA for a failed launch or kernel, FPD_ENAN once FPD_FLAG_NONFINITE
+ * is set (see fpd_flags). */
 int fpd_sync(fpd_sim *s);
+
+/* Sticky status bits of an instance, set on the device while it runs and
+ * kept until fpd_load replaces its state.  The paper has no counterpart:
+ * they guard the method's assumptions and report divergence.
+ *   FPD_FLAG_FAST_BEAD: a bead velocity component reached 0.5 cells per
+ *     step (Eq. 5 gave |V_x| or |V_y| >= 0.5), far outside the low-Mach
+ *     range of the lattice Boltzmann fluid (c_s = 0.577).  The sweep's early
+ *     update of tiles no bead marked assumes beads move less than a cell per
+ *     step; from the step after the flag is set every tile of the instance
+ *     waits for its bead phase instead, so results stay those of the
+ *     waiting path.
+ *   FPD_FLAG_NONFINITE: a non-finite bead velocity, or a non-finite
+ *     population found by the watchdog, a pass over the populations that
+ *     runs whenever the step count crosses a multiple of 1024.  fpd_sync and
+ *     the calls that synchronise then return FPD_ENAN. */
+#define FPD_FLAG_FAST_BEAD 1u
+#define FPD_FLAG_NONFINITE 2u
+
+/* Synchronise and copy the status bits of s into *flags (no error for a
+ * set bit).  FPD_EINVAL for a NULL argument. */
+int fpd_flags(fpd_sim *s, uint32_t *flags);
 
 /* Copy the macroscopic fields to caller-owned host arrays of ny*nx doubles
  * (row-major [j][i], cell centre (i + 1/2, j + 1/2)): velocity
@@ -327,13 +350,21 @@ int fpd_batch_set_tuning(fpd_batch *b, int32_t variant);
 /* Block until the batch's work has finished. */
 int fpd_batch_sync(fpd_batch *b);
 
-/* Synchronise, then list up to `capacity` finished instances not listed
- * before (done_slots may be NULL to only count them). */
+/* Synchronise, then list up to `capacity` instances that finished or
+ * failed and were not listed before (done_slots may be NULL to only count
+ * them).  An instance whose status has FPD_FLAG_NONFINITE set (a non-finite
+ * bead velocity, or a non-finite population found by the watchdog pass that
+ * every fpd_batch_run ends with and that also runs each time the global
+ * step count crosses a multiple of 1024) is stopped and listed as failed
+ * (state 3 in fpd_batch_slot_info); the other instances run on unchanged. */
 int fpd_batch_poll(fpd_batch *b, int32_t *done_slots, int32_t capacity, int32_t *n_done);
 
 /* out = {nx, ny, beads, steps done, steps requested, state (0 free,
- * 1 running, 2 finished)}. */
+ * 1 running, 2 finished, 3 failed: non-finite state)}. */
 int fpd_batch_slot_info(fpd_batch *b, int32_t slot, int64_t out[6]);
+
+/* As fpd_flags for one slot (running, finished or failed). */
+int fpd_batch_slot_flags(fpd_batch *b, int32_t slot, uint32_t *flags);
 
 /* As fpd_read_fields / fpd_read_beads / fpd_read_populations for one slot
  * (running or finished).  Synchronise. */

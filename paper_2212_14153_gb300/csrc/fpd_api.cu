@@ -315,7 +315,7 @@ int enqueue_step(fpd_sim *s, cudaStream_t st, int64_t t, bool profiled) {
         }
         e = fpd::launch_beads(s->precision, s->inst_d, nullptr, I.nb, s->pool, s->tab[0], s->tab[1],
                               s->masks[t % fpd::kMaskBufs], parity, 1, s->counters, profiled ? 0 : 1, st,
-                              fpd::BeadExport{s->ex_ring_d, s->ex_count, s->ex_slots, s->ex_stride});
+                              fpd::BeadExport{s->ex_ring_d, s->ex_count, s->ex_slots, s->ex_stride}, s->status);
         if (e != cudaSuccess) return cuda_fail(s, e, "bead kernel launch");
         if (profiled) {
             cudaEventRecord(b, st);
@@ -333,7 +333,7 @@ int enqueue_step(fpd_sim *s, cudaStream_t st, int64_t t, bool profiled) {
     // from step 1 on, the previous bead phase (or the initial marks) is in
     // the previous buffer
     const fpd::SweepMasks mk{s->masks[t % M], s->masks[(t + M - 1) % M], s->masks[(t + 1) % M],
-                             (t >= 1 && s->early_cold) ? 1 : 0};
+                             (t >= 1 && s->early_cold) ? 1 : 0, s->status};
     e = fpd::launch_lattice(s->precision, s->inst_d, I, s->pool, s->tab[parity], mk, parity, after_beads,
                             s->variant, st);
     if (e != cudaSuccess) return cuda_fail(s, e, "lattice kernel launch");
@@ -457,7 +457,8 @@ StateLayout state_layout(const fpd::Inst &I, size_t elem) {
     L.tab = up(L.pool + L.pool_bytes);
     L.masks = up(L.tab + L.tab_bytes);
     L.counters = up(L.masks + L.mask_bytes);
-    L.inst = up(L.counters + 16);  // last-block counter, then the 64-bit export counter at +8
+    // last-block counter, the 64-bit export counter at +8, the status word at +16
+    L.inst = up(L.counters + 32);
     L.total = up(L.inst + sizeof(fpd::Inst));
     return L;
 }
@@ -554,6 +555,7 @@ int create_impl(const fpd_params *p, void *stream, void *workspace, uint64_t wor
     s->mask_bytes = L.mask_bytes;
     s->counters = (unsigned *)(base + L.counters);
     s->ex_count = (unsigned long long *)(base + L.counters + 8);
+    s->status = (unsigned *)(base + L.counters + 16);
     s->inst_d = (fpd::Inst *)(base + L.inst);
     FPD_TRY(cudaMemcpyAsync(s->inst_d, &I, sizeof I, cudaMemcpyHostToDevice, s->stream), "copy instance");
     FPD_TRY(fpd::launch_init(s->precision, s->inst_d, I, s->pool, p->init_couette, s->stream), "init kernel");
@@ -583,6 +585,16 @@ int create_impl(const fpd_params *p, void *stream, void *workspace, uint64_t wor
 int fpd_step(fpd_sim *s, int64_t n_steps) {
     if (!s) return fail(nullptr, FPD_EINVAL, "fpd_step: NULL handle");
     if (n_steps < 0) return fail(s, FPD_EINVAL, "n_steps must be >= 0");
+    // watchdog: a pass over the populations each time the step count has
+    // crossed a multiple of kWatchSteps (between chunks, never inside one)
+    auto watch_if_due = [s]() -> int {
+        if (s->nstep < s->watch_next) return FPD_OK;
+        cudaError_t e = fpd::launch_watch(s->precision, nullptr, s->inst, nullptr, 0, s->pool, (int)(s->nstep & 1),
+                                          s->status, s->stream);
+        if (e != cudaSuccess) return cuda_fail(s, e, "watchdog launch");
+        s->watch_next = (s->nstep / fpd::kWatchSteps + 1) * fpd::kWatchSteps;
+        return FPD_OK;
+    };
     while (n_steps > 0) {
         // whole chunks of the step loop replay a captured graph (one launch
         // instead of two per step); the first step, remainders and profiled
@@ -597,12 +609,15 @@ int fpd_step(fpd_sim *s, int64_t n_steps) {
             if (e != cudaSuccess) return cuda_fail(s, e, "graph launch");
             s->nstep += fpd::kGraphSteps;
             n_steps -= fpd::kGraphSteps;
+            int rc = watch_if_due();
+            if (rc != FPD_OK) return rc;
             continue;
         }
         int rc = enqueue_step(s, s->stream, s->nstep, s->profiling);
         if (rc != FPD_OK) return rc;
         s->nstep++;
         --n_steps;
+        if ((rc = watch_if_due()) != FPD_OK) return rc;
     }
     return FPD_OK;
 }
@@ -633,6 +648,22 @@ int fpd_sync(fpd_sim *s) {
     if (!s) return fail(nullptr, FPD_EINVAL, "fpd_sync: NULL handle");
     cudaError_t e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "stream synchronize");
+    unsigned flags = 0;
+    e = cudaMemcpy(&flags, s->status, sizeof flags, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(s, e, "read status");
+    if (flags & fpd::kFlagNonFinite)
+        return fail(s, FPD_ENAN, "non-finite state found by step %lld (FPD_FLAG_NONFINITE)", (long long)s->nstep);
+    return FPD_OK;
+}
+
+int fpd_flags(fpd_sim *s, uint32_t *flags) {
+    if (!s || !flags) return fail(s, FPD_EINVAL, "fpd_flags: NULL argument");
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "stream synchronize");
+    unsigned v = 0;
+    e = cudaMemcpy(&v, s->status, sizeof v, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(s, e, "read status");
+    *flags = v;
     return FPD_OK;
 }
 
@@ -900,8 +931,11 @@ int fpd_load(fpd_sim *s, const char *path) {
     cudaError_t e = cudaMemcpy(s->pool, pool.data(), pool.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(s->tabmem, tabs.data(), tabs.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(s->masks[0], masks.data(), masks.size(), cudaMemcpyHostToDevice);
+    // the status flags describe the replaced run: they start over
+    if (e == cudaSuccess) e = cudaMemset(s->status, 0, sizeof(unsigned));
     if (e != cudaSuccess) return cuda_fail(s, e, "fpd_load");
     s->nstep = h.nstep;
+    s->watch_next = (s->nstep / fpd::kWatchSteps + 1) * fpd::kWatchSteps;
     // an active bead export restarts from the restored step count
     if (s->ex_ring) return fpd_export_beads(s, s->ex_slots);
     return FPD_OK;

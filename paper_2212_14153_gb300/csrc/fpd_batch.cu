@@ -28,7 +28,9 @@
 
 namespace {
 
-enum SlotState { kFree = 0, kActive = 1, kDone = 2 };
+// kFailed: the watchdog or the bead phase found a non-finite value in the
+// instance; it is taken out of the running set at the next poll.
+enum SlotState { kFree = 0, kActive = 1, kDone = 2, kFailed = 3 };
 
 struct Slot {
     int state = kFree;
@@ -100,6 +102,8 @@ struct fpd_batch {
     fpd::BeadTab tab[2]{};
     fpd::Inst *insts_d = nullptr;
     unsigned *counters = nullptr;
+    unsigned *status = nullptr;  // sticky FPD_FLAG_* bits per slot (device)
+    int64_t watch_next = fpd::kWatchSteps;  // global step of the next watchdog pass
     int2 *tiles_d = nullptr;
     int tiles_cap = 0, ntiles = 0;
     unsigned *masks = nullptr;  // kMaskBufs * tiles_cap * mask_words, in rotation by global step
@@ -157,6 +161,7 @@ void free_batch(fpd_batch *b) {
     cudaFree(b->tabmem);
     cudaFree(b->insts_d);
     cudaFree(b->counters);
+    cudaFree(b->status);
     cudaFree(b->tiles_d);
     cudaFree(b->masks);
     cudaFree(b->beads_all_d);
@@ -296,6 +301,7 @@ int fpd_batch_create(int32_t precision, int32_t max_slots, int64_t pool_bytes, i
         (e = cudaMalloc(&b->tabmem, 2 * tab_bytes)) != cudaSuccess ||
         (e = cudaMalloc(&b->insts_d, max_slots * sizeof(fpd::Inst))) != cudaSuccess ||
         (e = cudaMalloc(&b->counters, max_slots * sizeof(unsigned))) != cudaSuccess ||
+        (e = cudaMalloc(&b->status, max_slots * sizeof(unsigned))) != cudaSuccess ||
         (e = cudaMalloc(&b->beads_all_d, nbm * sizeof(int2))) != cudaSuccess ||
         (e = cudaMalloc(&b->beads_old_d, nbm * sizeof(int2))) != cudaSuccess ||
         (e = cudaMalloc(&b->beads_fresh_d, nbm * sizeof(int2))) != cudaSuccess) {
@@ -305,6 +311,7 @@ int fpd_batch_create(int32_t precision, int32_t max_slots, int64_t pool_bytes, i
     }
     cudaMemsetAsync(b->tabmem, 0, 2 * tab_bytes, b->stream);
     cudaMemsetAsync(b->counters, 0, max_slots * sizeof(unsigned), b->stream);
+    cudaMemsetAsync(b->status, 0, max_slots * sizeof(unsigned), b->stream);
     for (int t = 0; t < 2; ++t) {
         double *d = (double *)((char *)b->tabmem + t * tab_bytes);
         float *f = (float *)(d + fpd::kTabDoubles * nbm);
@@ -360,7 +367,9 @@ int fpd_batch_add(fpd_batch *b, const fpd_params *p, int64_t n_steps, int32_t *s
         b->bead_alloc.release(boff, I.nb);
         return bfail(b, FPD_EINVAL, "bead positions must be finite");
     }
-    cudaError_t e = fpd::launch_init(b->precision, nullptr, I, b->pool, p->init_couette, b->stream);
+    // the slot's status flags start clear (a removed instance may have left some)
+    cudaError_t e = cudaMemsetAsync(b->status + s, 0, sizeof(unsigned), b->stream);
+    if (e == cudaSuccess) e = fpd::launch_init(b->precision, nullptr, I, b->pool, p->init_couette, b->stream);
     if (e == cudaSuccess && I.nb > 0) {
         // initial positions into table 0 (V = 0); S, F, G follow at rebuild
         std::vector<double> zeros(I.nb, 0.0);
@@ -408,11 +417,12 @@ int enqueue_bstep(fpd_batch *b, cudaStream_t st, int64_t gstep, bool any_first) 
     // the previous buffer holds the previous bead phase's marks unless the
     // masks were reset before this step
     const fpd::SweepMasks mk{mw, b->masks + (size_t)((gstep + M - 1) % M) * mstride,
-                             b->masks + (size_t)((gstep + 1) % M) * mstride, gstep > b->rebuild_gstep ? 1 : 0};
+                             b->masks + (size_t)((gstep + 1) % M) * mstride, gstep > b->rebuild_gstep ? 1 : 0,
+                             b->status};
     cudaError_t e;
     if (nbl > 0) {
         e = fpd::launch_beads(b->precision, b->insts_d, blist, nbl, b->pool, b->tab[0], b->tab[1], mw, gp, 1,
-                              b->counters, 1, st);
+                              b->counters, 1, st, fpd::BeadExport{}, b->status);
         if (e != cudaSuccess) return bcuda(b, e, "batched bead phase");
     }
     e = fpd::launch_lattice_batch(b->precision, b->insts_d, b->tiles_d, b->ntiles, b->pool, b->tab[0], b->tab[1], mk,
@@ -469,7 +479,17 @@ int fpd_batch_run(fpd_batch *b, int64_t max_steps, int64_t *steps_done) {
     if (nactive == 0 || chunk <= 0) return FPD_OK;
     int rc;
     if (b->dirty && (rc = rebuild(b)) != FPD_OK) return rc;
+    // watchdog pass over every resident instance's populations (between
+    // captured chunks, never inside one)
+    auto watch = [b]() -> int {
+        cudaError_t e = fpd::launch_watch(b->precision, b->insts_d, b->insts_h[0], b->tiles_d, b->ntiles, b->pool,
+                                          (int)(b->gstep & 1), b->status, b->stream);
+        if (e != cudaSuccess) return bcuda(b, e, "watchdog launch");
+        b->watch_next = (b->gstep / fpd::kWatchSteps + 1) * fpd::kWatchSteps;
+        return FPD_OK;
+    };
     for (int64_t t = 0; t < chunk;) {
+        if (b->gstep >= b->watch_next && (rc = watch()) != FPD_OK) return rc;
         // on the first step after admissions the new instances skip the
         // bead advance (their table is the initial one)
         const bool any_first = b->n_old != b->n_all;
@@ -494,6 +514,9 @@ int fpd_batch_run(fpd_batch *b, int64_t max_steps, int64_t *steps_done) {
             b->n_old = b->n_all;
         }
     }
+    // and after the run, so that an instance reaching its count is checked
+    // before it is reported finished
+    if ((rc = watch()) != FPD_OK) return rc;
     b->cell_updates += cells * (double)chunk;
     for (auto &sl : b->slots)
         if (sl.state == kActive) {
@@ -528,10 +551,21 @@ int fpd_batch_poll(fpd_batch *b, int32_t *done_slots, int32_t capacity, int32_t 
     if (!b || !n_done) return FPD_EINVAL;
     int rc = fpd_batch_sync(b);
     if (rc) return rc;
+    // instances with a non-finite value leave the running set as failed
+    std::vector<unsigned> st(b->max_slots);
+    cudaError_t e = cudaMemcpy(st.data(), b->status, st.size() * sizeof(unsigned), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return bcuda(b, e, "read status");
+    for (int s = 0; s < b->max_slots; ++s) {
+        Slot &sl = b->slots[s];
+        if ((sl.state == kActive || (sl.state == kDone && !sl.reported)) && (st[s] & fpd::kFlagNonFinite)) {
+            if (sl.state == kActive) b->dirty = true;
+            sl.state = kFailed;
+        }
+    }
     int n = 0;
     for (int s = 0; s < b->max_slots && n < capacity; ++s) {
         Slot &sl = b->slots[s];
-        if (sl.state == kDone && !sl.reported) {
+        if ((sl.state == kDone || sl.state == kFailed) && !sl.reported) {
             sl.reported = true;
             if (done_slots) done_slots[n] = s;
             ++n;
@@ -550,6 +584,20 @@ int fpd_batch_slot_info(fpd_batch *b, int32_t slot, int64_t out[6]) {
     out[3] = sl.steps_done;
     out[4] = sl.steps_req;
     out[5] = sl.state;
+    return FPD_OK;
+}
+
+static int slot_ok(fpd_batch *b, int32_t slot);
+
+int fpd_batch_slot_flags(fpd_batch *b, int32_t slot, uint32_t *flags) {
+    int rc = slot_ok(b, slot);
+    if (rc) return rc;
+    if (!flags) return bfail(b, FPD_EINVAL, "NULL output");
+    if ((rc = fpd_batch_sync(b))) return rc;
+    unsigned v = 0;
+    cudaError_t e = cudaMemcpy(&v, b->status + slot, sizeof v, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return bcuda(b, e, "read status");
+    *flags = v;
     return FPD_OK;
 }
 

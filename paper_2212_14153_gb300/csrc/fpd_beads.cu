@@ -339,7 +339,8 @@ template <class S, int NT>
 __global__ void __launch_bounds__(NT, BeadMinBlocks<S, NT>::value)
     k_beads(const Inst *__restrict__ insts, const int2 *__restrict__ blist, const int nb_total,
             const S *__restrict__ pool, const BeadTab tab0, const BeadTab tab1, unsigned *__restrict__ mask_write,
-            int gparity, int advance, unsigned *__restrict__ counters, BeadExport ex) {
+            int gparity, int advance, unsigned *__restrict__ counters, BeadExport ex,
+            unsigned *__restrict__ status) {
     constexpr bool kF64 = std::is_same<S, double>::value;
     __shared__ Inst sI;
     // neighbour beads: old-table position (FP64 path), offset R_b - R_q and
@@ -563,6 +564,10 @@ __global__ void __launch_bounds__(NT, BeadMinBlocks<S, NT>::value)
         if (tid == 0) {
             const double inv_S = s_invS;
             const double Vx = ax * inv_S, Vy = ay * inv_S;
+            // the early update of unmarked tiles assumes a bead moves less
+            // than a cell per step; flag the instance when it does not
+            if (status && !(fabs(Vx) < kFastBead && fabs(Vy) < kFastBead))
+                atomicOr(status + ii, (isfinite(Vx) && isfinite(Vy)) ? kFlagFastBead : (kFlagFastBead | kFlagNonFinite));
             const double Rnx = Rx + Vx, Rny = Ry + Vy;
             tnew.Rx[b] = Rnx;
             tnew.Ry[b] = Rny;
@@ -781,20 +786,20 @@ int sm_count() {
 template <class S>
 cudaError_t launch_beads_t(cudaLaunchConfig_t &cfg, bool few, const Inst *inst_d, const int2 *blist, int nb_total,
                            const void *pool, BeadTab tab0, BeadTab tab1, unsigned *mask_write, int gparity,
-                           int advance, unsigned *counters, BeadExport ex) {
+                           int advance, unsigned *counters, BeadExport ex, unsigned *status) {
     cfg.blockDim = dim3(few ? kBeadThreadsFew : kBeadThreads);
     if (few)
         return cudaLaunchKernelEx(&cfg, k_beads<S, kBeadThreadsFew>, inst_d, blist, nb_total, (const S *)pool, tab0,
-                                  tab1, mask_write, gparity, advance, counters, ex);
+                                  tab1, mask_write, gparity, advance, counters, ex, status);
     return cudaLaunchKernelEx(&cfg, k_beads<S, kBeadThreads>, inst_d, blist, nb_total, (const S *)pool, tab0, tab1,
-                              mask_write, gparity, advance, counters, ex);
+                              mask_write, gparity, advance, counters, ex, status);
 }
 
 }  // namespace
 
 cudaError_t launch_beads(int precision, const Inst *inst_d, const int2 *blist, int nb_total, const void *pool,
                          BeadTab tab0, BeadTab tab1, unsigned *mask_write, int gparity, int advance,
-                         unsigned *counters, int pdl, cudaStream_t st, BeadExport ex) {
+                         unsigned *counters, int pdl, cudaStream_t st, BeadExport ex, unsigned *status) {
     if (nb_total <= 0) return cudaSuccess;
     // one CTA per bead: a grid capped at the resident CTAs (persistent) keeps
     // the bead CTAs on the SMs at once and leaves the sweep that follows
@@ -813,13 +818,13 @@ cudaError_t launch_beads(int precision, const Inst *inst_d, const int2 *blist, i
     switch (precision) {
         case 0:
             return launch_beads_t<double>(cfg, few, inst_d, blist, nb_total, pool, tab0, tab1, mask_write, gparity,
-                                          advance, counters, ex);
+                                          advance, counters, ex, status);
         case 1:
             return launch_beads_t<float>(cfg, few, inst_d, blist, nb_total, pool, tab0, tab1, mask_write, gparity,
-                                         advance, counters, ex);
+                                         advance, counters, ex, status);
         case 2:
             return launch_beads_t<__half>(cfg, few, inst_d, blist, nb_total, pool, tab0, tab1, mask_write, gparity,
-                                          advance, counters, ex);
+                                          advance, counters, ex, status);
     }
     return cudaErrorInvalidValue;
 }

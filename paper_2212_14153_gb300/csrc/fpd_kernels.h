@@ -34,7 +34,24 @@ struct SweepMasks {
     const unsigned *prev;  // the previous bead phase's marks
     unsigned *clear;       // zeroed for the next bead phase
     int early_cold;
+    // per-instance status words (index 0 for a single instance, the slot in
+    // a batch): an instance with kFlagFastBead set takes the waiting path
+    const unsigned *status;
 };
+
+// Sticky per-instance status bits, set on the device (values of the
+// FPD_FLAG_* constants of fpd.h).  kFlagFastBead: a bead phase found a bead
+// velocity component of magnitude >= kFastBead cells per step (or a
+// non-finite one); from then on the instance's sweeps no longer update
+// unmarked tiles early, because that path assumes a bead moves less than a
+// cell per step.  kFlagNonFinite: a non-finite bead velocity, or a
+// non-finite population found by the watchdog.
+constexpr unsigned kFlagFastBead = 1u;
+constexpr unsigned kFlagNonFinite = 2u;
+constexpr double kFastBead = 0.5;
+// Steps between two watchdog passes over the populations (a multiple of
+// kGraphSteps, so that the passes fall between captured chunks).
+constexpr int kWatchSteps = 1024;
 
 // One fused collide-stream-bounce-back sweep of a single instance (Sec. 2.3
 // item (2) with the item-(1) overlay of Eqs. 1, 2, 4 evaluated in hot tiles),
@@ -74,9 +91,21 @@ struct BeadExport {
     int slots = 0;
     int stride = 0;
 };
+// status: per-instance status words (indexed by instance slot), where a
+// bead velocity component of magnitude >= kFastBead or a non-finite one sets
+// kFlagFastBead (and kFlagNonFinite); NULL: not checked.
 cudaError_t launch_beads(int precision, const Inst *inst_d, const int2 *blist, int nb_total,
                          const void *pool, BeadTab tab0, BeadTab tab1, unsigned *mask_write, int gparity,
-                         int advance, unsigned *counters, int pdl, cudaStream_t st, BeadExport ex = BeadExport{});
+                         int advance, unsigned *counters, int pdl, cudaStream_t st, BeadExport ex = BeadExport{},
+                         unsigned *status = nullptr);
+
+// Watchdog: sets kFlagNonFinite in status[slot] of every instance holding a
+// non-finite population at its current step.  Batch form: tiles[t] =
+// (slot, by << 16 | bx) over insts (device records, each at its parity
+// gparity ^ par_xor); single form (tiles == NULL): every tile of inst_h at
+// parity gparity, status[0].
+cudaError_t launch_watch(int precision, const Inst *insts, const Inst &inst_h, const int2 *tiles, int ntiles,
+                         const void *pool, int gparity, unsigned *status, cudaStream_t st);
 
 // Batched sweep over a packed tile list of many instances (tiles[t] =
 // (slot, by << 16 | bx)); each instance at its own parity.  Under variant 2

@@ -111,12 +111,17 @@ __device__ __forceinline__ void cell_overlay(const Inst &I, const BeadTab &tab, 
 // support widened by a cell.  A bead moves less than a cell per step (its
 // velocity is a weighted mean of fluid velocities, which stay far below the
 // lattice's one cell per step), so no support reaches such a tile in this
-// step either, and the bead phase reads no population of it.  The lead CTA
-// always waits: the next launch in the stream then cannot start before the
-// bead phase has completed.
+// step either, and the bead phase reads no population of it.  The bead
+// phase checks that assumption (|V| < kFastBead per component, with the
+// marks covering moves of more than a cell): once it has failed for an
+// instance, its status word carries kFlagFastBead and every tile of it
+// waits.  That word was written by an earlier bead phase, which completed
+// before the previous sweep did.  The lead CTA always waits: the next launch
+// in the stream then cannot start before the bead phase has completed.
 __device__ __forceinline__ bool tile_cold_early(const unsigned *__restrict__ prev, const int W, const int early_cold,
-                                                const bool lead) {
+                                                const bool lead, const unsigned *__restrict__ status) {
     if (!early_cold || lead) return false;
+    if (__ldcg(status) & kFlagFastBead) return false;
     unsigned any = 0u;
     for (int w = 0; w < W; ++w) any |= prev[w];
     return any == 0u;
@@ -134,8 +139,9 @@ template <class S, int CY, bool kInner, bool kAlongX = false>
 __device__ __forceinline__ void lattice_tile(const Inst &I, S *__restrict__ pool, const BeadTab &tab,
                                              const unsigned *__restrict__ mask_read,
                                              const unsigned *__restrict__ mask_prev, unsigned *__restrict__ mask_clear,
-                                             const int bx, const int by, const int parity, const int early_load,
-                                             const int early_cold, const bool lead, const int tx, const int ty) {
+                                             const unsigned *__restrict__ status, const int bx, const int by,
+                                             const int parity, const int early_load, const int early_cold,
+                                             const bool lead, const int tx, const int ty) {
     using R = typename Real<S>::type;
     constexpr int RY = kAlongX ? 0 : kTileY / CY;
     constexpr int RX = kAlongX ? kTileX / CY : 0;
@@ -170,7 +176,7 @@ __device__ __forceinline__ void lattice_tile(const Inst &I, S *__restrict__ pool
     // populations come from the previous sweep; when the bead phase runs
     // between the two sweeps they may be loaded before waiting on it
     if (early_load) pull();
-    const bool cold = tile_cold_early(mask_prev + tile * W, W, early_cold, lead);
+    const bool cold = tile_cold_early(mask_prev + tile * W, W, early_cold, lead, status);
     if (!cold) pdl_wait();
     pdl_trigger();
     if (tx == 0 && ty == 0)  // a mask of two steps back, for the next bead phase
@@ -204,9 +210,9 @@ __device__ __forceinline__ int tile_order(int b, int n, int parity) { return (pa
 template <class S, int CY, bool kAlongX = false>
 __global__ void __launch_bounds__(kTileX *kTileY / CY)
     k_lattice(const Inst I, S *__restrict__ pool, const BeadTab tab, const unsigned *__restrict__ mask_read,
-              const unsigned *__restrict__ mask_prev, unsigned *__restrict__ mask_clear, const int parity,
-              const int early_load, const int early_cold) {
-    lattice_tile<S, CY, true, kAlongX>(I, pool, tab, mask_read, mask_prev, mask_clear,
+              const unsigned *__restrict__ mask_prev, unsigned *__restrict__ mask_clear,
+              const unsigned *__restrict__ status, const int parity, const int early_load, const int early_cold) {
+    lattice_tile<S, CY, true, kAlongX>(I, pool, tab, mask_read, mask_prev, mask_clear, status,
                                        tile_order(blockIdx.x, gridDim.x, parity),
                                        tile_order(blockIdx.y, gridDim.y, parity), parity, early_load, early_cold,
                                        (blockIdx.x | blockIdx.y) == 0, threadIdx.x, threadIdx.y);
@@ -231,8 +237,9 @@ template <class S, int CY, bool kAlongX = false>
 __global__ void __launch_bounds__(kTileX *kTileY / CY, BatchMinBlocks<S, CY>::value)
     k_lattice_batch(const Inst *__restrict__ insts, const int2 *__restrict__ tiles, S *__restrict__ pool,
                     const BeadTab tab0, const BeadTab tab1, const unsigned *__restrict__ mask_read,
-                    const unsigned *__restrict__ mask_prev, unsigned *__restrict__ mask_clear, const int gparity,
-                    const int early_load, const int early_cold) {
+                    const unsigned *__restrict__ mask_prev, unsigned *__restrict__ mask_clear,
+                    const unsigned *__restrict__ status, const int gparity, const int early_load,
+                    const int early_cold) {
     __shared__ Inst sI;
     const int2 t = tiles[blockIdx.x];
     {
@@ -243,9 +250,9 @@ __global__ void __launch_bounds__(kTileX *kTileY / CY, BatchMinBlocks<S, CY>::va
     }
     __syncthreads();
     const int parity = gparity ^ sI.par_xor;
-    lattice_tile<S, CY, BatchInner<S, CY, kAlongX>::value, kAlongX>(sI, pool, parity ? tab1 : tab0, mask_read, mask_prev, mask_clear,
-                                                  t.y & 0xffff, t.y >> 16, parity, early_load, early_cold,
-                                                  blockIdx.x == 0, threadIdx.x, threadIdx.y);
+    lattice_tile<S, CY, BatchInner<S, CY, kAlongX>::value, kAlongX>(
+        sI, pool, parity ? tab1 : tab0, mask_read, mask_prev, mask_clear, status + t.x, t.y & 0xffff, t.y >> 16,
+        parity, early_load, early_cold, blockIdx.x == 0, threadIdx.x, threadIdx.y);
 }
 
 // ------------------------------------------------ vectorised sweep (variant 2)
@@ -410,7 +417,8 @@ template <class S>
 __device__ __forceinline__ void lattice_tile_vec(const Inst &I, S *__restrict__ pool, const BeadTab &tab,
                                                  const unsigned *__restrict__ mask_read,
                                                  const unsigned *__restrict__ mask_prev,
-                                                 unsigned *__restrict__ mask_clear, const int bx, const int by,
+                                                 unsigned *__restrict__ mask_clear,
+                                                 const unsigned *__restrict__ status, const int bx, const int by,
                                                  const int parity, const int early_load, const int early_cold,
                                                  const bool lead) {
     using R = typename Real<S>::type;
@@ -424,7 +432,7 @@ __device__ __forceinline__ void lattice_tile_vec(const Inst &I, S *__restrict__ 
     const VCell C = make_vcell<NV>(I, x0, y, threadIdx.x);
     R g[NV][9];
     if (early_load) vload_pops<S, NV>(Asrc, I, C, g);
-    const bool cold = tile_cold_early(mask_prev + tile * W, W, early_cold, lead);
+    const bool cold = tile_cold_early(mask_prev + tile * W, W, early_cold, lead, status);
     if (!cold) pdl_wait();
     pdl_trigger();
     if (threadIdx.x == 0 && threadIdx.y == 0)
@@ -448,9 +456,11 @@ __device__ __forceinline__ void lattice_tile_vec(const Inst &I, S *__restrict__ 
 template <class S>
 __global__ void __launch_bounds__(kTileX / VecWidth<S>::value * kTileY)
     k_lattice_vec(const Inst I, S *__restrict__ pool, const BeadTab tab, const unsigned *__restrict__ mask_read,
-                  const unsigned *__restrict__ mask_prev, unsigned *__restrict__ mask_clear, const int parity,
-                  const int early_load, const int early_cold) {
-    lattice_tile_vec<S>(I, pool, tab, mask_read, mask_prev, mask_clear, tile_order(blockIdx.x, gridDim.x, parity),
+                  const unsigned *__restrict__ mask_prev, unsigned *__restrict__ mask_clear,
+                  const unsigned *__restrict__ status, const int parity, const int early_load,
+                  const int early_cold) {
+    lattice_tile_vec<S>(I, pool, tab, mask_read, mask_prev, mask_clear, status,
+                        tile_order(blockIdx.x, gridDim.x, parity),
                         tile_order(blockIdx.y, gridDim.y, parity), parity, early_load, early_cold,
                         (blockIdx.x | blockIdx.y) == 0);
 }
@@ -463,8 +473,9 @@ template <class S>
 __global__ void __launch_bounds__(kTileX / VecWidth<S>::value * kTileY, BatchVecMinBlocks<S>::value)
     k_lattice_batch_vec(const Inst *__restrict__ insts, const int2 *__restrict__ tiles, S *__restrict__ pool,
                         const BeadTab tab0, const BeadTab tab1, const unsigned *__restrict__ mask_read,
-                        const unsigned *__restrict__ mask_prev, unsigned *__restrict__ mask_clear, const int gparity,
-                        const int early_load, const int early_cold) {
+                        const unsigned *__restrict__ mask_prev, unsigned *__restrict__ mask_clear,
+                        const unsigned *__restrict__ status, const int gparity, const int early_load,
+                        const int early_cold) {
     constexpr int NT = kTileX / VecWidth<S>::value * kTileY;
     __shared__ Inst sI;
     const int2 t = tiles[blockIdx.x];
@@ -480,13 +491,13 @@ __global__ void __launch_bounds__(kTileX / VecWidth<S>::value * kTileY, BatchVec
     // on the same threads: NV cells per thread along y
     constexpr int NV = VecWidth<S>::value;
     if (sI.nx % NV == 0) {
-        lattice_tile_vec<S>(sI, pool, parity ? tab1 : tab0, mask_read, mask_prev, mask_clear, t.y & 0xffff,
-                            t.y >> 16, parity, early_load, early_cold, blockIdx.x == 0);
+        lattice_tile_vec<S>(sI, pool, parity ? tab1 : tab0, mask_read, mask_prev, mask_clear, status + t.x,
+                            t.y & 0xffff, t.y >> 16, parity, early_load, early_cold, blockIdx.x == 0);
     } else {
         const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-        lattice_tile<S, NV, false>(sI, pool, parity ? tab1 : tab0, mask_read, mask_prev, mask_clear, t.y & 0xffff,
-                                   t.y >> 16, parity, early_load, early_cold, blockIdx.x == 0, tid % kTileX,
-                                   tid / kTileX);
+        lattice_tile<S, NV, false>(sI, pool, parity ? tab1 : tab0, mask_read, mask_prev, mask_clear, status + t.x,
+                                   t.y & 0xffff, t.y >> 16, parity, early_load, early_cold, blockIdx.x == 0,
+                                   tid % kTileX, tid / kTileX);
     }
 }
 
@@ -673,6 +684,37 @@ __global__ void __launch_bounds__(kDiagThreads)
     }
 }
 
+// Watchdog: one tile per CTA (32 x 8 cells, a thread a cell) reads every
+// stored population of its cells in the instance's current buffer (each
+// plane at the cell's own element: the whole buffer but its row padding)
+// and sets kFlagNonFinite in the instance's status word if any is NaN or
+// infinite.  A non-finite population spreads to all nine outputs of the
+// next collision at its cell, so a pass every few hundred steps sees any
+// instance that has diverged.
+template <class S>
+__global__ void __launch_bounds__(kTileX *kTileY)
+    k_watch(const Inst *__restrict__ insts, const __grid_constant__ Inst I1, const int2 *__restrict__ tiles,
+            const S *__restrict__ pool, const int gparity, unsigned *__restrict__ status) {
+    int slot = 0, bx = blockIdx.x, by = blockIdx.y;
+    const Inst *Ip = &I1;
+    if (tiles) {
+        const int2 t = tiles[blockIdx.x];
+        slot = t.x;
+        bx = t.y & 0xffff;
+        by = t.y >> 16;
+        Ip = insts + slot;
+    }
+    const Inst &I = *Ip;
+    const int x = bx * kTileX + threadIdx.x, y = by * kTileY + threadIdx.y;
+    bool bad = false;
+    if (x < I.nx && y < I.ny) {
+        const S *A = pop_buffer(pool, I, gparity ^ I.par_xor) + (y * I.pitch + x);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) bad |= !isfinite(Store<S>::ld(A + k * I.plane32, 1.0f));
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0 && threadIdx.y == 0) atomicOr(status + slot, kFlagNonFinite);
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------- launchers
@@ -698,17 +740,17 @@ static cudaError_t lattice_v(int variant, const Inst &I, void *pool, BeadTab tab
     if (variant == 2 && I.nx % VecWidth<S>::value == 0) {
         const cudaLaunchConfig_t cfg = sweep_config(grid, dim3(kTileX / VecWidth<S>::value, kTileY), after_beads,
                                                     st, attr);
-        return cudaLaunchKernelEx(&cfg, k_lattice_vec<S>, I, (S *)pool, tab, mk.read, mk.prev, mk.clear, parity,
-                                  after_beads, ec);
+        return cudaLaunchKernelEx(&cfg, k_lattice_vec<S>, I, (S *)pool, tab, mk.read, mk.prev, mk.clear, mk.status,
+                                  parity, after_beads, ec);
     }
     if (variant == 1) {
         const cudaLaunchConfig_t cfg = sweep_config(grid, dim3(kTileX / 2, kTileY), after_beads, st, attr);
         return cudaLaunchKernelEx(&cfg, k_lattice<S, 2, true>, I, (S *)pool, tab, mk.read, mk.prev, mk.clear,
-                                  parity, after_beads, ec);
+                                  mk.status, parity, after_beads, ec);
     }
     const cudaLaunchConfig_t cfg = sweep_config(grid, dim3(kTileX, kTileY), after_beads, st, attr);
-    return cudaLaunchKernelEx(&cfg, k_lattice<S, 1>, I, (S *)pool, tab, mk.read, mk.prev, mk.clear, parity,
-                              after_beads, ec);
+    return cudaLaunchKernelEx(&cfg, k_lattice<S, 1>, I, (S *)pool, tab, mk.read, mk.prev, mk.clear, mk.status,
+                              parity, after_beads, ec);
 }
 
 cudaError_t launch_lattice(int precision, const Inst *, const Inst &inst_h, void *pool, BeadTab tab,
@@ -732,16 +774,16 @@ static cudaError_t lattice_batch_v(int variant, const Inst *insts, const int2 *t
         const cudaLaunchConfig_t cfg = sweep_config(grid, dim3(kTileX / VecWidth<S>::value, kTileY), after_beads,
                                                     st, attr);
         return cudaLaunchKernelEx(&cfg, k_lattice_batch_vec<S>, insts, tiles, (S *)pool, tab0, tab1, mk.read,
-                                  mk.prev, mk.clear, gparity, after_beads, ec);
+                                  mk.prev, mk.clear, mk.status, gparity, after_beads, ec);
     }
     if (variant == 1) {
         const cudaLaunchConfig_t cfg = sweep_config(grid, dim3(kTileX / 2, kTileY), after_beads, st, attr);
         return cudaLaunchKernelEx(&cfg, k_lattice_batch<S, 2, true>, insts, tiles, (S *)pool, tab0, tab1,
-                                  mk.read, mk.prev, mk.clear, gparity, after_beads, ec);
+                                  mk.read, mk.prev, mk.clear, mk.status, gparity, after_beads, ec);
     }
     const cudaLaunchConfig_t cfg = sweep_config(grid, dim3(kTileX, kTileY), after_beads, st, attr);
     return cudaLaunchKernelEx(&cfg, k_lattice_batch<S, 1>, insts, tiles, (S *)pool, tab0, tab1, mk.read, mk.prev,
-                              mk.clear, gparity, after_beads, ec);
+                              mk.clear, mk.status, gparity, after_beads, ec);
 }
 
 cudaError_t launch_lattice_batch(int precision, const Inst *insts, const int2 *tiles, int ntiles, void *pool,
@@ -794,6 +836,15 @@ cudaError_t launch_read_pops(int precision, const Inst *, const Inst &I, const v
 cudaError_t launch_write_pops(int precision, const Inst *, const Inst &I, void *pool, int parity, const double *f,
                               cudaStream_t st) {
     FPD_DISPATCH(precision, (k_write_pops<S><<<row_grid(I, 128), 128, 0, st>>>(I, (S *)pool, parity, f)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_watch(int precision, const Inst *insts, const Inst &I, const int2 *tiles, int ntiles,
+                         const void *pool, int gparity, unsigned *status, cudaStream_t st) {
+    const dim3 grid = tiles ? dim3(ntiles) : dim3(I.ntx, I.nty);
+    if (tiles && ntiles <= 0) return cudaSuccess;
+    FPD_DISPATCH(precision, (k_watch<S><<<grid, dim3(kTileX, kTileY), 0, st>>>(insts, I, tiles, (const S *)pool,
+                                                                               gparity, status)));
     return cudaGetLastError();
 }
 

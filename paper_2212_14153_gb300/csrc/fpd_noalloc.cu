@@ -21,6 +21,13 @@
 // array: calls whose device work overlaps (other streams, other handles on
 // the same device, other host threads) race on it and must be serialised by
 // the caller.
+//
+// The array's device address is looked up with cudaGetSymbolAddress once per
+// device and CUDA context, and cached with the context's ID: an application
+// that calls cudaDeviceReset gets a new primary context in which the library
+// module, and with it the array, is loaded afresh at another address, so a
+// cached address from the old context is never used in the new one.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -37,7 +44,32 @@ constexpr int kMaxDevices = 64;
 static __device__ __align__(256) double g_diag_scratch[4 * kNoAllocBlocks + 4];
 
 std::mutex g_setup_mu;
-double *g_scratch_addr[kMaxDevices] = {};  // device address of g_diag_scratch per device
+double *g_scratch_addr[kMaxDevices] = {};        // device address of g_diag_scratch per device
+unsigned long long g_scratch_ctx[kMaxDevices] = {};  // ID of the context that address belongs to
+
+// ID of the calling thread's current context (driver entry points resolved
+// through the runtime, so that no link to the driver library is needed).
+using CtxGetCurrentFn = CUresult (*)(CUcontext *);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long *);
+cudaError_t current_context_id(unsigned long long *id) {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    if (!get_current || !get_id) {
+        void *a = nullptr, *b = nullptr;
+        cudaDriverEntryPointQueryResult qa, qb;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &qa);
+        if (e == cudaSuccess) e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb);
+        if (e != cudaSuccess) return e;
+        if (qa != cudaDriverEntryPointSuccess || qb != cudaDriverEntryPointSuccess || !a || !b)
+            return cudaErrorNotSupported;
+        get_current = (CtxGetCurrentFn)a;
+        get_id = (CtxGetIdFn)b;
+    }
+    CUcontext ctx = nullptr;
+    if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return cudaErrorContextIsDestroyed;
+    if (get_id(ctx, id) != CUDA_SUCCESS) return cudaErrorContextIsDestroyed;
+    return cudaSuccess;
+}
 
 // Sum the per-block partials in block order (the order fpd_diag sums them
 // on the host) into the 4 slots after the partials.
@@ -91,14 +123,24 @@ extern "C" int fpd_diag_noalloc(fpd_sim *s, double out[4]) {
     double total[4] = {0.0, 0.0, 0.0, 0.0};
     double *scratch = nullptr;
     {
-        // set-up, once per device, with that device current: the host-side
-        // name g_diag_scratch is not a device address; ask the runtime for it
+        // set-up, once per device and context, with that device current: the
+        // host-side name g_diag_scratch is not a device address; ask the
+        // runtime for it
         std::lock_guard<std::mutex> lock(g_setup_mu);
-        if (!g_scratch_addr[dev]) {
+        unsigned long long ctx_id = 0;
+        e = current_context_id(&ctx_id);
+        if (e != cudaSuccess) {
+            rc = set_err(s, FPD_ECUDA, "fpd_diag_noalloc: current context", e);
+        } else if (!g_scratch_addr[dev] || g_scratch_ctx[dev] != ctx_id) {
             void *p = nullptr;
             e = cudaGetSymbolAddress(&p, g_diag_scratch);
-            if (e != cudaSuccess) rc = set_err(s, FPD_ECUDA, "fpd_diag_noalloc: cudaGetSymbolAddress", e);
-            else g_scratch_addr[dev] = (double *)p;
+            if (e != cudaSuccess) {
+                g_scratch_addr[dev] = nullptr;
+                rc = set_err(s, FPD_ECUDA, "fpd_diag_noalloc: cudaGetSymbolAddress", e);
+            } else {
+                g_scratch_addr[dev] = (double *)p;
+                g_scratch_ctx[dev] = ctx_id;
+            }
         }
         scratch = g_scratch_addr[dev];
     }

@@ -22,6 +22,7 @@ struct fpd_sim {
     double *tabmem = nullptr;       // two bead tables
     fpd::BeadTab tab[2]{};
     unsigned *counters = nullptr;   // one per instance (bead-phase last-block)
+    unsigned *status = nullptr;     // sticky FPD_FLAG_* bits of the instance (device word)
     unsigned *masks[fpd::kMaskBufs] = {};  // per-tile bead masks, in rotation by step (t % kMaskBufs)
     double *scratch = nullptr;      // fields / populations / diagnostics
     size_t scratch_bytes = 0;
@@ -53,6 +54,7 @@ struct fpd_sim {
     unsigned long long *ex_count = nullptr;
     int64_t ex_first = 0;
     bool early_cold = true;  // unmarked tiles update before the bead phase ends (same results)
+    int64_t watch_next = fpd::kWatchSteps;  // step count at which the next watchdog pass runs
     int variant = 0;  // lattice sweep variant (see launch_lattice)
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t graph[fpd::kMaskBufs] = {};  // captured step chunks, by first step % kMaskBufs

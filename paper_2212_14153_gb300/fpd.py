@@ -19,6 +19,8 @@ LIB_PATH = os.path.join(HERE, "libfpd.so")
 FPD_OK, FPD_EINVAL, FPD_ENOMEM, FPD_ECUDA, FPD_ETIMEOUT, FPD_ENAN, FPD_EBUSY = 0, -1, -2, -3, -4, -5, -6
 FPD_F64, FPD_F32, FPD_F32_F16STORE = 0, 1, 2
 FPD_MRT_MAGIC, FPD_MRT_LL, FPD_BGK = 0, 1, 2
+FPD_FLAG_FAST_BEAD, FPD_FLAG_NONFINITE = 1, 2
+SLOT_FREE, SLOT_RUNNING, SLOT_FINISHED, SLOT_FAILED = 0, 1, 2, 3
 
 _DP = ctypes.POINTER(ctypes.c_double)
 
@@ -61,6 +63,8 @@ SIGNATURES = {
     "fpd_create": (ctypes.c_int, [ctypes.POINTER(fpd_params), ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
     "fpd_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
     "fpd_sync": (ctypes.c_int, [ctypes.c_void_p]),
+    "fpd_flags": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint32)]),
+    "fpd_batch_slot_flags": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_uint32)]),
     "fpd_read_fields": (ctypes.c_int, [ctypes.c_void_p, _DP, _DP, _DP]),
     "fpd_internal_flow": (ctypes.c_int, [ctypes.c_void_p, _DP]),
     "fpd_workspace_bytes": (ctypes.c_int, [ctypes.POINTER(fpd_params), ctypes.POINTER(ctypes.c_uint64)]),
@@ -174,6 +178,18 @@ def fpd_step(h, n_steps: int) -> None:
 
 def fpd_sync(h) -> None:
     _check(load_library().fpd_sync(h), h)
+
+
+def fpd_flags(h) -> int:
+    v = ctypes.c_uint32()
+    _check(load_library().fpd_flags(h, ctypes.byref(v)), h)
+    return int(v.value)
+
+
+def fpd_batch_slot_flags(b, slot: int) -> int:
+    v = ctypes.c_uint32()
+    _bcheck(load_library().fpd_batch_slot_flags(b, slot, ctypes.byref(v)), b)
+    return int(v.value)
 
 
 def fpd_read_fields(h, ux, uy, rho) -> None:
@@ -362,6 +378,10 @@ class Simulation:
 
     def sync(self):
         fpd_sync(self.h)
+
+    def flags(self) -> int:
+        """Sticky FPD_FLAG_* bits of the instance (synchronises)."""
+        return fpd_flags(self.h)
 
     def fields(self):
         ux = np.zeros((self.ny, self.nx)); uy = np.zeros_like(ux); rho = np.zeros_like(ux)
@@ -571,6 +591,10 @@ class Batch:
 
     def info(self, slot: int) -> dict:
         return fpd_batch_slot_info(self.h, slot)
+
+    def flags(self, slot: int) -> int:
+        """Sticky FPD_FLAG_* bits of a slot (synchronises)."""
+        return fpd_batch_slot_flags(self.h, slot)
 
     def fields(self, slot: int):
         i = self.info(slot)

@@ -7,7 +7,14 @@ all admitted instances resident on the device, advances them together in
 chunks of time steps, and retires each as soon as it has run its steps
 (its bead positions and fields are read back to the host).  Requests that
 arrive while others are running join at the next chunk boundary; their work
-overlaps on the device with everything already resident.
+overlaps on the device with everything already resident, so a request's
+time-to-result includes up to one chunk of waiting for admission.
+
+Failures are per request: a request that cannot be admitted even with
+nothing resident (its state exceeds the memory cap or the pool, or its
+parameters are invalid) is rejected at once, and an instance the batch's
+watchdog finds with a non-finite state is retired with an error; the other
+requests run on unchanged.
 
 All arithmetic runs in the CUDA library; this module only schedules.
 """
@@ -31,6 +38,7 @@ class Request:
     done_s: float = -1.0
     slot: int = -1
     result: dict = field(default_factory=dict)
+    error: str = ""
 
 
 def state_bytes(cfg: dict, precision: int) -> int:
@@ -61,6 +69,8 @@ class Server:
         self.batch.close()
 
     def _try_admit(self, req: Request, now: float) -> bool:
+        """Admit req if a slot and memory are free; False if it has to wait.
+        Raises FpdError for a request the batch refuses outright."""
         need = state_bytes(req.cfg, self.precision)
         if self.resident_bytes + need > self.cap_bytes:
             return False
@@ -75,12 +85,22 @@ class Server:
         self.resident_bytes += need
         return True
 
+    @staticmethod
+    def _fail(req: Request, now: float, why: str):
+        req.error = why
+        req.result = {"error": why}
+        req.done_s = now
+
     def _retire(self, req: Request, now: float):
-        R, V, F, S = self.batch.beads(req.slot)
-        req.result = {"R": R, "V": V, "F": F}
-        if self.keep_fields:
-            req.result["fields"] = self.batch.fields(req.slot)
-            req.result["populations"] = self.batch.populations(req.slot)
+        failed = self.batch.info(req.slot)["state"] == fpd.SLOT_FAILED
+        if failed:
+            self._fail(req, now, "non-finite state found by the watchdog")
+        else:
+            R, V, F, S = self.batch.beads(req.slot)
+            req.result = {"R": R, "V": V, "F": F}
+            if self.keep_fields:
+                req.result["fields"] = self.batch.fields(req.slot)
+                req.result["populations"] = self.batch.populations(req.slot)
         self.batch.remove(req.slot)
         self.resident_bytes -= state_bytes(req.cfg, self.precision)
         req.done_s = now
@@ -100,7 +120,19 @@ class Server:
                 queue.append(pending[i])
                 i += 1
             while queue and len(running) < self.max_slots:
-                if not self._try_admit(queue[0], now):
+                try:
+                    admitted = self._try_admit(queue[0], now)
+                except fpd.FpdError as e:
+                    self._fail(queue.pop(0), now, f"rejected: {e}")
+                    continue
+                if not admitted:
+                    if not running:
+                        # nothing resident: no slot or memory will ever free
+                        # up for it, so it cannot run at all
+                        r = queue.pop(0)
+                        self._fail(r, now, "rejected: does not fit in the empty batch "
+                                   f"({state_bytes(r.cfg, self.precision)} state bytes, cap {self.cap_bytes})")
+                        continue
                     break
                 r = queue.pop(0)
                 running[r.slot] = r
@@ -115,9 +147,12 @@ class Server:
                 r = running.pop(slot)
                 self._retire(r, clock() - t0)
         wall = clock() - t0
-        lat = np.array([r.done_s - r.arrival_s for r in requests])
+        ok = [r for r in requests if not r.error]
+        lat = np.array([r.done_s - r.arrival_s for r in ok]) if ok else np.array([np.nan])
         return {
             "requests": len(requests),
+            "completed": len(ok),
+            "failed": len(requests) - len(ok),
             "wall_s": wall,
             "p50_s": float(np.percentile(lat, 50)),
             "p99_s": float(np.percentile(lat, 99)),

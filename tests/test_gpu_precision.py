@@ -66,6 +66,47 @@ def test_two_fiber_lattice_against_oracle(fpd):
         assert e["u"] < bounds[p][0] and e["R"] < bounds[p][1]
 
 
+@pytest.fixture(scope="module")
+def two_fiber_oracle_64():
+    # the oracle's 4096 x 1024 two-fiber run, 64 steps: shared by the
+    # full-size parity tests of every precision and launch shape
+    base = wl.two_fiber_large()
+    o = oracle.Sim(dict(base, threads=THREADS))
+    o.step(64)
+    oux, ouy, _ = o.fields()
+    return base, np.stack([oux, ouy]), o.beads()[0].copy()
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_timed_launch_shapes_against_oracle_at_full_size(fpd, precision, two_fiber_oracle_64, monkeypatch):
+    # the configuration the benchmark times: 4096 x 1024, two fibers, sweep
+    # variant 1 (two cells per thread 16 apart along x, precomputed pull
+    # offsets, tile order reversed every other step, early update of
+    # unmarked tiles, approximate 1/rho in FP32) and whatever variant the
+    # autotuner picks; 64 steps run as 1 direct step + a 32-step captured
+    # chunk + 31 direct steps, or all direct (no graphs)
+    base, ref_u, ref_R = two_fiber_oracle_64
+    bounds = {0: (1e-12, 1e-13), 1: (1e-5, 1e-9), 2: (5e-3, 1e-5)}[precision]
+    cfg = dict(base, precision=precision)
+    runs = []
+    for label, tuning, graphs in (("v1 graphs", 1, True), ("v1 direct", 1, False), ("auto", "auto", True)):
+        if not graphs:
+            monkeypatch.setenv("FPD_NO_GRAPHS", "1")
+        s = fpd.Simulation(cfg, tuning=tuning)
+        monkeypatch.delenv("FPD_NO_GRAPHS", raising=False)
+        s.step(1)
+        s.step(32)
+        s.step(31)
+        assert s.tuning()[0] in (0, 1, 2)
+        e = errors(s, ref_u, ref_R)
+        runs.append(s.populations())
+        s.close()
+        print(f"two-fiber 4096x1024, 64 steps, {NAMES[precision]} {label} vs oracle: {e}")
+        assert e["u"] < bounds[0] and e["R"] < bounds[1], (label, e)
+    # graphs or direct launches: the same numbers
+    assert np.array_equal(runs[0], runs[1])
+
+
 def test_two_fiber_lattice_long_against_fp64_gpu(fpd):
     base = wl.two_fiber_large()
     steps = 2000

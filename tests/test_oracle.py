@@ -489,3 +489,112 @@ def test_internal_flow_vanishes_for_uniform_translation_and_falls_with_viscosity
         d.step(6000)
         ev.append(d.internal_flow()[0] / d.beads()[1][0, 0] ** 2)
     assert ev[0] > 3 * ev[1] > 9 * ev[2] > 0
+
+
+# ------------------------------------------------------------ totals (momentum)
+def test_total_momentum_grows_by_body_force_each_step_in_periodic_box():
+    # Guo forcing adds exactly F to the post-collision momentum of each cell
+    # and streaming in a periodic box only moves it: sum_x f c = t g N_cells
+    # after t steps from rest, mass N_cells throughout.  A half force counted
+    # in the totals, a sign or an x/y mix-up would all break this.
+    nx, ny, gx, gy = 24, 18, 3e-6, -1.7e-6
+    s = oracle.Sim(dict(wl.couette_only(nx, ny, u=0.0, nu=0.13, init_couette=0), periodic_y=1, gx=gx, gy=gy))
+    N = nx * ny
+    for t in (0, 1, 5, 40):
+        s.step(t - s.nstep)
+        m, px, py = s.totals()
+        # rounding: each step rounds 9 N populations of size < 1/2, and in a
+        # uniform state all cells round alike (coherent), plus the final sum
+        floor = (t + 1) * 9 * N * 1.2e-16
+        assert abs(m - N) < 1e-12 * N
+        assert abs(px - t * gx * N) < floor
+        assert abs(py - t * gy * N) < floor
+        assert t == 0 or floor < 1e-6 * t * min(abs(gx), abs(gy)) * N  # far below a half-force error
+
+
+def test_total_momentum_gains_only_the_external_bead_forces():
+    # Eq. 4 spreads each bead force with weights phi_i / sum_x phi_i, which sum
+    # to one over the lattice, and the springs, bending and excluded volume
+    # are internal (they sum to zero): the fluid's momentum grows by the
+    # external force on every bead, N_b F_0 per step, and nothing else
+    nx = ny = 48
+    F0 = np.array([2e-6, -1e-6])
+    cfg = dict(wl.couette_only(nx, ny, u=0.0, nu=0.15, init_couette=0), periodic_y=1, n_beads=5, n_fibers=1,
+               a=2.0, xi=0.5, stiffness_K=0.0, k_b=0.02, bead_fx=F0[0], bead_fy=F0[1],
+               bead_xy=None, centres=[[23.7, 24.2]], theta0=[0.4])
+    cfg.pop("bead_xy")
+    s = oracle.Sim(cfg)
+    R0 = s.beads()[0]
+    # a bent start: the chain is not straight, so bending forces act
+    R0 = R0 + np.array([[0.0, 0.0], [0.1, -0.2], [0.0, 0.3], [-0.2, 0.1], [0.0, 0.0]])
+    s = oracle.Sim(cfg, R0=R0)
+    F = s.beads()[2]
+    assert np.abs(F - F0).max() > 1e-4   # internal forces are not small
+    for t in (1, 7, 30):
+        s.step(t - s.nstep)
+        m, px, py = s.totals()
+        assert abs(m - nx * ny) < 1e-12 * nx * ny
+        floor = (t + 1) * 9 * nx * ny * 1.2e-16 + 1e-13 * np.abs(s.beads()[2]).max() * t
+        assert abs(px - t * 5 * F0[0]) < floor and abs(py - t * 5 * F0[1]) < floor
+
+
+def test_total_momentum_of_linear_couette_state_with_unequal_walls():
+    # the linear wall profile is the exact discrete steady state: sum_x f c_x
+    # = N_x sum_j u(j + 1/2) = N_x N_y (u_bot + u_top) / 2 at every step
+    nx, ny, ub, ut = 30, 21, 0.004, 0.012
+    cfg = wl.couette_only(nx, ny, u=0.01, nu=0.17, init_couette=1)
+    cfg.update(u_bottom=ub, u_top=ut)
+    s = oracle.Sim(cfg)
+    for t in (0, 3, 50):
+        s.step(t - s.nstep)
+        m, px, py = s.totals()
+        # rounding as in the periodic case, doubled for the bounce-back terms
+        floor = (t + 1) * 9 * nx * ny * 2.4e-16
+        assert abs(px - nx * ny * (ub + ut) / 2) < floor
+        assert abs(py) < floor and abs(m - nx * ny) < 1e-12 * nx * ny
+
+
+# ------------------------------------------------------------ Eq. 5 weighting
+def _phi_moments(a, xi):
+    """Continuum moments of the Eq. 2 profile: phi = 1 / (1 + exp((r - a) /
+    sigma)), sigma = xi / 2, a Fermi function, whose radial moments are
+    int_0^inf r^n phi dr = -sigma^(n+1) n! Li_(n+1)(-exp(a / sigma)).
+    Returns int phi dA and the phi-weighted mean of (y - R_y)^2, which is
+    (1/2) int phi r^3 dr / int phi r dr."""
+    mpmath = pytest.importorskip("mpmath")
+    sig = xi / 2.0
+    z = -mpmath.e ** (a / sig)
+    i1 = -sig ** 2 * mpmath.polylog(2, z)
+    i3 = -6 * sig ** 4 * mpmath.polylog(4, z)
+    return float(2 * math.pi * i1), float(0.5 * i3 / i1)
+
+
+def test_bead_velocity_is_phi_weighted_mean_of_a_quadratic_shear_flow():
+    # Eq. 5 with u_x = c (y - y0)^2, u_y = 0, no forces (one bead, so no
+    # springs; f = 0):  V_x = c ((R_y - y0)^2 + <(y - R_y)^2>_phi),  V_y = 0.
+    # The phi-weighted second moment of Eq. 2's profile has the closed form
+    # of _phi_moments; at a = 10, xi = 2 the lattice sums differ from the
+    # integrals by < 1e-8 (the profile's kink at r = 0 has slope ~e^(-a/sigma)
+    # and the edge aliasing is ~exp(-2 pi^2 sigma); the cutoff tail at
+    # a + 12 xi is ~1e-10).  Weights phi^2 would give 22.9 instead of 29.09,
+    # an unweighted mean over the support ~290.
+    nx = ny = 96
+    a, xi, c, y0 = 10.0, 2.0, 3e-6, 40.2
+    cfg = dict(wl.couette_only(nx, ny, u=0.0, nu=0.1, init_couette=0), periodic_y=1, n_beads=1, n_fibers=1,
+               a=a, xi=xi, phi_cut=12.0, k_s=0.0, k_b=0.0, stiffness_K=0.0, k_ev=0.0,
+               centres=[[48.3, 47.7]], theta0=[0.0])
+    s = oracle.Sim(cfg)
+    s.step(1)   # step 0 has no bead advance
+    R = s.beads()[0][0].copy()
+    y = np.arange(ny) + 0.5
+    f = np.stack([oracle.feq(1.0, c * (yy - y0) ** 2, 0.0) for yy in y], axis=1)  # (9, ny)
+    s.set_populations(np.repeat(f[:, :, None], nx, axis=2))
+    s.step(1)
+    R1, V, F, S = s.beads()
+    area, m2 = _phi_moments(a, xi)
+    assert abs(m2 - 29.0914) < 1e-3
+    assert abs(S[0] / area - 1) < 5e-8            # S_i = int phi (Eq. 4's normaliser)
+    expect = c * ((R[1] - y0) ** 2 + m2)
+    assert abs(V[0, 0] / expect - 1) < 5e-8, (V[0, 0], expect)
+    assert abs(V[0, 1]) < 1e-12 * abs(V[0, 0])   # rounding of the u_y sum only
+    assert np.allclose(R1[0], R + V[0], rtol=0, atol=1e-15)   # forward Euler, dt = 1

@@ -11,6 +11,7 @@ class FakeBatch:
         self.max_slots, self.pool, self.used = max_slots, pool_bytes, 0
         self.slots = {}
         self.log = []
+        self.fail_at = set()  # step counts whose instances the fake reports as failed
 
     def add(self, cfg, n):
         need = serve.state_bytes(cfg, 1)
@@ -37,6 +38,11 @@ class FakeBatch:
         for s in out:
             self.slots[s].append("reported")
         return out
+
+    def info(self, slot):
+        v = self.slots[slot]
+        failed = v[1] in self.fail_at
+        return dict(state=fpd.SLOT_FAILED if failed else fpd.SLOT_FINISHED)
 
     def beads(self, slot):
         return np.zeros((1, 2)), np.zeros((1, 2)), np.zeros((1, 2)), np.zeros(1)
@@ -105,3 +111,43 @@ def test_state_bytes_pads_rows_to_128_bytes():
     assert serve.state_bytes(dict(nx=80, ny=40), 1) == 2 * 9 * 96 * 40 * 4
     assert serve.state_bytes(dict(nx=80, ny=40), 2) == 2 * 9 * 128 * 40 * 2
     assert serve.state_bytes(dict(nx=64, ny=10), 0) == 2 * 9 * 64 * 10 * 8
+
+
+def test_request_larger_than_the_cap_is_rejected_not_spun_on(fake):
+    # a request whose state alone exceeds the memory cap can never be
+    # admitted; with nothing resident the loop must reject it instead of
+    # waiting forever, and serve the others
+    one = serve.state_bytes(dict(nx=64, ny=32), 1)
+    srv = serve.Server(max_slots=4, cap_bytes=4 * one, chunk=50)
+    big = _req(0, 4096, 4096, 100, 0.0)
+    reqs = [big] + [_req(i, 64, 32, 100, 0.0) for i in range(1, 4)]
+    res = srv.serve(reqs, clock=FakeClock())
+    assert big.error.startswith("rejected") and big.slot == -1
+    assert res["failed"] == 1 and res["completed"] == 3
+    assert all(not r.error and r.result for r in reqs[1:])
+    assert srv.resident_bytes == 0
+
+
+def test_request_the_batch_refuses_outright_is_rejected(fake, monkeypatch):
+    plain_add = FakeBatch.add
+
+    def add(self, cfg, n):
+        if cfg["rid"] == 1:
+            raise fpd.FpdError(fpd.FPD_EINVAL, "bad parameters")
+        return plain_add(self, cfg, n)
+    monkeypatch.setattr(FakeBatch, "add", add)
+    srv = serve.Server(max_slots=4, cap_bytes=1 << 30, chunk=50)
+    reqs = [_req(i, 64, 32, 100, 0.0) for i in range(3)]
+    res = srv.serve(reqs, clock=FakeClock())
+    assert reqs[1].error.startswith("rejected") and res["completed"] == 2
+
+
+def test_failed_instance_is_retired_with_an_error_and_others_continue(fake):
+    srv = serve.Server(max_slots=4, cap_bytes=1 << 30, chunk=50)
+    srv.batch.fail_at = {150}     # the fake reports the 150-step request failed
+    reqs = [_req(0, 64, 32, 100, 0.0), _req(1, 64, 32, 150, 0.0), _req(2, 64, 32, 200, 0.0)]
+    res = srv.serve(reqs, clock=FakeClock())
+    assert reqs[1].error and "non-finite" in reqs[1].result["error"]
+    assert not reqs[0].error and not reqs[2].error and "R" in reqs[2].result
+    assert res["completed"] == 2 and res["failed"] == 1
+    assert srv.resident_bytes == 0 and not srv.batch.slots

@@ -34,6 +34,38 @@ def _check(fpd, sim):
         assert np.allclose(out[:3], ref[:3], rtol=1e-12, atol=1e-12 * abs(ref[0])), (out, ref)
 
 
+def test_noalloc_diag_allocates_nothing_on_a_fresh_handle(fpd):
+    # called first on a new handle (before any fpd_diag, which allocates the
+    # handle's scratch), the entry point must leave the device's free memory
+    # exactly as it was; only then is it compared with fpd_diag
+    import torch
+    from paper_2212_14153_gb300 import workloads as wl
+    # the process's first call loads the library's device module and looks
+    # up the array's address: done once here, on another handle
+    warm = fpd.Simulation(wl.couette_only(33, 17, precision=1))
+    fpd.fpd_diag_noalloc(warm.h, np.zeros(4))
+    warm.close()
+    sim = fpd.Simulation(wl.two_fiber_large(precision=1))
+    sim.step(5)
+    sim.sync()
+    torch.cuda.synchronize()
+    torch.cuda.mem_get_info()
+    free0 = torch.cuda.mem_get_info()[0]
+    outs = []
+    for _ in range(2):
+        out = np.full(4, np.nan)
+        fpd.fpd_diag_noalloc(sim.h, out)
+        outs.append(out)
+    free1 = torch.cuda.mem_get_info()[0]
+    assert free1 == free0, (free0, free1)
+    ref = np.zeros(4)
+    fpd.fpd_diag(sim.h, ref)
+    for out in outs:
+        assert out[3] == ref[3]
+        assert np.allclose(out[:3], ref[:3], rtol=1e-12, atol=1e-12 * abs(ref[0])), (out, ref)
+    sim.close()
+
+
 def test_noalloc_diag_matches_diag_two_calls_in_a_row(fpd):
     from paper_2212_14153_gb300 import workloads as wl
     # a large lattice first (1024 partial blocks), then small ones (few
