@@ -218,6 +218,19 @@ int derive(fpd_sim *s, const fpd_params &p) {
         I.scale[k] = (float)sc;
         I.inv_scale[k] = (float)(1.0 / sc);
     }
+    // the same constants in stored units (sigma_k = scale[k]): bounce-back
+    // terms and, per weight class (rest, axis, diagonal), sigma w and the
+    // multiples the two-relaxation-time collision uses
+    for (int k = 0; k < 9; ++k)
+        for (int wall = 0; wall < 2; ++wall) I.bbs[wall][k] = (float)(I.bbd[wall][k] * I.scale[k]);
+    const int rep[3] = {0, 1, 5};
+    for (int c = 0; c < 3; ++c) {
+        const double sw = (double)I.scale[rep[c]] * w[rep[c]];
+        I.trt_sw[c] = (float)sw;
+        I.trt_k45[c] = (float)(4.5 * sw);
+        I.trt_k3[c] = (float)(3.0 * sw);
+        I.trt_k9[c] = (float)(9.0 * sw);
+    }
     return FPD_OK;
 }
 

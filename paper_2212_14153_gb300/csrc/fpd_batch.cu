@@ -116,6 +116,7 @@ struct fpd_batch {
     double cell_updates = 0.0;
     bool dirty = true;
     int variant = 0;  // lattice sweep variant
+    int any_mrt = 0;  // some resident instance uses constant Lallemand-Luo rates
     // captured chunks of kGraphSteps steps, one per starting mask buffer
     // (global step mod kMaskBufs); valid until the next rebuild or tuning change
     cudaGraphExec_t graph[fpd::kMaskBufs] = {};
@@ -210,6 +211,9 @@ int rebuild(fpd_batch *b) {
         b->insts_h[s] = I;
     }
     b->ntiles = (int)tiles.size();
+    b->any_mrt = 0;
+    for (auto &sl : b->slots)
+        if (sl.state == kActive && sl.inst.collision == 1) b->any_mrt = 1;
     if (b->ntiles > b->tiles_cap || !b->masks) {
         cudaFree(b->tiles_d);
         cudaFree(b->masks);
@@ -426,7 +430,7 @@ int enqueue_bstep(fpd_batch *b, cudaStream_t st, int64_t gstep, bool any_first) 
         if (e != cudaSuccess) return bcuda(b, e, "batched bead phase");
     }
     e = fpd::launch_lattice_batch(b->precision, b->insts_d, b->tiles_d, b->ntiles, b->pool, b->tab[0], b->tab[1], mk,
-                                  gp, nbl > 0 ? 1 : 0, b->variant, st);
+                                  gp, nbl > 0 ? 1 : 0, b->variant, b->any_mrt, st);
     if (e != cudaSuccess) return bcuda(b, e, "batched lattice sweep");
     return FPD_OK;
 }

@@ -65,6 +65,12 @@ struct Inst {
     // direction k from a cell's own element in plane 0, for cells with no
     // wall and no periodic wrap among their neighbours
     int32_t pull_off[9];
+    // Stored units (FP16 storage keeps sigma_k g_k, sigma_k = scale[k]; the
+    // other precisions sigma = 1): bounce-back terms sigma_k bbf, and per
+    // weight class c (rest, axis, diagonal) sigma_c w_c, 4.5, 3 and 9 times
+    // that, for the two-relaxation-time collision in stored units
+    float bbs[2][9];
+    float trt_sw[3], trt_k45[3], trt_k3[3], trt_k9[3];
 };
 
 // phi(y) of the sandwich layers (Eq. 14) at height y
@@ -82,6 +88,14 @@ template <> __device__ __forceinline__ double bb_term<double>(const Inst &I, int
 }
 template <> __device__ __forceinline__ float bb_term<float>(const Inst &I, int wall, int k) {
     return I.bbf[wall][k];
+}
+// The same in stored units (scaled by sigma_k under FP16 storage).
+template <class R> __device__ __forceinline__ R bb_stored(const Inst &I, int wall, int k);
+template <> __device__ __forceinline__ double bb_stored<double>(const Inst &I, int wall, int k) {
+    return I.bbd[wall][k];
+}
+template <> __device__ __forceinline__ float bb_stored<float>(const Inst &I, int wall, int k) {
+    return I.bbs[wall][k];
 }
 
 // Bead table, structure of arrays.  FP64 state (Sec. 2.3 keeps R, V
@@ -105,22 +119,33 @@ __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;"
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 // ---------------------------------------------------------------- storage
+// ld / st convert between the stored value and g_k; ld_raw / st_raw move
+// the stored value itself (sigma_k g_k), converted to the arithmetic type.
 template <class T> struct Store;
 template <> struct Store<double> {
+    static constexpr bool kScaled = false;
     static __device__ __forceinline__ double ld(const double *p, float) { return *p; }
     static __device__ __forceinline__ void st(double *p, double v, float) { *p = v; }
+    static __device__ __forceinline__ double ld_raw(const double *p) { return *p; }
+    static __device__ __forceinline__ void st_raw(double *p, double v) { *p = v; }
 };
 template <> struct Store<float> {
+    static constexpr bool kScaled = false;
     static __device__ __forceinline__ float ld(const float *p, float) { return *p; }
     static __device__ __forceinline__ void st(float *p, float v, float) { *p = v; }
+    static __device__ __forceinline__ float ld_raw(const float *p) { return *p; }
+    static __device__ __forceinline__ void st_raw(float *p, float v) { *p = v; }
 };
 template <> struct Store<__half> {
+    static constexpr bool kScaled = true;
     static __device__ __forceinline__ float ld(const __half *p, float inv_scale) {
         return __half2float(*p) * inv_scale;
     }
     static __device__ __forceinline__ void st(__half *p, float v, float scale) {
         *p = __float2half_rn(v * scale);
     }
+    static __device__ __forceinline__ float ld_raw(const __half *p) { return __half2float(*p); }
+    static __device__ __forceinline__ void st_raw(__half *p, float v) { *p = __float2half_rn(v); }
 };
 
 // ------------------------------------------------------ population access
@@ -162,18 +187,22 @@ __device__ __forceinline__ Cell make_cell(const Inst &I, int x, int y) {
     return c;
 }
 
-// g_k(x) from the current buffer A.
-template <int k, class S, class R>
+// g_k(x) from the current buffer A (kRaw: in stored units, sigma_k g_k).
+template <int k, class S, class R, bool kRaw = false>
 __device__ __forceinline__ void pull_one(const S *__restrict__ A, const Inst &I, const Cell &C, R &g) {
     constexpr int cx = Q<k>::cx, cy = Q<k>::cy, o = Q<k>::opp;
     // source cell x - c_k; beyond a wall when it is row -1 or row ny
     const bool wall = (cy > 0 && C.bot) || (cy < 0 && C.top);
     if (wall) {
-        g = (R)Store<S>::ld(A + (o * I.plane32 + C.r0 + C.x), I.inv_scale[o]) + bb_term<R>(I, cy > 0 ? 0 : 1, k);
+        const S *p = A + (o * I.plane32 + C.r0 + C.x);
+        if constexpr (kRaw) g = (R)Store<S>::ld_raw(p) + bb_stored<R>(I, cy > 0 ? 0 : 1, k);
+        else g = (R)Store<S>::ld(p, I.inv_scale[o]) + bb_term<R>(I, cy > 0 ? 0 : 1, k);
     } else {
         const int rs = cy > 0 ? C.rm : (cy < 0 ? C.rp : C.r0);
         const int xs = cx > 0 ? C.xm : (cx < 0 ? C.xp : C.x);
-        g = (R)Store<S>::ld(A + (k * I.plane32 + rs + xs), I.inv_scale[k]);
+        const S *p = A + (k * I.plane32 + rs + xs);
+        if constexpr (kRaw) g = (R)Store<S>::ld_raw(p);
+        else g = (R)Store<S>::ld(p, I.inv_scale[k]);
     }
 }
 
@@ -192,32 +221,38 @@ __device__ __forceinline__ void place_one(S *__restrict__ A, const Inst &I, cons
     }
 }
 
-template <class S, class R>
+template <class S, class R, bool kRaw = false>
 __device__ __forceinline__ void pull_pops(const S *__restrict__ A, const Inst &I, const Cell &C, R g[9]) {
-    pull_one<0>(A, I, C, g[0]);
-    pull_one<1>(A, I, C, g[1]);
-    pull_one<2>(A, I, C, g[2]);
-    pull_one<3>(A, I, C, g[3]);
-    pull_one<4>(A, I, C, g[4]);
-    pull_one<5>(A, I, C, g[5]);
-    pull_one<6>(A, I, C, g[6]);
-    pull_one<7>(A, I, C, g[7]);
-    pull_one<8>(A, I, C, g[8]);
+    pull_one<0, S, R, kRaw>(A, I, C, g[0]);
+    pull_one<1, S, R, kRaw>(A, I, C, g[1]);
+    pull_one<2, S, R, kRaw>(A, I, C, g[2]);
+    pull_one<3, S, R, kRaw>(A, I, C, g[3]);
+    pull_one<4, S, R, kRaw>(A, I, C, g[4]);
+    pull_one<5, S, R, kRaw>(A, I, C, g[5]);
+    pull_one<6, S, R, kRaw>(A, I, C, g[6]);
+    pull_one<7, S, R, kRaw>(A, I, C, g[7]);
+    pull_one<8, S, R, kRaw>(A, I, C, g[8]);
 }
 
 // Pull of all nine directions for a cell with no wall and no periodic wrap
 // among its neighbours; p points at the cell's element in plane 0.
-template <class S, class R>
+template <class S, class R, bool kRaw = false>
 __device__ __forceinline__ void pull_inner(const S *__restrict__ p, const Inst &I, R g[9]) {
 #pragma unroll
-    for (int k = 0; k < 9; ++k) g[k] = (R)Store<S>::ld(p + I.pull_off[k], I.inv_scale[k]);
+    for (int k = 0; k < 9; ++k) {
+        if constexpr (kRaw) g[k] = (R)Store<S>::ld_raw(p + I.pull_off[k]);
+        else g[k] = (R)Store<S>::ld(p + I.pull_off[k], I.inv_scale[k]);
+    }
 }
 
 // Post-collision populations stored at the cell whose plane-0 element p is.
-template <class S, class R>
+template <class S, class R, bool kRaw = false>
 __device__ __forceinline__ void put_at(S *__restrict__ p, const Inst &I, const R g[9]) {
 #pragma unroll
-    for (int k = 0; k < 9; ++k) Store<S>::st(p + k * I.plane32, g[k], I.scale[k]);
+    for (int k = 0; k < 9; ++k) {
+        if constexpr (kRaw) Store<S>::st_raw(p + k * I.plane32, g[k]);
+        else Store<S>::st(p + k * I.plane32, g[k], I.scale[k]);
+    }
 }
 
 template <class S, class R>
@@ -414,6 +449,108 @@ __device__ __forceinline__ void collide(R g[9], R Fx, R Fy, R s_nu, R s_e, R s_e
     g[6] = base_dg - xd + yd - a8;
     g[7] = base_dg - xd - yd + a8;
     g[8] = base_dg + xd - yd - a8;
+}
+
+// The same collision in two-relaxation-time form, for the rate sets in
+// which every even non-conserved moment (e, eps, p_xx, p_xy) relaxes at one
+// rate sp = s_nu and every odd one (q_x, q_y) at sm = s_q: the magic rates
+// (s_e = s_eps = s_nu) and BGK.  There the moment-space update above is, in
+// exact arithmetic, the link-pair update
+//   g*_k = g_k - sp (g+_k - eq+_k) - sm (g-_k - eq-_k) + (1 - sp/2) S+_k + (1 - sm/2) S-_k
+// with g+-_k = (g_k +- g_opp k) / 2, the even and odd parts of the quadratic
+// equilibrium (deviation form, rho_0 = 1)
+//   eq+_k = w_k [(rho - 1) + rho (9/2 (c_k.u)^2 - 3/2 u^2)],  eq-_k = 3 w_k rho c_k.u,
+// and of Guo's source w_k [3 (c_k - u) + 9 (c_k.u) c_k].F
+//   S+_k = w_k [9 (c_k.u)(c_k.F) - 3 u.F],  S-_k = 3 w_k c_k.F,
+// with u = (sum_k g_k c_k + F/2) / rho as before (the conserved moments get
+// rho and j + F whatever the odd rate).  It works on stored values x_k =
+// sigma_k g_k (sigma = 1 unless FP16 storage; one sigma per weight class)
+// and returns stored values, so the FP16 path needs no per-population
+// rescaling.  About 70 operations per unforced cell against ~115 for the
+// moment form, with only the pair sums and differences kept live.
+template <class R, bool kScaled, bool kForced>
+__device__ __forceinline__ void collide_trt(R x[9], R Fx, R Fy, R sp, R sm, const Inst &I) {
+    // per weight class c = 0 (rest), 1 (axis), 2 (diagonal): sigma_c w_c
+    // and multiples, and 1 / sigma_c
+    R sw0, sw1, sw2, k45_1, k45_2, k3_1, k3_2, i0, i1, i2;
+    if constexpr (kScaled) {
+        sw0 = (R)I.trt_sw[0], sw1 = (R)I.trt_sw[1], sw2 = (R)I.trt_sw[2];
+        k45_1 = (R)I.trt_k45[1], k45_2 = (R)I.trt_k45[2];
+        k3_1 = (R)I.trt_k3[1], k3_2 = (R)I.trt_k3[2];
+        i0 = (R)I.inv_scale[0], i1 = (R)I.inv_scale[1], i2 = (R)I.inv_scale[5];
+    } else {
+        sw0 = (R)(4.0 / 9.0), sw1 = (R)(1.0 / 9.0), sw2 = (R)(1.0 / 36.0);
+        k45_1 = (R)0.5, k45_2 = (R)0.125, k3_1 = (R)(1.0 / 3.0), k3_2 = (R)(1.0 / 12.0);
+        i0 = i1 = i2 = (R)1;
+    }
+    // link pairs: a = x_k + x_opp = 2 sigma g+_k, b = x_k - x_opp = 2 sigma g-_k
+    const R a13 = x[1] + x[3], b13 = x[1] - x[3];
+    const R a24 = x[2] + x[4], b24 = x[2] - x[4];
+    const R a57 = x[5] + x[7], b57 = x[5] - x[7];
+    const R a68 = x[6] + x[8], b68 = x[6] - x[8];
+    R drho, jx, jy;
+    if constexpr (kScaled) {
+        drho = i2 * (a57 + a68) + (i1 * (a13 + a24) + i0 * x[0]);
+        jx = i2 * (b57 - b68) + i1 * b13;
+        jy = i2 * (b57 + b68) + i1 * b24;
+    } else {
+        drho = x[0] + (a13 + a24) + (a57 + a68);
+        jx = b13 + (b57 - b68);
+        jy = b24 + (b57 + b68);
+    }
+    const R rho = (R)1 + drho;
+    const R irho = recip(rho);
+    R ux, uy;
+    if constexpr (kForced) {
+        ux = (jx + (R)0.5 * Fx) * irho;
+        uy = (jy + (R)0.5 * Fy) * irho;
+    } else {
+        ux = jx * irho;
+        uy = jy * irho;
+    }
+    // sigma eq+_k = sigma w D + 4.5 sigma w rho (c.u)^2, D = rho - 1 - 1.5 rho u^2;
+    // sigma eq-_k = 3 sigma w rho c.u; here already times the rates
+    const R D = drho - (R)1.5 * (rho * (ux * ux + uy * uy));
+    const R spD = sp * D, spr = sp * rho, smr = sm * rho;
+    const R es1 = sw1 * spD, es2 = sw2 * spD;
+    const R qs1 = k45_1 * spr, qs2 = k45_2 * spr;
+    const R ts1 = k3_1 * smr, ts2 = k3_2 * smr;
+    const R c1 = (R)0.5 - (R)0.5 * sp, c2 = (R)0.5 - (R)0.5 * sm;
+    // forcing per class: (1 - sp/2) 9 sigma w, (1 - sp/2) 3 sigma w u.F, (1 - sm/2) 3 sigma w
+    R f9_1 = 0, f9_2 = 0, f3_0 = 0, f3_1 = 0, f3_2 = 0, h3_1 = 0, h3_2 = 0;
+    if constexpr (kForced) {
+        const R hp = (R)1 - (R)0.5 * sp, hm = (R)1 - (R)0.5 * sm;
+        const R hpuF = hp * (ux * Fx + uy * Fy);
+        if constexpr (kScaled) {
+            f9_1 = hp * (R)I.trt_k9[1], f9_2 = hp * (R)I.trt_k9[2];
+            f3_0 = hpuF * (R)I.trt_k3[0];
+        } else {
+            f9_1 = hp, f9_2 = (R)0.25 * hp;
+            f3_0 = (R)(4.0 / 3.0) * hpuF;
+        }
+        f3_1 = hpuF * k3_1, f3_2 = hpuF * k3_2;
+        h3_1 = hm * k3_1, h3_2 = hm * k3_2;
+    }
+    // rest population: x0 - sp (x0 - sigma_0 w_0 D) + sigma_0 (1 - sp/2) S+_0
+    x[0] = ((R)1 - sp) * x[0] + (sw0 * spD - f3_0);
+    // each pair: the even half (a/2) and the odd half (b/2) relax separately,
+    //   A = a/2 - sp (a/2 - sigma eq+) + sigma (1 - sp/2) S+,
+    //   B = b/2 - sm (b/2 - sigma eq-) + sigma (1 - sm/2) S-,
+    // and x*_k = A + B, x*_opp = A - B
+    auto pair = [&](int k, int ko, R cu, R cF, R a, R b, R es, R qs, R ts, R f9, R f3, R h3) {
+        R A = c1 * a + (qs * (cu * cu) + es);
+        R B = c2 * b + ts * cu;
+        if constexpr (kForced) {
+            A += (f9 * cu) * cF - f3;
+            B += h3 * cF;
+        }
+        x[k] = A + B;
+        x[ko] = A - B;
+    };
+    pair(1, 3, ux, Fx, a13, b13, es1, qs1, ts1, f9_1, f3_1, h3_1);
+    pair(2, 4, uy, Fy, a24, b24, es1, qs1, ts1, f9_1, f3_1, h3_1);
+    pair(5, 7, ux + uy, Fx + Fy, a57, b57, es2, qs2, ts2, f9_2, f3_2, h3_2);
+    pair(6, 8, uy - ux, Fy - Fx, a68, b68, es2, qs2, ts2, f9_2, f3_2, h3_2);
 }
 
 // Relaxation rates of one cell from its kinematic viscosity (Eq. 1 gives nu).

@@ -111,9 +111,12 @@ cudaError_t launch_watch(int precision, const Inst *insts, const Inst &inst_h, c
 // (slot, by << 16 | bx)); each instance at its own parity.  Under variant 2
 // the tiles of an instance whose nx is not a multiple of the vector width
 // run with that many cells per thread along y on the same threads.
+// any_mrt = 1 when some instance uses constant Lallemand-Luo rates
+// (collision 1): the sweep then runs variant 0 with both collision forms.
+// A single instance with collision 1 runs variant 0 as well.
 cudaError_t launch_lattice_batch(int precision, const Inst *insts, const int2 *tiles, int ntiles, void *pool,
                                  BeadTab tab0, BeadTab tab1, const SweepMasks &masks, int gparity, int after_beads,
-                                 int variant, cudaStream_t st);
+                                 int variant, int any_mrt, cudaStream_t st);
 
 cudaError_t launch_init(int precision, const Inst *inst_d, const Inst &inst_h, void *pool, int couette,
                         cudaStream_t st);

@@ -106,6 +106,44 @@ __device__ __forceinline__ void cell_overlay(const Inst &I, const BeadTab &tab, 
     }
 }
 
+// Which collision forms a kernel carries: the two-relaxation-time form only
+// (magic and BGK rate sets, collision 0 and 2: every instance of a launch),
+// the moment form only (constant Lallemand-Luo rates, collision 1), or both,
+// chosen per instance (a batch that mixes them).  Kernels with one form keep
+// the registers of that form alone.
+constexpr int kCollTrt = 0, kCollMrt = 1, kCollAny = 2;
+
+// Collision of one cell on stored values (sigma_k g_k): the two-relaxation-
+// time form for the magic and BGK rate sets (collision 0 and 2), the moment
+// form for constant Lallemand-Luo rates (collision 1).  forced: the tile has
+// a force density (beads marked in it, or a uniform body force).
+template <class S, class R, int kColl>
+__device__ __forceinline__ void collide_cell(const Inst &I, R g[9], R Fx, R Fy, R s_nu, R s_e, R s_eps, R s_q,
+                                             bool forced) {
+    constexpr bool kScaled = Store<S>::kScaled;
+    if (kColl == kCollMrt || (kColl == kCollAny && I.collision == 1)) {
+        if constexpr (kScaled) {
+#pragma unroll
+            for (int k = 0; k < 9; ++k) g[k] *= (R)I.inv_scale[k];
+        }
+        collide<R>(g, Fx, Fy, s_nu, s_e, s_eps, s_q);
+        if constexpr (kScaled) {
+#pragma unroll
+            for (int k = 0; k < 9; ++k) g[k] *= (R)I.scale[k];
+        }
+    } else if (forced) {
+        collide_trt<R, kScaled, true>(g, Fx, Fy, s_nu, s_q, I);
+    } else {
+        collide_trt<R, kScaled, false>(g, Fx, Fy, s_nu, s_q, I);
+    }
+}
+
+// Whether the uniform body force of the instance is non-zero.
+template <class R> __device__ __forceinline__ bool body_forced(const Inst &I) {
+    if constexpr (std::is_same<R, double>::value) return I.gx != 0.0 || I.gy != 0.0;
+    else return I.f_gx != 0.0f || I.f_gy != 0.0f;
+}
+
 // Whether a tile may be updated without waiting for this step's bead phase:
 // no bead marked it in the previous bead phase, whose marks cover each
 // support widened by a cell.  A bead moves less than a cell per step (its
@@ -135,7 +173,7 @@ __device__ __forceinline__ bool tile_cold_early(const unsigned *__restrict__ pre
 // plane lie a constant distance apart, so that one address serves all of
 // them (immediate offsets).  kInner: tiles away from walls and periodic
 // edges use the precomputed pull offsets.
-template <class S, int CY, bool kInner, bool kAlongX = false>
+template <class S, int CY, bool kInner, bool kAlongX, int kColl>
 __device__ __forceinline__ void lattice_tile(const Inst &I, S *__restrict__ pool, const BeadTab &tab,
                                              const unsigned *__restrict__ mask_read,
                                              const unsigned *__restrict__ mask_prev, unsigned *__restrict__ mask_clear,
@@ -162,15 +200,16 @@ __device__ __forceinline__ void lattice_tile(const Inst &I, S *__restrict__ pool
         valid[k] = x + k * RX < I.nx && y[k] < I.ny;
         if constexpr (!kInner) C[k] = make_cell(I, x + k * RX, valid[k] ? y[k] : 0);
     }
+    // populations in stored units (sigma_k g_k)
     auto pull = [&]() {
         if (inner) {
             const S *p = Asrc + (y[0] * I.pitch + x);
 #pragma unroll
-            for (int k = 0; k < CY; ++k) pull_inner<S, R>(p + (k * RY * I.pitch + k * RX), I, g[k]);
+            for (int k = 0; k < CY; ++k) pull_inner<S, R, true>(p + (k * RY * I.pitch + k * RX), I, g[k]);
         } else {
 #pragma unroll
             for (int k = 0; k < CY; ++k)
-                if (valid[k]) pull_pops<S, R>(Asrc, I, kInner ? make_cell(I, x + k * RX, y[k]) : C[k], g[k]);
+                if (valid[k]) pull_pops<S, R, true>(Asrc, I, kInner ? make_cell(I, x + k * RX, y[k]) : C[k], g[k]);
         }
     };
     // populations come from the previous sweep; when the bead phase runs
@@ -187,13 +226,14 @@ __device__ __forceinline__ void lattice_tile(const Inst &I, S *__restrict__ pool
     unsigned any = 0u;
     if (!cold)
         for (int w = 0; w < W; ++w) any |= m[w];
+    const bool forced = any != 0u || body_forced<R>(I);
 #pragma unroll
     for (int k = 0; k < CY; ++k) {
         if (!valid[k]) continue;
         R Fx, Fy, s_nu, s_e, s_eps, s_q;
         cell_overlay<R>(I, tab, m, W, any, x + k * RX, y[k], Fx, Fy, s_nu, s_e, s_eps, s_q);
-        collide<R>(g[k], Fx, Fy, s_nu, s_e, s_eps, s_q);
-        put_at<S, R>(Adst + (kInner ? y[k] * I.pitch + x + k * RX : C[k].r0 + C[k].x), I, g[k]);
+        collide_cell<S, R, kColl>(I, g[k], Fx, Fy, s_nu, s_e, s_eps, s_q, forced);
+        put_at<S, R, true>(Adst + (kInner ? y[k] * I.pitch + x + k * RX : C[k].r0 + C[k].x), I, g[k]);
     }
 }
 
@@ -207,12 +247,12 @@ __device__ __forceinline__ void lattice_tile(const Inst &I, S *__restrict__ pool
 // (its state is many times the L2: reversing measured no gain there).
 __device__ __forceinline__ int tile_order(int b, int n, int parity) { return (parity & 1) ? n - 1 - b : b; }
 
-template <class S, int CY, bool kAlongX = false>
+template <class S, int CY, bool kAlongX, int kColl>
 __global__ void __launch_bounds__(kTileX *kTileY / CY)
     k_lattice(const Inst I, S *__restrict__ pool, const BeadTab tab, const unsigned *__restrict__ mask_read,
               const unsigned *__restrict__ mask_prev, unsigned *__restrict__ mask_clear,
               const unsigned *__restrict__ status, const int parity, const int early_load, const int early_cold) {
-    lattice_tile<S, CY, true, kAlongX>(I, pool, tab, mask_read, mask_prev, mask_clear, status,
+    lattice_tile<S, CY, true, kAlongX, kColl>(I, pool, tab, mask_read, mask_prev, mask_clear, status,
                                        tile_order(blockIdx.x, gridDim.x, parity),
                                        tile_order(blockIdx.y, gridDim.y, parity), parity, early_load, early_cold,
                                        (blockIdx.x | blockIdx.y) == 0, threadIdx.x, threadIdx.y);
@@ -233,7 +273,7 @@ template <class S, int CY, bool kAlongX> struct BatchInner {
     static constexpr bool value = (CY == 1 || kAlongX) && !std::is_same<S, double>::value;
 };
 
-template <class S, int CY, bool kAlongX = false>
+template <class S, int CY, bool kAlongX, int kColl>
 __global__ void __launch_bounds__(kTileX *kTileY / CY, BatchMinBlocks<S, CY>::value)
     k_lattice_batch(const Inst *__restrict__ insts, const int2 *__restrict__ tiles, S *__restrict__ pool,
                     const BeadTab tab0, const BeadTab tab1, const unsigned *__restrict__ mask_read,
@@ -250,7 +290,7 @@ __global__ void __launch_bounds__(kTileX *kTileY / CY, BatchMinBlocks<S, CY>::va
     }
     __syncthreads();
     const int parity = gparity ^ sI.par_xor;
-    lattice_tile<S, CY, BatchInner<S, CY, kAlongX>::value, kAlongX>(
+    lattice_tile<S, CY, BatchInner<S, CY, kAlongX>::value, kAlongX, kColl>(
         sI, pool, parity ? tab1 : tab0, mask_read, mask_prev, mask_clear, status + t.x, t.y & 0xffff, t.y >> 16,
         parity, early_load, early_cold, blockIdx.x == 0, threadIdx.x, threadIdx.y);
 }
@@ -285,19 +325,15 @@ template <> struct VecIO<double, 2> {
     }
 };
 template <> struct VecIO<__half, 4> {
-    // same rounding as the scalar path: exact widening, then one multiply;
-    // one multiply, then round-to-nearest narrowing
-    static __device__ __forceinline__ void ld(const __half *p, float inv_scale, float v[4]) {
+    // stored values (sigma_k g_k): exact widening; round-to-nearest narrowing
+    static __device__ __forceinline__ void ld(const __half *p, float, float v[4]) {
         const uint2 t = *reinterpret_cast<const uint2 *>(p);
         const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&t.x));
         const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&t.y));
-        v[0] = a.x * inv_scale, v[1] = a.y * inv_scale, v[2] = b.x * inv_scale, v[3] = b.y * inv_scale;
+        v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
     }
-    static __device__ __forceinline__ __half2 pack(float a, float b, float scale) {
-        return __floats2half2_rn(a * scale, b * scale);
-    }
-    static __device__ __forceinline__ void st(__half *p, const float v[4], float scale) {
-        const __half2 a = pack(v[0], v[1], scale), b = pack(v[2], v[3], scale);
+    static __device__ __forceinline__ void st(__half *p, const float v[4], float) {
+        const __half2 a = __floats2half2_rn(v[0], v[1]), b = __floats2half2_rn(v[2], v[3]);
         uint2 t;
         t.x = *reinterpret_cast<const unsigned *>(&a);
         t.y = *reinterpret_cast<const unsigned *>(&b);
@@ -343,8 +379,9 @@ __device__ __forceinline__ void vload_one(const S *__restrict__ A, const Inst &I
     R v[NV];
     const bool wall = (cy > 0 && C.bot) || (cy < 0 && C.top);
     const int row = wall ? C.r0 : (cy > 0 ? C.rm : (cy < 0 ? C.rp : C.r0));
-    // scale[k] == scale[opp k]: one factor serves both planes
-    if (C.valid) VecIO<S, NV>::ld(A + ((wall ? o : k) * I.plane32 + row + C.x0), I.inv_scale[k], v);
+    // stored values (scale[k] == scale[opp k]: the wall's reflected plane
+    // is in the same units)
+    if (C.valid) VecIO<S, NV>::ld(A + ((wall ? o : k) * I.plane32 + row + C.x0), 1.0f, v);
     else {
 #pragma unroll
         for (int j = 0; j < NV; ++j) v[j] = (R)0;
@@ -353,7 +390,7 @@ __device__ __forceinline__ void vload_one(const S *__restrict__ A, const Inst &I
     if constexpr (cx > 0) nb = __shfl_up_sync(0xffffffffu, v[NV - 1], 1, G);
     if constexpr (cx < 0) nb = __shfl_down_sync(0xffffffffu, v[0], 1, G);
     if (wall) {
-        const R b = bb_term<R>(I, cy > 0 ? 0 : 1, k);
+        const R b = bb_stored<R>(I, cy > 0 ? 0 : 1, k);
 #pragma unroll
         for (int j = 0; j < NV; ++j) g[j][k] = v[j] + b;
         return;
@@ -362,12 +399,12 @@ __device__ __forceinline__ void vload_one(const S *__restrict__ A, const Inst &I
 #pragma unroll
         for (int j = 0; j < NV; ++j) g[j][k] = v[j];
     } else if constexpr (cx > 0) {
-        if (C.left && C.valid) nb = (R)Store<S>::ld(A + (k * I.plane32 + row + C.xm), I.inv_scale[k]);
+        if (C.left && C.valid) nb = (R)Store<S>::ld_raw(A + (k * I.plane32 + row + C.xm));
         g[0][k] = nb;
 #pragma unroll
         for (int j = 1; j < NV; ++j) g[j][k] = v[j - 1];
     } else {
-        if (C.right && C.valid) nb = (R)Store<S>::ld(A + (k * I.plane32 + row + C.xp), I.inv_scale[k]);
+        if (C.right && C.valid) nb = (R)Store<S>::ld_raw(A + (k * I.plane32 + row + C.xp));
 #pragma unroll
         for (int j = 0; j < NV - 1; ++j) g[j][k] = v[j + 1];
         g[NV - 1][k] = nb;
@@ -381,7 +418,7 @@ __device__ __forceinline__ void vstore_one(S *__restrict__ D, const Inst &I, con
     R v[NV];
 #pragma unroll
     for (int j = 0; j < NV; ++j) v[j] = g[j][k];
-    VecIO<S, NV>::st(D + (k * I.plane32 + C.r0 + C.x0), v, I.scale[k]);
+    VecIO<S, NV>::st(D + (k * I.plane32 + C.r0 + C.x0), v, 1.0f);
 }
 
 template <class S, int NV, class R>
@@ -443,11 +480,12 @@ __device__ __forceinline__ void lattice_tile_vec(const Inst &I, S *__restrict__ 
         unsigned any = 0u;
         if (!cold)
             for (int w = 0; w < W; ++w) any |= m[w];
+        const bool forced = any != 0u || body_forced<R>(I);
 #pragma unroll
         for (int j = 0; j < NV; ++j) {
             R Fx, Fy, s_nu, s_e, s_eps, s_q;
             cell_overlay<R>(I, tab, m, W, any, x0 + j, y, Fx, Fy, s_nu, s_e, s_eps, s_q);
-            collide<R>(g[j], Fx, Fy, s_nu, s_e, s_eps, s_q);
+            collide_cell<S, R, kCollTrt>(I, g[j], Fx, Fy, s_nu, s_e, s_eps, s_q, forced);
         }
     }
     vstore_pops<S, NV>(Adst, I, C, g);
@@ -495,7 +533,7 @@ __global__ void __launch_bounds__(kTileX / VecWidth<S>::value * kTileY, BatchVec
                             t.y & 0xffff, t.y >> 16, parity, early_load, early_cold, blockIdx.x == 0);
     } else {
         const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-        lattice_tile<S, NV, false>(sI, pool, parity ? tab1 : tab0, mask_read, mask_prev, mask_clear, status + t.x,
+        lattice_tile<S, NV, false, false, kCollTrt>(sI, pool, parity ? tab1 : tab0, mask_read, mask_prev, mask_clear, status + t.x,
                                    t.y & 0xffff, t.y >> 16, parity, early_load, early_cold, blockIdx.x == 0,
                                    tid % kTileX, tid / kTileX);
     }
@@ -737,6 +775,12 @@ static cudaError_t lattice_v(int variant, const Inst &I, void *pool, BeadTab tab
     cudaLaunchAttribute attr[1];
     const dim3 grid(I.ntx, I.nty);
     const int ec = after_beads ? mk.early_cold : 0;
+    // constant Lallemand-Luo rates: the moment form, one cell per thread
+    if (I.collision == 1) {
+        const cudaLaunchConfig_t cfg = sweep_config(grid, dim3(kTileX, kTileY), after_beads, st, attr);
+        return cudaLaunchKernelEx(&cfg, k_lattice<S, 1, false, kCollMrt>, I, (S *)pool, tab, mk.read, mk.prev,
+                                  mk.clear, mk.status, parity, after_beads, ec);
+    }
     if (variant == 2 && I.nx % VecWidth<S>::value == 0) {
         const cudaLaunchConfig_t cfg = sweep_config(grid, dim3(kTileX / VecWidth<S>::value, kTileY), after_beads,
                                                     st, attr);
@@ -745,12 +789,12 @@ static cudaError_t lattice_v(int variant, const Inst &I, void *pool, BeadTab tab
     }
     if (variant == 1) {
         const cudaLaunchConfig_t cfg = sweep_config(grid, dim3(kTileX / 2, kTileY), after_beads, st, attr);
-        return cudaLaunchKernelEx(&cfg, k_lattice<S, 2, true>, I, (S *)pool, tab, mk.read, mk.prev, mk.clear,
-                                  mk.status, parity, after_beads, ec);
+        return cudaLaunchKernelEx(&cfg, k_lattice<S, 2, true, kCollTrt>, I, (S *)pool, tab, mk.read, mk.prev,
+                                  mk.clear, mk.status, parity, after_beads, ec);
     }
     const cudaLaunchConfig_t cfg = sweep_config(grid, dim3(kTileX, kTileY), after_beads, st, attr);
-    return cudaLaunchKernelEx(&cfg, k_lattice<S, 1>, I, (S *)pool, tab, mk.read, mk.prev, mk.clear, mk.status,
-                              parity, after_beads, ec);
+    return cudaLaunchKernelEx(&cfg, k_lattice<S, 1, false, kCollTrt>, I, (S *)pool, tab, mk.read, mk.prev,
+                              mk.clear, mk.status, parity, after_beads, ec);
 }
 
 cudaError_t launch_lattice(int precision, const Inst *, const Inst &inst_h, void *pool, BeadTab tab,
@@ -766,10 +810,17 @@ cudaError_t launch_lattice(int precision, const Inst *, const Inst &inst_h, void
 template <class S>
 static cudaError_t lattice_batch_v(int variant, const Inst *insts, const int2 *tiles, int ntiles, void *pool,
                                    BeadTab tab0, BeadTab tab1, const SweepMasks &mk, int gparity, int after_beads,
-                                   cudaStream_t st) {
+                                   int any_mrt, cudaStream_t st) {
     cudaLaunchAttribute attr[1];
     const dim3 grid(ntiles);
     const int ec = after_beads ? mk.early_cold : 0;
+    // a batch holding instances with constant Lallemand-Luo rates: both
+    // collision forms, one cell per thread
+    if (any_mrt) {
+        const cudaLaunchConfig_t cfg = sweep_config(grid, dim3(kTileX, kTileY), after_beads, st, attr);
+        return cudaLaunchKernelEx(&cfg, k_lattice_batch<S, 1, false, kCollAny>, insts, tiles, (S *)pool, tab0, tab1,
+                                  mk.read, mk.prev, mk.clear, mk.status, gparity, after_beads, ec);
+    }
     if (variant == 2) {
         const cudaLaunchConfig_t cfg = sweep_config(grid, dim3(kTileX / VecWidth<S>::value, kTileY), after_beads,
                                                     st, attr);
@@ -778,22 +829,22 @@ static cudaError_t lattice_batch_v(int variant, const Inst *insts, const int2 *t
     }
     if (variant == 1) {
         const cudaLaunchConfig_t cfg = sweep_config(grid, dim3(kTileX / 2, kTileY), after_beads, st, attr);
-        return cudaLaunchKernelEx(&cfg, k_lattice_batch<S, 2, true>, insts, tiles, (S *)pool, tab0, tab1,
+        return cudaLaunchKernelEx(&cfg, k_lattice_batch<S, 2, true, kCollTrt>, insts, tiles, (S *)pool, tab0, tab1,
                                   mk.read, mk.prev, mk.clear, mk.status, gparity, after_beads, ec);
     }
     const cudaLaunchConfig_t cfg = sweep_config(grid, dim3(kTileX, kTileY), after_beads, st, attr);
-    return cudaLaunchKernelEx(&cfg, k_lattice_batch<S, 1>, insts, tiles, (S *)pool, tab0, tab1, mk.read, mk.prev,
-                              mk.clear, mk.status, gparity, after_beads, ec);
+    return cudaLaunchKernelEx(&cfg, k_lattice_batch<S, 1, false, kCollTrt>, insts, tiles, (S *)pool, tab0, tab1,
+                              mk.read, mk.prev, mk.clear, mk.status, gparity, after_beads, ec);
 }
 
 cudaError_t launch_lattice_batch(int precision, const Inst *insts, const int2 *tiles, int ntiles, void *pool,
                                  BeadTab tab0, BeadTab tab1, const SweepMasks &masks, int gparity, int after_beads,
-                                 int variant, cudaStream_t st) {
+                                 int variant, int any_mrt, cudaStream_t st) {
     if (ntiles <= 0) return cudaSuccess;
     switch (precision) {
-        case 0: return lattice_batch_v<double>(variant, insts, tiles, ntiles, pool, tab0, tab1, masks, gparity, after_beads, st);
-        case 1: return lattice_batch_v<float>(variant, insts, tiles, ntiles, pool, tab0, tab1, masks, gparity, after_beads, st);
-        case 2: return lattice_batch_v<__half>(variant, insts, tiles, ntiles, pool, tab0, tab1, masks, gparity, after_beads, st);
+        case 0: return lattice_batch_v<double>(variant, insts, tiles, ntiles, pool, tab0, tab1, masks, gparity, after_beads, any_mrt, st);
+        case 1: return lattice_batch_v<float>(variant, insts, tiles, ntiles, pool, tab0, tab1, masks, gparity, after_beads, any_mrt, st);
+        case 2: return lattice_batch_v<__half>(variant, insts, tiles, ntiles, pool, tab0, tab1, masks, gparity, after_beads, any_mrt, st);
     }
     return cudaErrorInvalidValue;
 }

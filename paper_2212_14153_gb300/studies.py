@@ -107,6 +107,64 @@ def sweep(name: str, a: float = 2.0, precision: int = 1, values=None) -> dict:
     return out
 
 
+# One rigid tumbling case (Sec. 4.2: K = 3.3, C = 0.2, Re_ps = 0.25, N = 10
+# beads of a = 2, r_eta = 100, r_xi = 0.125, L_x = 25 d) and variants that
+# each change one reading or numerical choice, to find what sets the period:
+# (label, overrides of tumbling_case's arguments, overrides of the config).
+READINGS = [
+    ("base", {}, {}),
+    ("r_eta 50", dict(r_eta=50.0), {}),
+    ("r_eta 300", dict(r_eta=300.0), {}),
+    ("r_eta 1000", dict(r_eta=1000.0), {}),
+    ("K 33", dict(K=33.0), {}),
+    ("K 330", dict(K=330.0), {}),
+    ("k_s x10", {}, dict(k_s="x10")),
+    ("phi_cut 4", {}, dict(phi_cut=4.0)),
+    ("Re_ps 0.1", dict(Re_ps=0.1), {}),
+    ("C 0.1", dict(C=0.1, U=0.04), {}),
+    ("L_x 50 d", dict(lx_over_d=50.0), {}),
+    ("a 4", dict(a=4.0, U=0.04), {}),
+    ("a 4, r_xi 0.0625", dict(a=4.0, U=0.04, r_xi=0.0625), {}),
+    ("a 4, r_xi 0.25", dict(a=4.0, U=0.04, r_xi=0.25), {}),
+    ("LL rates", {}, dict(collision=1)),
+    ("N 2", dict(N=2), {}),
+    ("N 2, r_eta 1000", dict(N=2, r_eta=1000.0), {}),
+]
+
+
+def readings(precision: int = 1, variants=READINGS) -> dict:
+    """gamma_dot T (180-degree turn) and the aspect ratio r_e fitted to
+    omega(theta) by Eq. 19 for each variant of the rigid tumbling case, beside
+    Jeffery's pi (r + 1/r) for the geometric r_c = 1/N and for r_e."""
+    cases = []
+    for label, kw, over in variants:
+        base = dict(K=RIGID, C=0.2, Re_ps=0.25)
+        base.update(kw)
+        K, C, Re_ps = base.pop("K"), base.pop("C"), base.pop("Re_ps")
+        cfg, g = tb.tumbling_case(K, C, Re_ps, **base)
+        for k, v in over.items():
+            if v == "x10":
+                d = 2.0 * cfg["a"]
+                cfg[k] = 10 * 0.25 * math.pi * cfg["a"] ** 2 * d * d
+            else:
+                cfg[k] = v
+        cases.append((label, cfg, g, 1.0 / cfg["n_beads"]))
+    g_min = min(g / (1.0 / r + r) for _, _, g, r in cases)
+    res = tb.measure_periods([c for _, c, _, _ in cases], int(2.2 * math.pi / g_min),
+                             sample_every=100, precision=precision)
+    rows = []
+    for (label, cfg, g, r_c), r in zip(cases, res):
+        t, th, e2e = r.track.arrays()
+        row = dict(variant=label, nx=cfg["nx"], ny=cfg["ny"], gamma_dot=g, gT=r.T * g,
+                   gT_jeffery_geometric=tb.jeffery_half_period(r_c, 1.0), min_e2e=float(e2e.min()))
+        if math.isfinite(r.T):
+            keep = t > 0.3 * r.T
+            r_fit, rms = tb.jeffery_fit(t[keep], th[keep], g)
+            row.update(r_fit=r_fit, fit_rms=rms, gT_jeffery_fitted=tb.jeffery_half_period(r_fit, 1.0))
+        rows.append(row)
+    return dict(study="readings", rows=rows)
+
+
 def hasimoto_drag(a: float, L: float) -> float:
     """F / (eta V) of a square array (period L) of rigid discs of radius a in
     Stokes flow (Hasimoto 1959), to third order in the area fraction c."""
@@ -175,7 +233,7 @@ def internal_flow(a: float = 8.0, precision: int = 1, points=INTERNAL_FLOW, visc
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("study", choices=["resolution", "internal-flow"] + sorted(SWEEPS))
+    ap.add_argument("study", choices=["resolution", "internal-flow", "readings"] + sorted(SWEEPS))
     ap.add_argument("--a", type=float, default=2.0, help="bead radius in lattice units")
     ap.add_argument("--precision", type=int, default=1, choices=[0, 1, 2])
     args = ap.parse_args(argv)
@@ -186,6 +244,8 @@ def main(argv=None):
     build.build()
     if args.study == "resolution":
         out = resolution(precision=args.precision)
+    elif args.study == "readings":
+        out = readings(precision=args.precision)
     elif args.study == "internal-flow":
         out = internal_flow(a=args.a if args.a != 2.0 else 8.0, precision=args.precision)
     else:
