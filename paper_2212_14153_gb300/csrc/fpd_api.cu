@@ -229,7 +229,6 @@ int derive(fpd_sim *s, const fpd_params &p) {
         I.trt_sw[c] = (float)sw;
         I.trt_k45[c] = (float)(4.5 * sw);
         I.trt_k3[c] = (float)(3.0 * sw);
-        I.trt_k9[c] = (float)(9.0 * sw);
     }
     return FPD_OK;
 }
@@ -346,7 +345,7 @@ int enqueue_step(fpd_sim *s, cudaStream_t st, int64_t t, bool profiled) {
     // from step 1 on, the previous bead phase (or the initial marks) is in
     // the previous buffer
     const fpd::SweepMasks mk{s->masks[t % M], s->masks[(t + M - 1) % M], s->masks[(t + 1) % M],
-                             (t >= 1 && s->early_cold) ? 1 : 0, s->status};
+                             (t >= 1 && s->early_cold) ? 1 : 0};
     e = fpd::launch_lattice(s->precision, s->inst_d, I, s->pool, s->tab[parity], mk, parity, after_beads,
                             s->variant, st);
     if (e != cudaSuccess) return cuda_fail(s, e, "lattice kernel launch");

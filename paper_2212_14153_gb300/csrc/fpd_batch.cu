@@ -421,8 +421,7 @@ int enqueue_bstep(fpd_batch *b, cudaStream_t st, int64_t gstep, bool any_first) 
     // the previous buffer holds the previous bead phase's marks unless the
     // masks were reset before this step
     const fpd::SweepMasks mk{mw, b->masks + (size_t)((gstep + M - 1) % M) * mstride,
-                             b->masks + (size_t)((gstep + 1) % M) * mstride, gstep > b->rebuild_gstep ? 1 : 0,
-                             b->status};
+                             b->masks + (size_t)((gstep + 1) % M) * mstride, gstep > b->rebuild_gstep ? 1 : 0};
     cudaError_t e;
     if (nbl > 0) {
         e = fpd::launch_beads(b->precision, b->insts_d, blist, nbl, b->pool, b->tab[0], b->tab[1], mw, gp, 1,

@@ -359,7 +359,7 @@ __global__ void __launch_bounds__(NT, BeadMinBlocks<S, NT>::value)
     __shared__ Box s_box;
     __shared__ double s_invS;
     __shared__ unsigned s_hits[kMaxBeads / 32];
-    __shared__ int s_last, s_nn;
+    __shared__ int s_last, s_nn, s_markall;
 
     // wait for the preceding sweep (the populations read below, and through
     // it the previous bead phase), then let the next sweep launch at once:
@@ -393,6 +393,7 @@ __global__ void __launch_bounds__(NT, BeadMinBlocks<S, NT>::value)
         Ry = told.Ry[b];
         if (tid == 0) S_old = told.S[b];
     }
+    if (tid == 0) s_markall = 0;
     __syncthreads();
     const Inst &I = sI;
     // populations are pulled from the current buffer (the instance's parity)
@@ -565,9 +566,16 @@ __global__ void __launch_bounds__(NT, BeadMinBlocks<S, NT>::value)
             const double inv_S = s_invS;
             const double Vx = ax * inv_S, Vy = ay * inv_S;
             // the early update of unmarked tiles assumes a bead moves less
-            // than a cell per step; flag the instance when it does not
-            if (status && !(fabs(Vx) < kFastBead && fabs(Vy) < kFastBead))
-                atomicOr(status + ii, (isfinite(Vx) && isfinite(Vy)) ? kFlagFastBead : (kFlagFastBead | kFlagNonFinite));
+            // than a cell per step; flag the instance when it does not, and
+            // from then on mark all its tiles in every phase (this bead's
+            // CTA now, the first bead's in later phases), so that they wait
+            if (status) {
+                const bool fast = !(fabs(Vx) < kFastBead && fabs(Vy) < kFastBead);
+                if (fast)
+                    atomicOr(status + ii, (isfinite(Vx) && isfinite(Vy)) ? kFlagFastBead
+                                                                         : (kFlagFastBead | kFlagNonFinite));
+                s_markall = fast || ((__ldcg(status + ii) & kFlagFastBead) && b == I.bead_off);
+            }
             const double Rnx = Rx + Vx, Rny = Ry + Vy;
             tnew.Rx[b] = Rnx;
             tnew.Ry[b] = Rny;
@@ -624,6 +632,13 @@ __global__ void __launch_bounds__(NT, BeadMinBlocks<S, NT>::value)
                 atomicOr(mask_write + tile * I.mask_words + (lb >> 5), bit);
             }
         }
+    }
+
+    // an instance flagged for a fast bead: every tile waits for this phase
+    if (s_markall) {
+        const int lb = b - I.bead_off;
+        for (int t = tid; t < I.ntx * I.nty; t += blockDim.x)
+            atomicOr(mask_write + (I.tile_base + t) * I.mask_words + (lb >> 5), 1u << (lb & 31));
     }
 
     // S_b = sum_x phi_b at the new position

@@ -67,10 +67,10 @@ struct Inst {
     int32_t pull_off[9];
     // Stored units (FP16 storage keeps sigma_k g_k, sigma_k = scale[k]; the
     // other precisions sigma = 1): bounce-back terms sigma_k bbf, and per
-    // weight class c (rest, axis, diagonal) sigma_c w_c, 4.5, 3 and 9 times
+    // weight class c (rest, axis, diagonal) sigma_c w_c, 4.5 and 3 times
     // that, for the two-relaxation-time collision in stored units
     float bbs[2][9];
-    float trt_sw[3], trt_k45[3], trt_k3[3], trt_k9[3];
+    float trt_sw[3], trt_k45[3], trt_k3[3];
 };
 
 // phi(y) of the sandwich layers (Eq. 14) at height y
@@ -451,25 +451,23 @@ __device__ __forceinline__ void collide(R g[9], R Fx, R Fy, R s_nu, R s_e, R s_e
     g[8] = base_dg + xd - yd - a8;
 }
 
-// The same collision in two-relaxation-time form, for the rate sets in
-// which every even non-conserved moment (e, eps, p_xx, p_xy) relaxes at one
-// rate sp = s_nu and every odd one (q_x, q_y) at sm = s_q: the magic rates
-// (s_e = s_eps = s_nu) and BGK.  There the moment-space update above is, in
-// exact arithmetic, the link-pair update
-//   g*_k = g_k - sp (g+_k - eq+_k) - sm (g-_k - eq-_k) + (1 - sp/2) S+_k + (1 - sm/2) S-_k
-// with g+-_k = (g_k +- g_opp k) / 2, the even and odd parts of the quadratic
-// equilibrium (deviation form, rho_0 = 1)
+// The same collision in two-relaxation-time form for an unforced cell, for
+// the rate sets in which every even non-conserved moment (e, eps, p_xx,
+// p_xy) relaxes at one rate sp = s_nu and every odd one (q_x, q_y) at
+// sm = s_q: the magic rates (s_e = s_eps = s_nu) and BGK.  There the
+// moment-space update above with F = 0 is, in exact arithmetic, the
+// link-pair update
+//   g*_k = g_k - sp (g+_k - eq+_k) - sm (g-_k - eq-_k)
+// with g+-_k = (g_k +- g_opp k) / 2 and the even and odd parts of the
+// quadratic equilibrium (deviation form, rho_0 = 1)
 //   eq+_k = w_k [(rho - 1) + rho (9/2 (c_k.u)^2 - 3/2 u^2)],  eq-_k = 3 w_k rho c_k.u,
-// and of Guo's source w_k [3 (c_k - u) + 9 (c_k.u) c_k].F
-//   S+_k = w_k [9 (c_k.u)(c_k.F) - 3 u.F],  S-_k = 3 w_k c_k.F,
-// with u = (sum_k g_k c_k + F/2) / rho as before (the conserved moments get
-// rho and j + F whatever the odd rate).  It works on stored values x_k =
-// sigma_k g_k (sigma = 1 unless FP16 storage; one sigma per weight class)
-// and returns stored values, so the FP16 path needs no per-population
-// rescaling.  About 70 operations per unforced cell against ~115 for the
-// moment form, with only the pair sums and differences kept live.
-template <class R, bool kScaled, bool kForced>
-__device__ __forceinline__ void collide_trt(R x[9], R Fx, R Fy, R sp, R sm, const Inst &I) {
+// u = sum_k g_k c_k / rho.  It works on stored values x_k = sigma_k g_k
+// (sigma = 1 unless FP16 storage; one sigma per weight class) and returns
+// stored values, so the FP16 path needs no per-population rescaling, and it
+// keeps only the pair sums and differences live: about 60 operations per
+// cell against ~115 for the moment form.
+template <class R, bool kScaled>
+__device__ __forceinline__ void collide_trt(R x[9], R sp, R sm, const Inst &I) {
     // per weight class c = 0 (rest), 1 (axis), 2 (diagonal): sigma_c w_c
     // and multiples, and 1 / sigma_c
     R sw0, sw1, sw2, k45_1, k45_2, k3_1, k3_2, i0, i1, i2;
@@ -500,14 +498,7 @@ __device__ __forceinline__ void collide_trt(R x[9], R Fx, R Fy, R sp, R sm, cons
     }
     const R rho = (R)1 + drho;
     const R irho = recip(rho);
-    R ux, uy;
-    if constexpr (kForced) {
-        ux = (jx + (R)0.5 * Fx) * irho;
-        uy = (jy + (R)0.5 * Fy) * irho;
-    } else {
-        ux = jx * irho;
-        uy = jy * irho;
-    }
+    const R ux = jx * irho, uy = jy * irho;
     // sigma eq+_k = sigma w D + 4.5 sigma w rho (c.u)^2, D = rho - 1 - 1.5 rho u^2;
     // sigma eq-_k = 3 sigma w rho c.u; here already times the rates
     const R D = drho - (R)1.5 * (rho * (ux * ux + uy * uy));
@@ -516,41 +507,21 @@ __device__ __forceinline__ void collide_trt(R x[9], R Fx, R Fy, R sp, R sm, cons
     const R qs1 = k45_1 * spr, qs2 = k45_2 * spr;
     const R ts1 = k3_1 * smr, ts2 = k3_2 * smr;
     const R c1 = (R)0.5 - (R)0.5 * sp, c2 = (R)0.5 - (R)0.5 * sm;
-    // forcing per class: (1 - sp/2) 9 sigma w, (1 - sp/2) 3 sigma w u.F, (1 - sm/2) 3 sigma w
-    R f9_1 = 0, f9_2 = 0, f3_0 = 0, f3_1 = 0, f3_2 = 0, h3_1 = 0, h3_2 = 0;
-    if constexpr (kForced) {
-        const R hp = (R)1 - (R)0.5 * sp, hm = (R)1 - (R)0.5 * sm;
-        const R hpuF = hp * (ux * Fx + uy * Fy);
-        if constexpr (kScaled) {
-            f9_1 = hp * (R)I.trt_k9[1], f9_2 = hp * (R)I.trt_k9[2];
-            f3_0 = hpuF * (R)I.trt_k3[0];
-        } else {
-            f9_1 = hp, f9_2 = (R)0.25 * hp;
-            f3_0 = (R)(4.0 / 3.0) * hpuF;
-        }
-        f3_1 = hpuF * k3_1, f3_2 = hpuF * k3_2;
-        h3_1 = hm * k3_1, h3_2 = hm * k3_2;
-    }
-    // rest population: x0 - sp (x0 - sigma_0 w_0 D) + sigma_0 (1 - sp/2) S+_0
-    x[0] = ((R)1 - sp) * x[0] + (sw0 * spD - f3_0);
+    // rest population: x0 - sp (x0 - sigma_0 w_0 D)
+    x[0] = ((R)1 - sp) * x[0] + sw0 * spD;
     // each pair: the even half (a/2) and the odd half (b/2) relax separately,
-    //   A = a/2 - sp (a/2 - sigma eq+) + sigma (1 - sp/2) S+,
-    //   B = b/2 - sm (b/2 - sigma eq-) + sigma (1 - sm/2) S-,
+    //   A = a/2 - sp (a/2 - sigma eq+),  B = b/2 - sm (b/2 - sigma eq-),
     // and x*_k = A + B, x*_opp = A - B
-    auto pair = [&](int k, int ko, R cu, R cF, R a, R b, R es, R qs, R ts, R f9, R f3, R h3) {
-        R A = c1 * a + (qs * (cu * cu) + es);
-        R B = c2 * b + ts * cu;
-        if constexpr (kForced) {
-            A += (f9 * cu) * cF - f3;
-            B += h3 * cF;
-        }
+    auto pair = [&](int k, int ko, R cu, R a, R b, R es, R qs, R ts) {
+        const R A = c1 * a + (qs * (cu * cu) + es);
+        const R B = c2 * b + ts * cu;
         x[k] = A + B;
         x[ko] = A - B;
     };
-    pair(1, 3, ux, Fx, a13, b13, es1, qs1, ts1, f9_1, f3_1, h3_1);
-    pair(2, 4, uy, Fy, a24, b24, es1, qs1, ts1, f9_1, f3_1, h3_1);
-    pair(5, 7, ux + uy, Fx + Fy, a57, b57, es2, qs2, ts2, f9_2, f3_2, h3_2);
-    pair(6, 8, uy - ux, Fy - Fx, a68, b68, es2, qs2, ts2, f9_2, f3_2, h3_2);
+    pair(1, 3, ux, a13, b13, es1, qs1, ts1);
+    pair(2, 4, uy, a24, b24, es1, qs1, ts1);
+    pair(5, 7, ux + uy, a57, b57, es2, qs2, ts2);
+    pair(6, 8, uy - ux, a68, b68, es2, qs2, ts2);
 }
 
 // Relaxation rates of one cell from its kinematic viscosity (Eq. 1 gives nu).

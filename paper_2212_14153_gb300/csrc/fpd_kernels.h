@@ -34,18 +34,16 @@ struct SweepMasks {
     const unsigned *prev;  // the previous bead phase's marks
     unsigned *clear;       // zeroed for the next bead phase
     int early_cold;
-    // per-instance status words (index 0 for a single instance, the slot in
-    // a batch): an instance with kFlagFastBead set takes the waiting path
-    const unsigned *status;
 };
 
 // Sticky per-instance status bits, set on the device (values of the
 // FPD_FLAG_* constants of fpd.h).  kFlagFastBead: a bead phase found a bead
 // velocity component of magnitude >= kFastBead cells per step (or a
-// non-finite one); from then on the instance's sweeps no longer update
-// unmarked tiles early, because that path assumes a bead moves less than a
-// cell per step.  kFlagNonFinite: a non-finite bead velocity, or a
-// non-finite population found by the watchdog.
+// non-finite one); that phase and every later one then mark all tiles of the
+// instance, so that no sweep updates a tile early any more (that path
+// assumes a bead moves less than a cell per step).  kFlagNonFinite: a
+// non-finite bead velocity, or a non-finite population found by the
+// watchdog.
 constexpr unsigned kFlagFastBead = 1u;
 constexpr unsigned kFlagNonFinite = 2u;
 constexpr double kFastBead = 0.5;
@@ -93,7 +91,8 @@ struct BeadExport {
 };
 // status: per-instance status words (indexed by instance slot), where a
 // bead velocity component of magnitude >= kFastBead or a non-finite one sets
-// kFlagFastBead (and kFlagNonFinite); NULL: not checked.
+// kFlagFastBead (and kFlagNonFinite), after which every tile of the
+// instance is marked in mask_write; NULL: not checked.
 cudaError_t launch_beads(int precision, const Inst *inst_d, const int2 *blist, int nb_total,
                          const void *pool, BeadTab tab0, BeadTab tab1, unsigned *mask_write, int gparity,
                          int advance, unsigned *counters, int pdl, cudaStream_t st, BeadExport ex = BeadExport{},

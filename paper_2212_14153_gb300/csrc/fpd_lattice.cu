@@ -106,22 +106,25 @@ __device__ __forceinline__ void cell_overlay(const Inst &I, const BeadTab &tab, 
     }
 }
 
-// Which collision forms a kernel carries: the two-relaxation-time form only
-// (magic and BGK rate sets, collision 0 and 2: every instance of a launch),
-// the moment form only (constant Lallemand-Luo rates, collision 1), or both,
-// chosen per instance (a batch that mixes them).  Kernels with one form keep
-// the registers of that form alone.
+// Which collision forms a kernel carries: the moment form only (constant
+// Lallemand-Luo rates, collision 1), or the two-relaxation-time form for
+// unforced cells of the magic and BGK rate sets (collision 0 and 2) with the
+// moment form for the rest, or that choice made per instance (a batch that
+// mixes rate sets).  Kernels with fewer forms keep fewer registers.
 constexpr int kCollTrt = 0, kCollMrt = 1, kCollAny = 2;
 
-// Collision of one cell on stored values (sigma_k g_k): the two-relaxation-
-// time form for the magic and BGK rate sets (collision 0 and 2), the moment
-// form for constant Lallemand-Luo rates (collision 1).  forced: the tile has
-// a force density (beads marked in it, or a uniform body force).
+// Collision of one cell on stored values (sigma_k g_k).  The moment form
+// serves constant Lallemand-Luo rates and every forced cell (a tile with
+// beads marked in it, or a uniform body force); the two-relaxation-time form,
+// equal in exact arithmetic, serves the unforced cells of the magic and BGK
+// rate sets (most of a lattice).  Every kernel makes the same choice per
+// cell, so an instance gives the same bits in every launch shape and in a
+// batch.
 template <class S, class R, int kColl>
 __device__ __forceinline__ void collide_cell(const Inst &I, R g[9], R Fx, R Fy, R s_nu, R s_e, R s_eps, R s_q,
                                              bool forced) {
     constexpr bool kScaled = Store<S>::kScaled;
-    if (kColl == kCollMrt || (kColl == kCollAny && I.collision == 1)) {
+    if (kColl == kCollMrt || (kColl == kCollAny && I.collision == 1) || forced) {
         if constexpr (kScaled) {
 #pragma unroll
             for (int k = 0; k < 9; ++k) g[k] *= (R)I.inv_scale[k];
@@ -131,10 +134,8 @@ __device__ __forceinline__ void collide_cell(const Inst &I, R g[9], R Fx, R Fy, 
 #pragma unroll
             for (int k = 0; k < 9; ++k) g[k] *= (R)I.scale[k];
         }
-    } else if (forced) {
-        collide_trt<R, kScaled, true>(g, Fx, Fy, s_nu, s_q, I);
     } else {
-        collide_trt<R, kScaled, false>(g, Fx, Fy, s_nu, s_q, I);
+        collide_trt<R, kScaled>(g, s_nu, s_q, I);
     }
 }
 
@@ -152,14 +153,12 @@ template <class R> __device__ __forceinline__ bool body_forced(const Inst &I) {
 // step either, and the bead phase reads no population of it.  The bead
 // phase checks that assumption (|V| < kFastBead per component, with the
 // marks covering moves of more than a cell): once it has failed for an
-// instance, its status word carries kFlagFastBead and every tile of it
-// waits.  That word was written by an earlier bead phase, which completed
-// before the previous sweep did.  The lead CTA always waits: the next launch
-// in the stream then cannot start before the bead phase has completed.
+// instance, that phase and every later one mark all tiles of the instance,
+// so that they all wait.  The lead CTA always waits: the next launch in the
+// stream then cannot start before the bead phase has completed.
 __device__ __forceinline__ bool tile_cold_early(const unsigned *__restrict__ prev, const int W, const int early_cold,
-                                                const bool lead, const unsigned *__restrict__ status) {
+                                                const bool lead) {
     if (!early_cold || lead) return false;
-    if (__ldcg(status) & kFlagFastBead) return false;
     unsigned any = 0u;
     for (int w = 0; w < W; ++w) any |= prev[w];
     return any == 0u;
@@ -177,9 +176,8 @@ template <class S, int CY, bool kInner, bool kAlongX, int kColl>
 __device__ __forceinline__ void lattice_tile(const Inst &I, S *__restrict__ pool, const BeadTab &tab,
                                              const unsigned *__restrict__ mask_read,
                                              const unsigned *__restrict__ mask_prev, unsigned *__restrict__ mask_clear,
-                                             const unsigned *__restrict__ status, const int bx, const int by,
-                                             const int parity, const int early_load, const int early_cold,
-                                             const bool lead, const int tx, const int ty) {
+                                             const int bx, const int by, const int parity, const int early_load,
+                                             const int early_cold, const bool lead, const int tx, const int ty) {
     using R = typename Real<S>::type;
     constexpr int RY = kAlongX ? 0 : kTileY / CY;
     constexpr int RX = kAlongX ? kTileX / CY : 0;
@@ -215,7 +213,7 @@ __device__ __forceinline__ void lattice_tile(const Inst &I, S *__restrict__ pool
     // populations come from the previous sweep; when the bead phase runs
     // between the two sweeps they may be loaded before waiting on it
     if (early_load) pull();
-    const bool cold = tile_cold_early(mask_prev + tile * W, W, early_cold, lead, status);
+    const bool cold = tile_cold_early(mask_prev + tile * W, W, early_cold, lead);
     if (!cold) pdl_wait();
     pdl_trigger();
     if (tx == 0 && ty == 0)  // a mask of two steps back, for the next bead phase
@@ -250,9 +248,9 @@ __device__ __forceinline__ int tile_order(int b, int n, int parity) { return (pa
 template <class S, int CY, bool kAlongX, int kColl>
 __global__ void __launch_bounds__(kTileX *kTileY / CY)
     k_lattice(const Inst I, S *__restrict__ pool, const BeadTab tab, const unsigned *__restrict__ mask_read,
-              const unsigned *__restrict__ mask_prev, unsigned *__restrict__ mask_clear,
-              const unsigned *__restrict__ status, const int parity, const int early_load, const int early_cold) {
-    lattice_tile<S, CY, true, kAlongX, kColl>(I, pool, tab, mask_read, mask_prev, mask_clear, status,
+              const unsigned *__restrict__ mask_prev, unsigned *__restrict__ mask_clear, const int parity,
+              const int early_load, const int early_cold) {
+    lattice_tile<S, CY, true, kAlongX, kColl>(I, pool, tab, mask_read, mask_prev, mask_clear,
                                        tile_order(blockIdx.x, gridDim.x, parity),
                                        tile_order(blockIdx.y, gridDim.y, parity), parity, early_load, early_cold,
                                        (blockIdx.x | blockIdx.y) == 0, threadIdx.x, threadIdx.y);
@@ -277,9 +275,8 @@ template <class S, int CY, bool kAlongX, int kColl>
 __global__ void __launch_bounds__(kTileX *kTileY / CY, BatchMinBlocks<S, CY>::value)
     k_lattice_batch(const Inst *__restrict__ insts, const int2 *__restrict__ tiles, S *__restrict__ pool,
                     const BeadTab tab0, const BeadTab tab1, const unsigned *__restrict__ mask_read,
-                    const unsigned *__restrict__ mask_prev, unsigned *__restrict__ mask_clear,
-                    const unsigned *__restrict__ status, const int gparity, const int early_load,
-                    const int early_cold) {
+                    const unsigned *__restrict__ mask_prev, unsigned *__restrict__ mask_clear, const int gparity,
+                    const int early_load, const int early_cold) {
     __shared__ Inst sI;
     const int2 t = tiles[blockIdx.x];
     {
@@ -291,8 +288,8 @@ __global__ void __launch_bounds__(kTileX *kTileY / CY, BatchMinBlocks<S, CY>::va
     __syncthreads();
     const int parity = gparity ^ sI.par_xor;
     lattice_tile<S, CY, BatchInner<S, CY, kAlongX>::value, kAlongX, kColl>(
-        sI, pool, parity ? tab1 : tab0, mask_read, mask_prev, mask_clear, status + t.x, t.y & 0xffff, t.y >> 16,
-        parity, early_load, early_cold, blockIdx.x == 0, threadIdx.x, threadIdx.y);
+        sI, pool, parity ? tab1 : tab0, mask_read, mask_prev, mask_clear, t.y & 0xffff, t.y >> 16, parity,
+        early_load, early_cold, blockIdx.x == 0, threadIdx.x, threadIdx.y);
 }
 
 // ------------------------------------------------ vectorised sweep (variant 2)
@@ -454,8 +451,7 @@ template <class S>
 __device__ __forceinline__ void lattice_tile_vec(const Inst &I, S *__restrict__ pool, const BeadTab &tab,
                                                  const unsigned *__restrict__ mask_read,
                                                  const unsigned *__restrict__ mask_prev,
-                                                 unsigned *__restrict__ mask_clear,
-                                                 const unsigned *__restrict__ status, const int bx, const int by,
+                                                 unsigned *__restrict__ mask_clear, const int bx, const int by,
                                                  const int parity, const int early_load, const int early_cold,
                                                  const bool lead) {
     using R = typename Real<S>::type;
@@ -469,7 +465,7 @@ __device__ __forceinline__ void lattice_tile_vec(const Inst &I, S *__restrict__ 
     const VCell C = make_vcell<NV>(I, x0, y, threadIdx.x);
     R g[NV][9];
     if (early_load) vload_pops<S, NV>(Asrc, I, C, g);
-    const bool cold = tile_cold_early(mask_prev + tile * W, W, early_cold, lead, status);
+    const bool cold = tile_cold_early(mask_prev + tile * W, W, early_cold, lead);
     if (!cold) pdl_wait();
     pdl_trigger();
     if (threadIdx.x == 0 && threadIdx.y == 0)
@@ -494,11 +490,9 @@ __device__ __forceinline__ void lattice_tile_vec(const Inst &I, S *__restrict__ 
 template <class S>
 __global__ void __launch_bounds__(kTileX / VecWidth<S>::value * kTileY)
     k_lattice_vec(const Inst I, S *__restrict__ pool, const BeadTab tab, const unsigned *__restrict__ mask_read,
-                  const unsigned *__restrict__ mask_prev, unsigned *__restrict__ mask_clear,
-                  const unsigned *__restrict__ status, const int parity, const int early_load,
-                  const int early_cold) {
-    lattice_tile_vec<S>(I, pool, tab, mask_read, mask_prev, mask_clear, status,
-                        tile_order(blockIdx.x, gridDim.x, parity),
+                  const unsigned *__restrict__ mask_prev, unsigned *__restrict__ mask_clear, const int parity,
+                  const int early_load, const int early_cold) {
+    lattice_tile_vec<S>(I, pool, tab, mask_read, mask_prev, mask_clear, tile_order(blockIdx.x, gridDim.x, parity),
                         tile_order(blockIdx.y, gridDim.y, parity), parity, early_load, early_cold,
                         (blockIdx.x | blockIdx.y) == 0);
 }
@@ -511,9 +505,8 @@ template <class S>
 __global__ void __launch_bounds__(kTileX / VecWidth<S>::value * kTileY, BatchVecMinBlocks<S>::value)
     k_lattice_batch_vec(const Inst *__restrict__ insts, const int2 *__restrict__ tiles, S *__restrict__ pool,
                         const BeadTab tab0, const BeadTab tab1, const unsigned *__restrict__ mask_read,
-                        const unsigned *__restrict__ mask_prev, unsigned *__restrict__ mask_clear,
-                        const unsigned *__restrict__ status, const int gparity, const int early_load,
-                        const int early_cold) {
+                        const unsigned *__restrict__ mask_prev, unsigned *__restrict__ mask_clear, const int gparity,
+                        const int early_load, const int early_cold) {
     constexpr int NT = kTileX / VecWidth<S>::value * kTileY;
     __shared__ Inst sI;
     const int2 t = tiles[blockIdx.x];
@@ -529,13 +522,13 @@ __global__ void __launch_bounds__(kTileX / VecWidth<S>::value * kTileY, BatchVec
     // on the same threads: NV cells per thread along y
     constexpr int NV = VecWidth<S>::value;
     if (sI.nx % NV == 0) {
-        lattice_tile_vec<S>(sI, pool, parity ? tab1 : tab0, mask_read, mask_prev, mask_clear, status + t.x,
-                            t.y & 0xffff, t.y >> 16, parity, early_load, early_cold, blockIdx.x == 0);
+        lattice_tile_vec<S>(sI, pool, parity ? tab1 : tab0, mask_read, mask_prev, mask_clear, t.y & 0xffff,
+                            t.y >> 16, parity, early_load, early_cold, blockIdx.x == 0);
     } else {
         const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-        lattice_tile<S, NV, false, false, kCollTrt>(sI, pool, parity ? tab1 : tab0, mask_read, mask_prev, mask_clear, status + t.x,
-                                   t.y & 0xffff, t.y >> 16, parity, early_load, early_cold, blockIdx.x == 0,
-                                   tid % kTileX, tid / kTileX);
+        lattice_tile<S, NV, false, false, kCollTrt>(sI, pool, parity ? tab1 : tab0, mask_read, mask_prev,
+                                                    mask_clear, t.y & 0xffff, t.y >> 16, parity, early_load,
+                                                    early_cold, blockIdx.x == 0, tid % kTileX, tid / kTileX);
     }
 }
 
@@ -779,22 +772,22 @@ static cudaError_t lattice_v(int variant, const Inst &I, void *pool, BeadTab tab
     if (I.collision == 1) {
         const cudaLaunchConfig_t cfg = sweep_config(grid, dim3(kTileX, kTileY), after_beads, st, attr);
         return cudaLaunchKernelEx(&cfg, k_lattice<S, 1, false, kCollMrt>, I, (S *)pool, tab, mk.read, mk.prev,
-                                  mk.clear, mk.status, parity, after_beads, ec);
+                                  mk.clear, parity, after_beads, ec);
     }
     if (variant == 2 && I.nx % VecWidth<S>::value == 0) {
         const cudaLaunchConfig_t cfg = sweep_config(grid, dim3(kTileX / VecWidth<S>::value, kTileY), after_beads,
                                                     st, attr);
-        return cudaLaunchKernelEx(&cfg, k_lattice_vec<S>, I, (S *)pool, tab, mk.read, mk.prev, mk.clear, mk.status,
+        return cudaLaunchKernelEx(&cfg, k_lattice_vec<S>, I, (S *)pool, tab, mk.read, mk.prev, mk.clear,
                                   parity, after_beads, ec);
     }
     if (variant == 1) {
         const cudaLaunchConfig_t cfg = sweep_config(grid, dim3(kTileX / 2, kTileY), after_beads, st, attr);
         return cudaLaunchKernelEx(&cfg, k_lattice<S, 2, true, kCollTrt>, I, (S *)pool, tab, mk.read, mk.prev,
-                                  mk.clear, mk.status, parity, after_beads, ec);
+                                  mk.clear, parity, after_beads, ec);
     }
     const cudaLaunchConfig_t cfg = sweep_config(grid, dim3(kTileX, kTileY), after_beads, st, attr);
     return cudaLaunchKernelEx(&cfg, k_lattice<S, 1, false, kCollTrt>, I, (S *)pool, tab, mk.read, mk.prev,
-                              mk.clear, mk.status, parity, after_beads, ec);
+                              mk.clear, parity, after_beads, ec);
 }
 
 cudaError_t launch_lattice(int precision, const Inst *, const Inst &inst_h, void *pool, BeadTab tab,
@@ -819,22 +812,22 @@ static cudaError_t lattice_batch_v(int variant, const Inst *insts, const int2 *t
     if (any_mrt) {
         const cudaLaunchConfig_t cfg = sweep_config(grid, dim3(kTileX, kTileY), after_beads, st, attr);
         return cudaLaunchKernelEx(&cfg, k_lattice_batch<S, 1, false, kCollAny>, insts, tiles, (S *)pool, tab0, tab1,
-                                  mk.read, mk.prev, mk.clear, mk.status, gparity, after_beads, ec);
+                                  mk.read, mk.prev, mk.clear, gparity, after_beads, ec);
     }
     if (variant == 2) {
         const cudaLaunchConfig_t cfg = sweep_config(grid, dim3(kTileX / VecWidth<S>::value, kTileY), after_beads,
                                                     st, attr);
         return cudaLaunchKernelEx(&cfg, k_lattice_batch_vec<S>, insts, tiles, (S *)pool, tab0, tab1, mk.read,
-                                  mk.prev, mk.clear, mk.status, gparity, after_beads, ec);
+                                  mk.prev, mk.clear, gparity, after_beads, ec);
     }
     if (variant == 1) {
         const cudaLaunchConfig_t cfg = sweep_config(grid, dim3(kTileX / 2, kTileY), after_beads, st, attr);
         return cudaLaunchKernelEx(&cfg, k_lattice_batch<S, 2, true, kCollTrt>, insts, tiles, (S *)pool, tab0, tab1,
-                                  mk.read, mk.prev, mk.clear, mk.status, gparity, after_beads, ec);
+                                  mk.read, mk.prev, mk.clear, gparity, after_beads, ec);
     }
     const cudaLaunchConfig_t cfg = sweep_config(grid, dim3(kTileX, kTileY), after_beads, st, attr);
     return cudaLaunchKernelEx(&cfg, k_lattice_batch<S, 1, false, kCollTrt>, insts, tiles, (S *)pool, tab0, tab1,
-                              mk.read, mk.prev, mk.clear, mk.status, gparity, after_beads, ec);
+                              mk.read, mk.prev, mk.clear, gparity, after_beads, ec);
 }
 
 cudaError_t launch_lattice_batch(int precision, const Inst *insts, const int2 *tiles, int ntiles, void *pool,

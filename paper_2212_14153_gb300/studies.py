@@ -132,6 +132,19 @@ READINGS = [
 ]
 
 
+# The interface-width series of the rigid case: beads of a = 8 cells (so that
+# thin interfaces stay resolved), r_xi = xi / d from 0.125 down to 1/64, and
+# the viscosity ratio at the thinnest interfaces.
+INTERFACE = [
+    ("a 8, r_xi 0.125", dict(a=8.0, U=0.04), {}),
+    ("a 8, r_xi 0.0625", dict(a=8.0, U=0.04, r_xi=0.0625), {}),
+    ("a 8, r_xi 0.03125", dict(a=8.0, U=0.04, r_xi=0.03125), {}),
+    ("a 8, r_xi 0.015625", dict(a=8.0, U=0.04, r_xi=0.015625), {}),
+    ("a 8, r_xi 0.03125, r_eta 20", dict(a=8.0, U=0.04, r_xi=0.03125, r_eta=20.0), {}),
+    ("a 8, r_xi 0.03125, r_eta 500", dict(a=8.0, U=0.04, r_xi=0.03125, r_eta=500.0), {}),
+]
+
+
 def readings(precision: int = 1, variants=READINGS) -> dict:
     """gamma_dot T (180-degree turn) and the aspect ratio r_e fitted to
     omega(theta) by Eq. 19 for each variant of the rigid tumbling case, beside
@@ -156,8 +169,9 @@ def readings(precision: int = 1, variants=READINGS) -> dict:
     for (label, cfg, g, r_c), r in zip(cases, res):
         t, th, e2e = r.track.arrays()
         row = dict(variant=label, nx=cfg["nx"], ny=cfg["ny"], gamma_dot=g, gT=r.T * g,
-                   gT_jeffery_geometric=tb.jeffery_half_period(r_c, 1.0), min_e2e=float(e2e.min()))
-        if math.isfinite(r.T):
+                   gT_jeffery_geometric=tb.jeffery_half_period(r_c, 1.0),
+                   min_e2e=float(e2e.min()) if len(e2e) else float("nan"))
+        if math.isfinite(r.T) and len(t) > 10:
             keep = t > 0.3 * r.T
             r_fit, rms = tb.jeffery_fit(t[keep], th[keep], g)
             row.update(r_fit=r_fit, fit_rms=rms, gT_jeffery_fitted=tb.jeffery_half_period(r_fit, 1.0))
@@ -233,7 +247,7 @@ def internal_flow(a: float = 8.0, precision: int = 1, points=INTERNAL_FLOW, visc
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("study", choices=["resolution", "internal-flow", "readings"] + sorted(SWEEPS))
+    ap.add_argument("study", choices=["resolution", "internal-flow", "readings", "interface"] + sorted(SWEEPS))
     ap.add_argument("--a", type=float, default=2.0, help="bead radius in lattice units")
     ap.add_argument("--precision", type=int, default=1, choices=[0, 1, 2])
     args = ap.parse_args(argv)
@@ -246,6 +260,8 @@ def main(argv=None):
         out = resolution(precision=args.precision)
     elif args.study == "readings":
         out = readings(precision=args.precision)
+    elif args.study == "interface":
+        out = readings(precision=args.precision, variants=INTERFACE)
     elif args.study == "internal-flow":
         out = internal_flow(a=args.a if args.a != 2.0 else 8.0, precision=args.precision)
     else:

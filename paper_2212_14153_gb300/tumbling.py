@@ -204,7 +204,8 @@ def measure_periods(configs: list[dict], max_steps: int, sample_every: int = 200
     horizontal to horizontal).  An instance leaves the batch as soon as its
     period is measured, or when over the last `stuck_window` steps (default
     max_steps / 5) it has turned by less than `stuck_deg` degrees (stuck,
-    Secs. 4.2-4.3), or at max_steps (T = inf)."""
+    Secs. 4.2-4.3), or at max_steps (T = inf), or once its beads are no
+    longer finite (T = nan)."""
     from . import fpd
     W = stuck_window or max(sample_every, max_steps // 5)
     cells = sum(int(c["nx"]) * int(c["ny"]) for c in configs)
@@ -222,6 +223,12 @@ def measure_periods(configs: list[dict], max_steps: int, sample_every: int = 200
         for i in list(live):
             c = configs[i]
             R = b.beads(slots[i])[0]
+            if not np.all(np.isfinite(R)):
+                # diverged (an unstable parameter set): no period
+                res[i] = PeriodResult(float("nan"), float("nan"), tracks[i])
+                live.discard(i)
+                b.remove(slots[i])
+                continue
             tracks[i].add(t, orientation(R, c["n_beads"]),
                           end_to_end_ratio(R, c["n_beads"], 2.0 * c["a"]))
 
@@ -235,6 +242,8 @@ def measure_periods(configs: list[dict], max_steps: int, sample_every: int = 200
         sample(done)
         for i in list(live):
             t, th, _ = tracks[i].arrays()
+            if len(t) == 0:
+                continue
             # orientation is taken modulo pi; align the first sample with theta0
             th = th + math.pi * round((th0[i] - th[0]) / math.pi)
             t1 = _crossing(t, th, th0[i] - math.pi / 2)
