@@ -179,6 +179,55 @@ def readings(precision: int = 1, variants=READINGS) -> dict:
     return dict(study="readings", rows=rows)
 
 
+def sensitivity(checkpoints=(2000, 10000, 50000, 100000, 200000), seed: int = 7) -> dict:
+    """How much the FP64 trajectory of the 1024 x 256 flexible-fiber case
+    (K = 3.3e-5, Re = 10) moves when its initial populations are perturbed
+    by one ulp, by the FP32 unit roundoff (6e-8 of each deviation f - w, random
+    sign) and by the FP16 one (4.9e-4), against the FP32- and FP16-storage runs
+    of the same case: velocity relative L2 and largest bead displacement
+    against the unperturbed FP64 run at each checkpoint.  A trajectory that
+    amplified perturbations would carry the perturbed runs as far as the
+    reduced-precision ones; a stable one keeps them near their start."""
+    from . import fpd, workloads as wl
+    base = wl.single_fiber_medium()
+    rng = np.random.default_rng(seed)
+    w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)[:, None, None]
+
+    def make(prec, pert=None):
+        s = fpd.Simulation(dict(base, precision=prec))
+        if pert is not None:
+            f = s.populations()
+            if pert == "ulp":
+                f2 = np.nextafter(f, np.inf)
+            else:
+                f2 = f + (f - w) * pert * rng.choice([-1.0, 1.0], size=f.shape)
+            s.set_populations(f2)
+        return s
+
+    sims = {"ref": make(0), "ulp": make(0, "ulp"), "fp32_roundoff": make(0, 6e-8),
+            "fp16_roundoff": make(0, 4.9e-4), "fp32_storage": make(1), "fp16_storage": make(2)}
+    rows = []
+    done = 0
+    for c in checkpoints:
+        for sim in sims.values():
+            sim.step(c - done)
+        done = c
+        ux, uy, _ = sims["ref"].fields()
+        ref_u, ref_R = np.stack([ux, uy]), sims["ref"].beads()[0]
+        row = dict(steps=c)
+        for k, sim in sims.items():
+            if k == "ref":
+                continue
+            a, b, _ = sim.fields()
+            R = sim.beads()[0]
+            row[k] = dict(u=float(np.linalg.norm(np.stack([a, b]) - ref_u) / np.linalg.norm(ref_u)),
+                          dR=float(np.abs(R - ref_R).max()))
+        rows.append(row)
+    for sim in sims.values():
+        sim.close()
+    return dict(study="sensitivity", case=base["name"], rows=rows)
+
+
 def hasimoto_drag(a: float, L: float) -> float:
     """F / (eta V) of a square array (period L) of rigid discs of radius a in
     Stokes flow (Hasimoto 1959), to third order in the area fraction c."""
@@ -247,7 +296,8 @@ def internal_flow(a: float = 8.0, precision: int = 1, points=INTERNAL_FLOW, visc
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("study", choices=["resolution", "internal-flow", "readings", "interface"] + sorted(SWEEPS))
+    ap.add_argument("study", choices=["resolution", "internal-flow", "readings", "interface", "sensitivity"]
+                    + sorted(SWEEPS))
     ap.add_argument("--a", type=float, default=2.0, help="bead radius in lattice units")
     ap.add_argument("--precision", type=int, default=1, choices=[0, 1, 2])
     args = ap.parse_args(argv)
@@ -262,6 +312,8 @@ def main(argv=None):
         out = readings(precision=args.precision)
     elif args.study == "interface":
         out = readings(precision=args.precision, variants=INTERFACE)
+    elif args.study == "sensitivity":
+        out = sensitivity()
     elif args.study == "internal-flow":
         out = internal_flow(a=args.a if args.a != 2.0 else 8.0, precision=args.precision)
     else:
