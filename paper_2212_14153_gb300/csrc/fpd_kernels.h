@@ -89,10 +89,10 @@ struct BeadExport {
     int slots = 0;
     int stride = 0;
 };
-// status: per-instance status words (indexed by instance slot), where a
-// bead velocity component of magnitude >= kFastBead or a non-finite one sets
-// kFlagFastBead (and kFlagNonFinite), after which every tile of the
-// instance is marked in mask_write; NULL: not checked.
+// status: per-instance status words (indexed by instance slot), where the
+// instance's last CTA sets kFlagFastBead (and kFlagNonFinite) when a bead
+// velocity component reaches kFastBead in magnitude (or is not finite), and
+// marks every tile of a flagged instance in mask_write; NULL: not checked.
 cudaError_t launch_beads(int precision, const Inst *inst_d, const int2 *blist, int nb_total,
                          const void *pool, BeadTab tab0, BeadTab tab1, unsigned *mask_write, int gparity,
                          int advance, unsigned *counters, int pdl, cudaStream_t st, BeadExport ex = BeadExport{},
