@@ -179,15 +179,17 @@ int fpd_flags(fpd_sim *s, uint32_t *flags);
 
 /* Copy the macroscopic fields to caller-owned host arrays of ny*nx doubles
  * (row-major [j][i], cell centre (i + 1/2, j + 1/2)): velocity
- * u = (sum_k f_k c_k + f/2) / rho with f the force density of the current
- * bead table (the one used by the last collision), and rho = sum_k f_k.
+ * u = (sum_k f_k c_k + f/2) / rho with f the force density of Eq. 4 for the
+ * current bead table (the one used by the last collision; the velocity that
+ * Eq. 5 averages), and rho = sum_k f_k.
  * Any pointer may be NULL.  Synchronises. */
 int fpd_read_fields(fpd_sim *s, double *ux, double *uy, double *rho);
 
 /* Copy the bead table to caller-owned host arrays of n_fibers*n_beads
  * entries (fiber-major): positions and velocities (x, y pairs) of the last
- * advance (V = 0 before the first), forces F_i (Eqs. 11-12 + excluded
- * volume, x, y pairs) and support integrals S_i = sum_x phi_i (one double
+ * advance (V of Eq. 5; V = 0 before the first), forces F_i (Eqs. 11-12 +
+ * excluded volume, x, y pairs) and support integrals S_i = sum_x phi_i,
+ * the lattice form of the integral of phi_i in Eqs. 4-5 (one double
  * each).  Positions are unwrapped in x.  Any pointer may be NULL.
  * Synchronises. */
 int fpd_read_beads(fpd_sim *s, double *pos, double *vel, double *force, double *support);

@@ -55,7 +55,9 @@ def run_both(cfg, steps):
 def compare_f64(g, o, tol=1e-12, tol_f=1e-9):
     """Velocity and bead positions/velocities/forces/support sums within
     tol (relative L2).  Floors keep round-off-sized references from turning
-    into large relative numbers: velocity 1e-6 per cell, force 1e-9.  The
+    into large relative numbers: the velocity norm is taken as at least that
+    of 1e-4 in every component of every cell (1e-4 sqrt(2 ncell)), forces
+    against the physical scale below.  The
     population deviations f - w are compared at tol_f: the oracle stores
     plain f (|f| <= 0.45, ulp 5.6e-17), so its own rounding floor relative
     to |f - w| ~ 1e-4 is ~1e-12 per step before any difference in the GPU
