@@ -114,6 +114,7 @@ class Server:
         t0 = clock()
         i = 0
         cell_updates = 0.0
+        peak = 0  # most requests resident at once
         while i < len(pending) or queue or running:
             now = clock() - t0
             while i < len(pending) and pending[i].arrival_s <= now:
@@ -140,6 +141,7 @@ class Server:
                 if i < len(pending):
                     time.sleep(max(0.0, min(0.01, pending[i].arrival_s - (clock() - t0))))
                 continue
+            peak = max(peak, len(running))
             cells = sum(r.cfg["nx"] * r.cfg["ny"] for r in running.values())
             steps = self.batch.run(self.chunk)
             cell_updates += cells * steps
@@ -159,4 +161,5 @@ class Server:
             "mean_s": float(lat.mean()),
             "aggregate_mlups": cell_updates / wall / 1e6,
             "cell_updates": cell_updates,
+            "peak_resident": peak,
         }

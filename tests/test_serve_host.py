@@ -88,7 +88,8 @@ def test_all_requests_complete_with_positive_latency(fake):
 def test_slot_limit_and_fifo_admission(fake):
     srv = serve.Server(max_slots=2, cap_bytes=1 << 30, chunk=50)
     reqs = [_req(i, 32, 32, 100, 0.0) for i in range(5)]
-    srv.serve(reqs, clock=FakeClock())
+    res = srv.serve(reqs, clock=FakeClock())
+    assert res["peak_resident"] == 2
     order = [rid for kind, rid, s in srv.batch.log if kind == "add"]
     assert order == [0, 1, 2, 3, 4]                     # first come, first served
     adm = sorted(reqs, key=lambda r: r.admitted_s)
@@ -99,7 +100,8 @@ def test_memory_cap_limits_residency(fake):
     one = serve.state_bytes(dict(nx=128, ny=64), 1)
     srv = serve.Server(max_slots=16, cap_bytes=2 * one + 10, chunk=50)
     reqs = [_req(i, 128, 64, 100, 0.0) for i in range(4)]
-    srv.serve(reqs, clock=FakeClock())
+    res = srv.serve(reqs, clock=FakeClock())
+    assert res["peak_resident"] == 2 and res["completed"] == 4
     # at most two resident at any time: the third admission follows a retirement
     adm = sorted(reqs, key=lambda r: r.admitted_s)
     assert adm[2].admitted_s >= min(r.done_s for r in adm[:2])
