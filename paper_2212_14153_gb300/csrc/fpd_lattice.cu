@@ -171,8 +171,9 @@ __device__ __forceinline__ bool tile_cold_early(const unsigned *__restrict__ pre
 // (x0 + tx + k kTileX / CY, y0 + ty) of its row, whose elements in every
 // plane lie a constant distance apart, so that one address serves all of
 // them (immediate offsets).  kInner: tiles away from walls and periodic
-// edges use the precomputed pull offsets.
-template <class S, int CY, bool kInner, bool kAlongX, int kColl>
+// edges use the precomputed pull offsets.  kStream: the population loads
+// and stores carry the L2 evict-first priority (the single-lattice sweep).
+template <class S, int CY, bool kInner, bool kAlongX, int kColl, bool kStream = false>
 __device__ __forceinline__ void lattice_tile(const Inst &I, S *__restrict__ pool, const BeadTab &tab,
                                              const unsigned *__restrict__ mask_read,
                                              const unsigned *__restrict__ mask_prev, unsigned *__restrict__ mask_clear,
@@ -203,11 +204,11 @@ __device__ __forceinline__ void lattice_tile(const Inst &I, S *__restrict__ pool
         if (inner) {
             const S *p = Asrc + (y[0] * I.pitch + x);
 #pragma unroll
-            for (int k = 0; k < CY; ++k) pull_inner<S, R, true>(p + (k * RY * I.pitch + k * RX), I, g[k]);
+            for (int k = 0; k < CY; ++k) pull_inner<S, R, true, kStream>(p + (k * RY * I.pitch + k * RX), I, g[k]);
         } else {
 #pragma unroll
             for (int k = 0; k < CY; ++k)
-                if (valid[k]) pull_pops<S, R, true>(Asrc, I, kInner ? make_cell(I, x + k * RX, y[k]) : C[k], g[k]);
+                if (valid[k]) pull_pops<S, R, true, kStream>(Asrc, I, kInner ? make_cell(I, x + k * RX, y[k]) : C[k], g[k]);
         }
     };
     // populations come from the previous sweep; when the bead phase runs
@@ -231,7 +232,7 @@ __device__ __forceinline__ void lattice_tile(const Inst &I, S *__restrict__ pool
         R Fx, Fy, s_nu, s_e, s_eps, s_q;
         cell_overlay<R>(I, tab, m, W, any, x + k * RX, y[k], Fx, Fy, s_nu, s_e, s_eps, s_q);
         collide_cell<S, R, kColl>(I, g[k], Fx, Fy, s_nu, s_e, s_eps, s_q, forced);
-        put_at<S, R, true>(Adst + (kInner ? y[k] * I.pitch + x + k * RX : C[k].r0 + C[k].x), I, g[k]);
+        put_at<S, R, true, kStream>(Adst + (kInner ? y[k] * I.pitch + x + k * RX : C[k].r0 + C[k].x), I, g[k]);
     }
 }
 
@@ -250,7 +251,7 @@ __global__ void __launch_bounds__(kTileX *kTileY / CY)
     k_lattice(const Inst I, S *__restrict__ pool, const BeadTab tab, const unsigned *__restrict__ mask_read,
               const unsigned *__restrict__ mask_prev, unsigned *__restrict__ mask_clear, const int parity,
               const int early_load, const int early_cold) {
-    lattice_tile<S, CY, true, kAlongX, kColl>(I, pool, tab, mask_read, mask_prev, mask_clear,
+    lattice_tile<S, CY, true, kAlongX, kColl, true>(I, pool, tab, mask_read, mask_prev, mask_clear,
                                        tile_order(blockIdx.x, gridDim.x, parity),
                                        tile_order(blockIdx.y, gridDim.y, parity), parity, early_load, early_cold,
                                        (blockIdx.x | blockIdx.y) == 0, threadIdx.x, threadIdx.y);
