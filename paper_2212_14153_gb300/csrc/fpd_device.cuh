@@ -129,8 +129,8 @@ template <> struct Store<double> {
     static __device__ __forceinline__ double ld_raw(const double *p) { return *p; }
     static __device__ __forceinline__ void st_raw(double *p, double v) { *p = v; }
     // the FP64 path keeps plain accesses
-    static __device__ __forceinline__ double ld_stream(const double *p) { return *p; }
-    static __device__ __forceinline__ void st_stream(double *p, double v) { *p = v; }
+    static __device__ __forceinline__ double ld_stream(const double *p, uint64_t) { return *p; }
+    static __device__ __forceinline__ void st_stream(double *p, double v, uint64_t) { *p = v; }
 };
 // L2 eviction priority of the population stream of a single-lattice sweep
 // (createpolicy, applied per access through .L2::cache_hint).  Each element
@@ -152,13 +152,13 @@ template <> struct Store<float> {
     static __device__ __forceinline__ void st_raw(float *p, float v) { *p = v; }
     // population stream of a sweep: read-only during the sweep (the other
     // buffer takes the writes), both marked first to leave L2
-    static __device__ __forceinline__ float ld_stream(const float *p) {
+    static __device__ __forceinline__ float ld_stream(const float *p, uint64_t pol) {
         float v;
-        asm volatile("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol_evict_first()));
+        asm volatile("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
         return v;
     }
-    static __device__ __forceinline__ void st_stream(float *p, float v) {
-        asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(v), "l"(pol_evict_first()) : "memory");
+    static __device__ __forceinline__ void st_stream(float *p, float v, uint64_t pol) {
+        asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(v), "l"(pol) : "memory");
     }
 };
 template <> struct Store<__half> {
@@ -171,14 +171,14 @@ template <> struct Store<__half> {
     }
     static __device__ __forceinline__ float ld_raw(const __half *p) { return __half2float(*p); }
     static __device__ __forceinline__ void st_raw(__half *p, float v) { *p = __float2half_rn(v); }
-    static __device__ __forceinline__ float ld_stream(const __half *p) {
+    static __device__ __forceinline__ float ld_stream(const __half *p, uint64_t pol) {
         unsigned short h;
-        asm volatile("ld.global.nc.L2::cache_hint.b16 %0, [%1], %2;" : "=h"(h) : "l"(p), "l"(pol_evict_first()));
+        asm volatile("ld.global.nc.L2::cache_hint.b16 %0, [%1], %2;" : "=h"(h) : "l"(p), "l"(pol));
         return __half2float(__ushort_as_half(h));
     }
-    static __device__ __forceinline__ void st_stream(__half *p, float v) {
+    static __device__ __forceinline__ void st_stream(__half *p, float v, uint64_t pol) {
         asm volatile("st.global.L2::cache_hint.b16 [%0], %1, %2;" ::"l"(p), "h"(__half_as_ushort(__float2half_rn(v))),
-                     "l"(pol_evict_first())
+                     "l"(pol)
                      : "memory");
     }
 };
@@ -225,20 +225,20 @@ __device__ __forceinline__ Cell make_cell(const Inst &I, int x, int y) {
 // g_k(x) from the current buffer A (kRaw: in stored units, sigma_k g_k;
 // kStream: with the sweep's L2 eviction priority, raw only).
 template <int k, class S, class R, bool kRaw = false, bool kStream = false>
-__device__ __forceinline__ void pull_one(const S *__restrict__ A, const Inst &I, const Cell &C, R &g) {
+__device__ __forceinline__ void pull_one(const S *__restrict__ A, const Inst &I, const Cell &C, R &g, uint64_t pol = 0) {
     constexpr int cx = Q<k>::cx, cy = Q<k>::cy, o = Q<k>::opp;
     // source cell x - c_k; beyond a wall when it is row -1 or row ny
     const bool wall = (cy > 0 && C.bot) || (cy < 0 && C.top);
     if (wall) {
         const S *p = A + (o * I.plane32 + C.r0 + C.x);
-        if constexpr (kRaw && kStream) g = (R)Store<S>::ld_stream(p) + bb_stored<R>(I, cy > 0 ? 0 : 1, k);
+        if constexpr (kRaw && kStream) g = (R)Store<S>::ld_stream(p, pol) + bb_stored<R>(I, cy > 0 ? 0 : 1, k);
         else if constexpr (kRaw) g = (R)Store<S>::ld_raw(p) + bb_stored<R>(I, cy > 0 ? 0 : 1, k);
         else g = (R)Store<S>::ld(p, I.inv_scale[o]) + bb_term<R>(I, cy > 0 ? 0 : 1, k);
     } else {
         const int rs = cy > 0 ? C.rm : (cy < 0 ? C.rp : C.r0);
         const int xs = cx > 0 ? C.xm : (cx < 0 ? C.xp : C.x);
         const S *p = A + (k * I.plane32 + rs + xs);
-        if constexpr (kRaw && kStream) g = (R)Store<S>::ld_stream(p);
+        if constexpr (kRaw && kStream) g = (R)Store<S>::ld_stream(p, pol);
         else if constexpr (kRaw) g = (R)Store<S>::ld_raw(p);
         else g = (R)Store<S>::ld(p, I.inv_scale[k]);
     }
@@ -260,25 +260,25 @@ __device__ __forceinline__ void place_one(S *__restrict__ A, const Inst &I, cons
 }
 
 template <class S, class R, bool kRaw = false, bool kStream = false>
-__device__ __forceinline__ void pull_pops(const S *__restrict__ A, const Inst &I, const Cell &C, R g[9]) {
-    pull_one<0, S, R, kRaw, kStream>(A, I, C, g[0]);
-    pull_one<1, S, R, kRaw, kStream>(A, I, C, g[1]);
-    pull_one<2, S, R, kRaw, kStream>(A, I, C, g[2]);
-    pull_one<3, S, R, kRaw, kStream>(A, I, C, g[3]);
-    pull_one<4, S, R, kRaw, kStream>(A, I, C, g[4]);
-    pull_one<5, S, R, kRaw, kStream>(A, I, C, g[5]);
-    pull_one<6, S, R, kRaw, kStream>(A, I, C, g[6]);
-    pull_one<7, S, R, kRaw, kStream>(A, I, C, g[7]);
-    pull_one<8, S, R, kRaw, kStream>(A, I, C, g[8]);
+__device__ __forceinline__ void pull_pops(const S *__restrict__ A, const Inst &I, const Cell &C, R g[9], uint64_t pol = 0) {
+    pull_one<0, S, R, kRaw, kStream>(A, I, C, g[0], pol);
+    pull_one<1, S, R, kRaw, kStream>(A, I, C, g[1], pol);
+    pull_one<2, S, R, kRaw, kStream>(A, I, C, g[2], pol);
+    pull_one<3, S, R, kRaw, kStream>(A, I, C, g[3], pol);
+    pull_one<4, S, R, kRaw, kStream>(A, I, C, g[4], pol);
+    pull_one<5, S, R, kRaw, kStream>(A, I, C, g[5], pol);
+    pull_one<6, S, R, kRaw, kStream>(A, I, C, g[6], pol);
+    pull_one<7, S, R, kRaw, kStream>(A, I, C, g[7], pol);
+    pull_one<8, S, R, kRaw, kStream>(A, I, C, g[8], pol);
 }
 
 // Pull of all nine directions for a cell with no wall and no periodic wrap
 // among its neighbours; p points at the cell's element in plane 0.
 template <class S, class R, bool kRaw = false, bool kStream = false>
-__device__ __forceinline__ void pull_inner(const S *__restrict__ p, const Inst &I, R g[9]) {
+__device__ __forceinline__ void pull_inner(const S *__restrict__ p, const Inst &I, R g[9], uint64_t pol = 0) {
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
-        if constexpr (kRaw && kStream) g[k] = (R)Store<S>::ld_stream(p + I.pull_off[k]);
+        if constexpr (kRaw && kStream) g[k] = (R)Store<S>::ld_stream(p + I.pull_off[k], pol);
         else if constexpr (kRaw) g[k] = (R)Store<S>::ld_raw(p + I.pull_off[k]);
         else g[k] = (R)Store<S>::ld(p + I.pull_off[k], I.inv_scale[k]);
     }
@@ -286,10 +286,10 @@ __device__ __forceinline__ void pull_inner(const S *__restrict__ p, const Inst &
 
 // Post-collision populations stored at the cell whose plane-0 element p is.
 template <class S, class R, bool kRaw = false, bool kStream = false>
-__device__ __forceinline__ void put_at(S *__restrict__ p, const Inst &I, const R g[9]) {
+__device__ __forceinline__ void put_at(S *__restrict__ p, const Inst &I, const R g[9], uint64_t pol = 0) {
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
-        if constexpr (kRaw && kStream) Store<S>::st_stream(p + k * I.plane32, g[k]);
+        if constexpr (kRaw && kStream) Store<S>::st_stream(p + k * I.plane32, g[k], pol);
         else if constexpr (kRaw) Store<S>::st_raw(p + k * I.plane32, g[k]);
         else Store<S>::st(p + k * I.plane32, g[k], I.scale[k]);
     }

@@ -199,16 +199,19 @@ __device__ __forceinline__ void lattice_tile(const Inst &I, S *__restrict__ pool
         valid[k] = x + k * RX < I.nx && y[k] < I.ny;
         if constexpr (!kInner) C[k] = make_cell(I, x + k * RX, valid[k] ? y[k] : 0);
     }
+    // the population stream's L2 priority, made once per thread
+    uint64_t pol = 0;
+    if constexpr (kStream) pol = pol_evict_first();
     // populations in stored units (sigma_k g_k)
     auto pull = [&]() {
         if (inner) {
             const S *p = Asrc + (y[0] * I.pitch + x);
 #pragma unroll
-            for (int k = 0; k < CY; ++k) pull_inner<S, R, true, kStream>(p + (k * RY * I.pitch + k * RX), I, g[k]);
+            for (int k = 0; k < CY; ++k) pull_inner<S, R, true, kStream>(p + (k * RY * I.pitch + k * RX), I, g[k], pol);
         } else {
 #pragma unroll
             for (int k = 0; k < CY; ++k)
-                if (valid[k]) pull_pops<S, R, true, kStream>(Asrc, I, kInner ? make_cell(I, x + k * RX, y[k]) : C[k], g[k]);
+                if (valid[k]) pull_pops<S, R, true, kStream>(Asrc, I, kInner ? make_cell(I, x + k * RX, y[k]) : C[k], g[k], pol);
         }
     };
     // populations come from the previous sweep; when the bead phase runs
@@ -232,7 +235,7 @@ __device__ __forceinline__ void lattice_tile(const Inst &I, S *__restrict__ pool
         R Fx, Fy, s_nu, s_e, s_eps, s_q;
         cell_overlay<R>(I, tab, m, W, any, x + k * RX, y[k], Fx, Fy, s_nu, s_e, s_eps, s_q);
         collide_cell<S, R, kColl>(I, g[k], Fx, Fy, s_nu, s_e, s_eps, s_q, forced);
-        put_at<S, R, true, kStream>(Adst + (kInner ? y[k] * I.pitch + x + k * RX : C[k].r0 + C[k].x), I, g[k]);
+        put_at<S, R, true, kStream>(Adst + (kInner ? y[k] * I.pitch + x + k * RX : C[k].r0 + C[k].x), I, g[k], pol);
     }
 }
 
