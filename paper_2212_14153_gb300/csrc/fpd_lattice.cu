@@ -29,10 +29,48 @@ template <> struct Real<double> { using type = double; };
 
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 
+// A tile with beads marked in its mask (the same for every thread of the
+// CTA, so all of them call this): the FP32 overlay entries of those beads
+// (x hi + lo, y hi + lo, G = F / S) are staged in shared memory, indexed by
+// the bead's place in its instance, in one round of loads.  Each cell's loop
+// over the marked beads then reads shared memory instead of waiting on a
+// memory round trip per bead, which under the sweep's load made the marked
+// tiles the last to finish a step (13 us after the bead phase released them,
+// FP32).  kStaged: the single-lattice sweeps; the batched sweep (held to 32
+// registers) and the FP64 path read the tables, with the same values in the
+// same order, so every launch shape still gives the same bits.
+template <class R, bool kStaged>
+__device__ __forceinline__ const float *stage_overlay(const Inst &I, const BeadTab &tab,
+                                                      const unsigned *__restrict__ m, const unsigned any) {
+    if constexpr (std::is_same<R, double>::value || !kStaged) {
+        return nullptr;
+    } else {
+        __shared__ float s_ov[kTabFloats * kMaxBeads];
+        if (any != 0u) {
+            const int nt = blockDim.x * blockDim.y, t = threadIdx.y * blockDim.x + threadIdx.x;
+            for (int q = t; q < I.nb; q += nt)
+                if ((m[q >> 5] >> (q & 31)) & 1u) {
+                    const int gq = I.bead_off + q;
+                    s_ov[q] = tab.xh[gq];
+                    s_ov[kMaxBeads + q] = tab.xl[gq];
+                    s_ov[2 * kMaxBeads + q] = tab.yh[gq];
+                    s_ov[3 * kMaxBeads + q] = tab.yl[gq];
+                    s_ov[4 * kMaxBeads + q] = tab.gxf[gq];
+                    s_ov[5 * kMaxBeads + q] = tab.gyf[gq];
+                }
+            __syncthreads();
+        }
+        return s_ov;
+    }
+}
+
 // Relaxation rates and force density of one cell (Eqs. 1, 2, 4) from the
 // beads marked in its tile's mask (m, W words; any = OR of the words).
-template <class R>
-__device__ __forceinline__ void cell_overlay(const Inst &I, const BeadTab &tab, const unsigned *__restrict__ m,
+// kStaged: the FP32 overlay entries are read from sov (stage_overlay), else
+// from the table; the values and their order are the same either way.
+template <class R, bool kStaged>
+__device__ __forceinline__ void cell_overlay(const Inst &I, const BeadTab &tab, const float *__restrict__ sov,
+                                             const unsigned *__restrict__ m,
                                              const int W, const unsigned any, const int x, const int y, R &Fx,
                                              R &Fy, R &s_nu, R &s_e, R &s_eps, R &s_q) {
     if constexpr (std::is_same<R, double>::value) {
@@ -79,26 +117,32 @@ __device__ __forceinline__ void cell_overlay(const Inst &I, const BeadTab &tab, 
         for (int w = 0; w < W && any; ++w) {
             unsigned bits = m[w];
             while (bits) {
-                const int q = I.bead_off + 32 * w + __ffs(bits) - 1;
+                const int q = 32 * w + __ffs(bits) - 1;  // place in the instance
                 bits &= bits - 1u;
+                // entry j of bead q: staged, or from the table
+                auto ov = [&](int j) -> float {
+                    if constexpr (kStaged) return sov[j * kMaxBeads + q];
+                    const float *col[kTabFloats] = {tab.xh, tab.xl, tab.yh, tab.yl, tab.gxf, tab.gyf};
+                    return col[j][I.bead_off + q];
+                };
                 // (x_c - R_x) with R_x = hi + lo; the periodic shift is
                 // applied to the cell centre first so that xc - hi is exact
-                const float bx = tab.xh[q];
+                const float bx = ov(0);
                 float xcl = xc;
                 const float d0 = xcl - bx;
                 xcl = (d0 > hnx) ? xcl - fnx : ((d0 < -hnx) ? xcl + fnx : xcl);
-                const float dx = (xcl - bx) - tab.xl[q];
-                const float by_ = tab.yh[q];
+                const float dx = (xcl - bx) - ov(1);
+                const float by_ = ov(2);
                 float ycl = yc;
                 if (I.periodic_y) {
                     const float e0 = ycl - by_;
                     ycl = (e0 > hny) ? ycl - fny : ((e0 < -hny) ? ycl + fny : ycl);
                 }
-                const float dy = (ycl - by_) - tab.yl[q];
+                const float dy = (ycl - by_) - ov(3);
                 const float ph = phi_f32(dx, dy, I.f_a, I.f_inv_xi, I.f_rcut2);
                 Phi += ph;
-                Fx += ph * tab.gxf[q];
-                Fy += ph * tab.gyf[q];
+                Fx += ph * ov(4);
+                Fy += ph * ov(5);
             }
         }
         const float nu = I.f_nu_f * (1.0f + I.f_visc_m1 * Phi);
@@ -222,18 +266,19 @@ __device__ __forceinline__ void lattice_tile(const Inst &I, S *__restrict__ pool
     pdl_trigger();
     if (tx == 0 && ty == 0)  // a mask of two steps back, for the next bead phase
         for (int w = 0; w < W; ++w) mask_clear[tile * W + w] = 0u;
-    if (!valid[0]) return;  // the thread's other cells (further along its column or row) are invalid too
-    if (!early_load) pull();
     const unsigned *m = mask_read + tile * W;
     unsigned any = 0u;
     if (!cold)
         for (int w = 0; w < W; ++w) any |= m[w];
+    const float *sov = stage_overlay<R, kStream>(I, tab, m, any);  // every thread of the CTA
+    if (!valid[0]) return;  // the thread's other cells (further along its column or row) are invalid too
+    if (!early_load) pull();
     const bool forced = any != 0u || body_forced<R>(I);
 #pragma unroll
     for (int k = 0; k < CY; ++k) {
         if (!valid[k]) continue;
         R Fx, Fy, s_nu, s_e, s_eps, s_q;
-        cell_overlay<R>(I, tab, m, W, any, x + k * RX, y[k], Fx, Fy, s_nu, s_e, s_eps, s_q);
+        cell_overlay<R, kStream>(I, tab, sov, m, W, any, x + k * RX, y[k], Fx, Fy, s_nu, s_e, s_eps, s_q);
         collide_cell<S, R, kColl>(I, g[k], Fx, Fy, s_nu, s_e, s_eps, s_q, forced);
         put_at<S, R, true, kStream>(Adst + (kInner ? y[k] * I.pitch + x + k * RX : C[k].r0 + C[k].x), I, g[k], pol);
     }
@@ -475,16 +520,17 @@ __device__ __forceinline__ void lattice_tile_vec(const Inst &I, S *__restrict__ 
     if (threadIdx.x == 0 && threadIdx.y == 0)
         for (int w = 0; w < W; ++w) mask_clear[tile * W + w] = 0u;
     if (!early_load) vload_pops<S, NV>(Asrc, I, C, g);
+    const unsigned *m = mask_read + tile * W;
+    unsigned any = 0u;
+    if (!cold)
+        for (int w = 0; w < W; ++w) any |= m[w];
+    const float *sov = stage_overlay<R, true>(I, tab, m, any);  // every thread of the CTA
     if (C.valid) {
-        const unsigned *m = mask_read + tile * W;
-        unsigned any = 0u;
-        if (!cold)
-            for (int w = 0; w < W; ++w) any |= m[w];
         const bool forced = any != 0u || body_forced<R>(I);
 #pragma unroll
         for (int j = 0; j < NV; ++j) {
             R Fx, Fy, s_nu, s_e, s_eps, s_q;
-            cell_overlay<R>(I, tab, m, W, any, x0 + j, y, Fx, Fy, s_nu, s_e, s_eps, s_q);
+            cell_overlay<R, true>(I, tab, sov, m, W, any, x0 + j, y, Fx, Fy, s_nu, s_e, s_eps, s_q);
             collide_cell<S, R, kCollTrt>(I, g[j], Fx, Fy, s_nu, s_e, s_eps, s_q, forced);
         }
     }
