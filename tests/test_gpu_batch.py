@@ -71,6 +71,24 @@ def test_batch_equals_alone_bit_for_bit(fpd, precision):
 
 
 @pytest.mark.parametrize("precision", [0, 1, 2])
+def test_fiber_across_the_periodic_edge_and_near_a_wall_batch_equals_alone(fpd, precision):
+    # marked tiles that wrap across x = 0 and touch the bottom wall, on a
+    # lattice with ragged tiles in x and y: a lone run stages those tiles'
+    # bead entries in shared memory, the batch reads them from the table;
+    # the same bits either way
+    rng = np.random.default_rng(90 + precision)
+    cfg = wl.random_fiber(rng, 70, 37, n_beads=5, a=2.0, xi=1.0, n_fibers=2, precision=precision,
+                          centres=[[1.5, 8.0], [68.0, 28.5]], theta0=[0.3, 2.6])
+    b = fpd.Batch(precision, max_slots=2, pool_bytes=16 << 20, max_beads=64)
+    s = b.add(cfg, 57)
+    while b.run(1000):
+        pass
+    assert b.poll() == [s]
+    _same((b.populations(s), b.beads(s)), _alone(fpd, cfg, 57))
+    b.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2])
 def test_batch_longer_than_the_sms_equals_alone(fpd, precision):
     # a bead list longer than the GPU's SM count runs in narrower bead CTAs
     # than an instance alone; the per-bead sums are taken over the same
