@@ -382,6 +382,21 @@ int fpd_batch_slot_flags(fpd_batch *b, int32_t slot, uint32_t *flags);
  * (running or finished).  Synchronise. */
 int fpd_batch_read_fields(fpd_batch *b, int32_t slot, double *ux, double *uy, double *rho);
 int fpd_batch_read_beads(fpd_batch *b, int32_t slot, double *pos, double *vel, double *force, double *support);
+
+/* Advance every active instance by up to n steps (n >= 0): fpd_batch_run
+ * repeated until n steps are done or no instance is active any more (a run
+ * stops where an instance reaches its requested count, which then finishes).
+ * Each step is the coupled step of Sec. 2.3 for every instance; the batch as
+ * a whole is the sweep over independent problems of Sec. 4 (Fig. 10).
+ * FPD_EINVAL for n < 0; launch errors as fpd_batch_run. */
+int fpd_batch_step(fpd_batch *b, int64_t n);
+
+/* Velocity field (ux, uy: ny*nx doubles, row-major, as fpd_read_fields:
+ * the velocity of Eq. 5) and bead positions (pos: n_fibers*n_beads x, y
+ * pairs, unwrapped in x) of one slot, running or finished, into
+ * caller-owned host arrays; any pointer may be NULL.  Synchronises.
+ * FPD_EINVAL for a slot that holds no instance. */
+int fpd_batch_read(fpd_batch *b, int32_t slot, double *ux, double *uy, double *pos);
 int fpd_batch_read_populations(fpd_batch *b, int32_t slot, double *f);
 /* As fpd_internal_flow for one slot (running or finished).  Synchronises. */
 int fpd_batch_internal_flow(fpd_batch *b, int32_t slot, double *eps);

@@ -744,4 +744,30 @@ int fpd_batch_destroy(fpd_batch *b) {
     return FPD_OK;
 }
 
+// Up to n steps of every active instance: fpd_batch_run repeated until n
+// steps are done or no instance is active (each run stops where an instance
+// reaches its requested count).
+int fpd_batch_step(fpd_batch *b, int64_t n) {
+    if (!b) return FPD_EINVAL;
+    if (n < 0) return bfail(b, FPD_EINVAL, "n must be >= 0");
+    for (int64_t done = 0; done < n;) {
+        int64_t d = 0;
+        const int rc = fpd_batch_run(b, n - done, &d);
+        if (rc != FPD_OK) return rc;
+        if (d == 0) break;
+        done += d;
+    }
+    return FPD_OK;
+}
+
+// Velocity field and bead positions of one instance (any pointer may be
+// NULL): fpd_batch_read_fields and fpd_batch_read_beads in one call.
+int fpd_batch_read(fpd_batch *b, int32_t slot, double *ux, double *uy, double *pos) {
+    if (!b) return FPD_EINVAL;
+    int rc = FPD_OK;
+    if ((ux || uy) && (rc = fpd_batch_read_fields(b, slot, ux, uy, nullptr)) != FPD_OK) return rc;
+    if (pos && (rc = fpd_batch_read_beads(b, slot, pos, nullptr, nullptr, nullptr)) != FPD_OK) return rc;
+    return FPD_OK;
+}
+
 }  // extern "C"

@@ -104,6 +104,8 @@ SIGNATURES = {
     "fpd_batch_slot_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64)]),
     "fpd_batch_read_fields": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, _DP, _DP, _DP]),
     "fpd_batch_read_beads": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, _DP, _DP, _DP, _DP]),
+    "fpd_batch_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
+    "fpd_batch_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, _DP, _DP, _DP]),
     "fpd_batch_read_populations": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, _DP]),
     "fpd_batch_remove": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "fpd_batch_stats": (ctypes.c_int, [ctypes.c_void_p, _DP]),
@@ -545,6 +547,14 @@ def fpd_batch_read_beads(b, slot: int, pos, vel, force, support=None) -> None:
     _bcheck(load_library().fpd_batch_read_beads(b, int(slot), _ptr(pos), _ptr(vel), _ptr(force), _ptr(support)), b)
 
 
+def fpd_batch_step(b, n: int) -> None:
+    _bcheck(load_library().fpd_batch_step(b, int(n)), b)
+
+
+def fpd_batch_read(b, slot: int, ux, uy, pos) -> None:
+    _bcheck(load_library().fpd_batch_read(b, int(slot), _ptr(ux), _ptr(uy), _ptr(pos)), b)
+
+
 def fpd_batch_read_populations(b, slot: int, f) -> None:
     _bcheck(load_library().fpd_batch_read_populations(b, int(slot), _ptr(f)), b)
 
@@ -599,6 +609,18 @@ class Batch:
 
     def run(self, max_steps: int) -> int:
         return fpd_batch_run(self.h, max_steps)
+
+    def step(self, n: int):
+        """Up to n steps of every active instance (fpd_batch_step)."""
+        fpd_batch_step(self.h, n)
+
+    def read(self, slot: int):
+        """Velocity field and bead positions of a slot (fpd_batch_read)."""
+        i = self.info(slot)
+        ux = np.zeros((i["ny"], i["nx"])); uy = np.zeros_like(ux)
+        R = np.zeros((max(i["beads"], 1), 2))
+        fpd_batch_read(self.h, slot, ux, uy, R)
+        return ux, uy, R[:i["beads"]]
 
     def sync(self):
         fpd_batch_sync(self.h)

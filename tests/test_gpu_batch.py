@@ -88,6 +88,32 @@ def test_fiber_across_the_periodic_edge_and_near_a_wall_batch_equals_alone(fpd, 
     b.close()
 
 
+@pytest.mark.parametrize("precision", [1])
+def test_batch_step_and_read_match_run_and_the_split_reads(fpd, precision):
+    # fpd_batch_step(n) = fpd_batch_run repeated up to n steps; it stops when
+    # every instance has finished; fpd_batch_read = the field and bead reads
+    cases = _cases(precision)[:2]
+    a = fpd.Batch(precision, max_slots=4, pool_bytes=32 << 20, max_beads=64)
+    b = fpd.Batch(precision, max_slots=4, pool_bytes=32 << 20, max_beads=64)
+    sa = [a.add(c, n) for c, n in zip(cases, (23, 40))]
+    sb = [b.add(c, n) for c, n in zip(cases, (23, 40))]
+    a.step(30)
+    assert a.info(sa[0])["steps_done"] == 23 and a.info(sa[1])["steps_done"] == 30
+    a.step(1000)  # stops at 40: nothing is active any more
+    while b.run(1000):
+        pass
+    for x, y in zip(sa, sb):
+        assert a.info(x)["steps_done"] == b.info(y)["steps_done"]
+        ux, uy, R = a.read(x)
+        fx, fy, _ = b.fields(y)
+        assert np.array_equal(ux, fx) and np.array_equal(uy, fy)
+        assert np.array_equal(R, b.beads(y)[0])
+    with pytest.raises(fpd.FpdError):
+        a.step(-1)
+    a.close()
+    b.close()
+
+
 @pytest.mark.parametrize("precision", [0, 1, 2])
 def test_batch_longer_than_the_sms_equals_alone(fpd, precision):
     # a bead list longer than the GPU's SM count runs in narrower bead CTAs
