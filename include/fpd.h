@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define FPD_ABI_VERSION 3
+#define FPD_ABI_VERSION 4
 
 typedef enum {
     FPD_OK = 0,

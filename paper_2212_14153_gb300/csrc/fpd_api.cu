@@ -91,18 +91,14 @@ int derive(fpd_sim *s, const fpd_params &p) {
     std::memset(&I, 0, sizeof I);
     I.nx = p.nx;
     I.ny = p.ny;
-    const size_t es = elem_size(p.precision);
-    const int align = (int)(128 / es);  // rows start on 128-byte boundaries
-    I.pitch = (p.nx + align - 1) / align * align;
+    // populations in strips of kStripW columns (fpd_device.cuh): the width is
+    // padded to whole strips
+    I.pitch = (p.nx + fpd::kStripW - 1) / fpd::kStripW * fpd::kStripW;
     I.precision = p.precision;
     I.plane = (int64_t)I.pitch * p.ny;
     if (9 * I.plane > (int64_t)INT32_MAX)
         return fail(nullptr, FPD_EINVAL, "lattice of %d x %d cells exceeds 32-bit element offsets", p.nx, p.ny);
-    I.plane32 = (int32_t)I.plane;
-    {
-        static const int cx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1}, cy[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
-        for (int k = 0; k < 9; ++k) I.pull_off[k] = k * I.plane32 - cy[k] * I.pitch - cx[k];
-    }
+    I.strip = p.ny * fpd::kRowStride;
     I.pop_off = 0;
     I.ntx = (p.nx + fpd::kTileX - 1) / fpd::kTileX;
     I.nty = (p.ny + fpd::kTileY - 1) / fpd::kTileY;

@@ -19,9 +19,22 @@ template <int k> struct Q {
     static constexpr double w = (k == 0) ? 4.0 / 9.0 : (k <= 4) ? 1.0 / 9.0 : 1.0 / 36.0;
 };
 
+// Population layout.  A buffer holds the nine planes of g_k in strips of
+// kStripW columns: strip x / kStripW is one block of ny rows, and each row of
+// a strip holds its kStripW elements of plane 0, then of plane 1, ... plane
+// 8.  Element (x, y, k) sits at
+//   (x / kStripW) strip + y kRowStride + k kPlaneStride + x % kStripW.
+// Plane and row strides are compile-time constants, so the nine planes of a
+// cell and of its y neighbours lie at immediate offsets from one address;
+// only a pull across a strip edge needs the runtime strip length.  A strip is
+// one lattice tile wide, so a tile's cells and their y halo are contiguous.
+constexpr int kStripW = 32;
+constexpr int kPlaneStride = kStripW;
+constexpr int kRowStride = 9 * kStripW;
+
 // Per-instance constants, device resident (an array of them for batches).
 struct Inst {
-    int32_t nx, ny, pitch, precision;
+    int32_t nx, ny, pitch, precision;  // pitch: nx rounded up to whole strips
     int64_t plane;        // elements per direction plane (pitch * ny)
     int64_t pop_off;      // element offset of this instance's planes
     double u_bot, u_top;  // wall speeds
@@ -30,7 +43,7 @@ struct Inst {
     double k_s, k_b, k_ev;
     int32_t collision, n_beads, n_fibers, nb;
     int32_t bead_off;     // offset of this instance's beads in the tables
-    int32_t plane32;      // plane as int: 9 planes of an instance fit in int32
+    int32_t strip;        // elements per strip of kStripW columns: ny kRowStride
     int32_t ntx, nty;     // lattice tiles (kTileX x kTileY cells) in x and y
     int32_t tile_base;    // first tile of this instance in the tile-mask arrays
     int32_t mask_words;   // 32-bit words per tile mask: ceil(nb / 32), >= 1
@@ -61,10 +74,6 @@ struct Inst {
     float f_inv_ny;
     double ext_fx, ext_fy;
     float f_ext_fx, f_ext_fy;
-    // k plane - c_ky pitch - c_kx: element offset of the pull source of
-    // direction k from a cell's own element in plane 0, for cells with no
-    // wall and no periodic wrap among their neighbours
-    int32_t pull_off[9];
     // Stored units (FP16 storage keeps sigma_k g_k, sigma_k = scale[k]; the
     // other precisions sigma = 1): bounce-back terms sigma_k bbf, and per
     // weight class c (rest, axis, diagonal) sigma_c w_c, 4.5 and 3 times
@@ -72,6 +81,10 @@ struct Inst {
     float bbs[2][9];
     float trt_sw[3], trt_k45[3], trt_k3[3];
 };
+
+// Element offset of column x (>= 0) within its row of plane 0.
+static_assert(kStripW == 32, "col_off, strip_left and strip_right shift by 5");
+__device__ __forceinline__ int col_off(const Inst &I, int x) { return (x >> 5) * I.strip + (x & 31); }
 
 // phi(y) of the sandwich layers (Eq. 14) at height y
 __device__ __forceinline__ double sandwich_phi_f64(const Inst &I, double y) {
@@ -184,7 +197,7 @@ template <> struct Store<__half> {
 };
 
 // ------------------------------------------------------ population access
-// Two buffers of 9 planes A[k][y][x] per instance hold deviations g_k =
+// Two buffers of 9 planes per instance (in strips, see kStripW) hold deviations g_k =
 // f_k - w_k.  After t completed steps, buffer t & 1 holds the post-collision
 // populations g*_k(x) of the last step at their own cell (the initial state
 // is placed so that the same pull yields it).  A step pulls
@@ -201,43 +214,59 @@ __device__ __forceinline__ S *pop_buffer(S *pool, const Inst &I, int which) {
     return pool + I.pop_off + (which ? (int64_t)9 * I.plane : (int64_t)0);
 }
 
-// A cell with its periodic x neighbours and the element offsets of its row
-// and the rows above and below (wrapped when y is periodic; the row beyond a
-// wall is never used).
+// A cell as the element offset of its own element in plane 0 and the
+// corrections a pull needs on top of the in-strip offset PullOff<k> (below):
+// across a strip edge or the periodic wrap in x, and across the periodic
+// wrap in y (walls do not wrap: a source beyond one is replaced by
+// bounce-back, and bot / top mark the rows next to them).
 struct Cell {
-    int x, xm, xp;  // column, column to the left / right (periodic)
-    int r0, rm, rp; // element offsets of rows y, y - 1, y + 1
+    int o;          // y kRowStride + col_off(x)
+    int shl, shr;   // added for sources at x - 1 (c_kx = +1) and x + 1 (c_kx = -1)
+    bool y0, yn;    // first / last row: a source beyond it wraps by ny rows when y is periodic
     bool bot, top;  // first / last fluid row next to a wall (half a cell beyond)
 };
 __device__ __forceinline__ Cell make_cell(const Inst &I, int x, int y) {
     Cell c;
-    c.x = x;
-    c.xm = (x == 0) ? I.nx - 1 : x - 1;
-    c.xp = (x == I.nx - 1) ? 0 : x + 1;
-    c.r0 = y * I.pitch;
-    c.rm = ((y == 0) ? I.ny - 1 : y - 1) * I.pitch;
-    c.rp = ((y == I.ny - 1) ? 0 : y + 1) * I.pitch;
+    const int cx = col_off(I, x);
+    c.o = y * kRowStride + cx;
+    // in-strip offsets assume the neighbour column at cx -/+ 1
+    c.shl = (x == 0) ? col_off(I, I.nx - 1) - cx + 1 : ((x & 31) == 0 ? kStripW - I.strip : 0);
+    c.shr = (x == I.nx - 1) ? -cx - 1 : ((x & 31) == 31 ? I.strip - kStripW : 0);
+    c.y0 = y == 0;
+    c.yn = y == I.ny - 1;
     c.bot = (y == 0) && !I.periodic_y;
     c.top = (y == I.ny - 1) && !I.periodic_y;
     return c;
+}
+
+// Element offset of the pull source of direction k, x - c_k, from the
+// cell's own element in plane 0, within the cell's strip.
+template <int k> struct PullOff {
+    static constexpr int value = k * kPlaneStride - Q<k>::cy * kRowStride - Q<k>::cx;
+};
+// Element offset of the source of direction k of cell C (no wall between).
+template <int k> __device__ __forceinline__ int src_off(const Inst &I, const Cell &C) {
+    constexpr int cx = Q<k>::cx, cy = Q<k>::cy;
+    int off = C.o + PullOff<k>::value + (cx > 0 ? C.shl : (cx < 0 ? C.shr : 0));
+    if (cy > 0 && C.y0) off += I.ny * kRowStride;
+    if (cy < 0 && C.yn) off -= I.ny * kRowStride;
+    return off;
 }
 
 // g_k(x) from the current buffer A (kRaw: in stored units, sigma_k g_k;
 // kStream: with the sweep's L2 eviction priority, raw only).
 template <int k, class S, class R, bool kRaw = false, bool kStream = false>
 __device__ __forceinline__ void pull_one(const S *__restrict__ A, const Inst &I, const Cell &C, R &g, uint64_t pol = 0) {
-    constexpr int cx = Q<k>::cx, cy = Q<k>::cy, o = Q<k>::opp;
+    constexpr int cy = Q<k>::cy, o = Q<k>::opp;
     // source cell x - c_k; beyond a wall when it is row -1 or row ny
     const bool wall = (cy > 0 && C.bot) || (cy < 0 && C.top);
     if (wall) {
-        const S *p = A + (o * I.plane32 + C.r0 + C.x);
+        const S *p = A + (C.o + o * kPlaneStride);
         if constexpr (kRaw && kStream) g = (R)Store<S>::ld_stream(p, pol) + bb_stored<R>(I, cy > 0 ? 0 : 1, k);
         else if constexpr (kRaw) g = (R)Store<S>::ld_raw(p) + bb_stored<R>(I, cy > 0 ? 0 : 1, k);
         else g = (R)Store<S>::ld(p, I.inv_scale[o]) + bb_term<R>(I, cy > 0 ? 0 : 1, k);
     } else {
-        const int rs = cy > 0 ? C.rm : (cy < 0 ? C.rp : C.r0);
-        const int xs = cx > 0 ? C.xm : (cx < 0 ? C.xp : C.x);
-        const S *p = A + (k * I.plane32 + rs + xs);
+        const S *p = A + src_off<k>(I, C);
         if constexpr (kRaw && kStream) g = (R)Store<S>::ld_stream(p, pol);
         else if constexpr (kRaw) g = (R)Store<S>::ld_raw(p);
         else g = (R)Store<S>::ld(p, I.inv_scale[k]);
@@ -248,50 +277,72 @@ __device__ __forceinline__ void pull_one(const S *__restrict__ A, const Inst &I,
 // yields it (initial state, writes of a given state).
 template <int k, class S, class R>
 __device__ __forceinline__ void place_one(S *__restrict__ A, const Inst &I, const Cell &C, R g) {
-    constexpr int cx = Q<k>::cx, cy = Q<k>::cy, o = Q<k>::opp;
+    constexpr int cy = Q<k>::cy, o = Q<k>::opp;
     const bool wall = (cy > 0 && C.bot) || (cy < 0 && C.top);
     if (wall) {
-        Store<S>::st(A + (o * I.plane32 + C.r0 + C.x), g - bb_term<R>(I, cy > 0 ? 0 : 1, k), I.scale[o]);
+        Store<S>::st(A + (C.o + o * kPlaneStride), g - bb_term<R>(I, cy > 0 ? 0 : 1, k), I.scale[o]);
     } else {
-        const int rs = cy > 0 ? C.rm : (cy < 0 ? C.rp : C.r0);
-        const int xs = cx > 0 ? C.xm : (cx < 0 ? C.xp : C.x);
-        Store<S>::st(A + (k * I.plane32 + rs + xs), g, I.scale[k]);
+        Store<S>::st(A + src_off<k>(I, C), g, I.scale[k]);
     }
 }
 
 template <class S, class R, bool kRaw = false, bool kStream = false>
 __device__ __forceinline__ void pull_pops(const S *__restrict__ A, const Inst &I, const Cell &C, R g[9], uint64_t pol = 0) {
+    // grouped by the x shift of the source (c_kx = 0, +1, -1)
     pull_one<0, S, R, kRaw, kStream>(A, I, C, g[0], pol);
-    pull_one<1, S, R, kRaw, kStream>(A, I, C, g[1], pol);
     pull_one<2, S, R, kRaw, kStream>(A, I, C, g[2], pol);
-    pull_one<3, S, R, kRaw, kStream>(A, I, C, g[3], pol);
     pull_one<4, S, R, kRaw, kStream>(A, I, C, g[4], pol);
+    pull_one<1, S, R, kRaw, kStream>(A, I, C, g[1], pol);
     pull_one<5, S, R, kRaw, kStream>(A, I, C, g[5], pol);
+    pull_one<8, S, R, kRaw, kStream>(A, I, C, g[8], pol);
+    pull_one<3, S, R, kRaw, kStream>(A, I, C, g[3], pol);
     pull_one<6, S, R, kRaw, kStream>(A, I, C, g[6], pol);
     pull_one<7, S, R, kRaw, kStream>(A, I, C, g[7], pol);
-    pull_one<8, S, R, kRaw, kStream>(A, I, C, g[8], pol);
 }
 
-// Pull of all nine directions for a cell with no wall and no periodic wrap
-// among its neighbours; p points at the cell's element in plane 0.
-template <class S, class R, bool kRaw = false, bool kStream = false>
-__device__ __forceinline__ void pull_inner(const S *__restrict__ p, const Inst &I, R g[9], uint64_t pol = 0) {
-#pragma unroll
-    for (int k = 0; k < 9; ++k) {
-        if constexpr (kRaw && kStream) g[k] = (R)Store<S>::ld_stream(p + I.pull_off[k], pol);
-        else if constexpr (kRaw) g[k] = (R)Store<S>::ld_raw(p + I.pull_off[k]);
-        else g[k] = (R)Store<S>::ld(p + I.pull_off[k], I.inv_scale[k]);
-    }
+template <int k, class S, class R, bool kRaw, bool kStream>
+__device__ __forceinline__ void pull_inner_one(const S *__restrict__ p, const Inst &I, R &g, uint64_t pol) {
+    const S *q = p + PullOff<k>::value;
+    if constexpr (kRaw && kStream) g = (R)Store<S>::ld_stream(q, pol);
+    else if constexpr (kRaw) g = (R)Store<S>::ld_raw(q);
+    else g = (R)Store<S>::ld(q, I.inv_scale[k]);
 }
+// Pull of all nine directions for a cell with no wall and no periodic wrap
+// among its neighbours; p points at the cell's element in plane 0.  A source
+// left of the strip (c_kx = +1 from its first column) is reached from
+// pl = p + shl, one right of it (c_kx = -1 from its last column) from
+// pr = p + shr: shl and shr (strip_left, strip_right) shift by a strip less
+// or more one row of a plane there, and are 0 elsewhere.
+template <class S, class R, bool kRaw = false, bool kStream = false>
+__device__ __forceinline__ void pull_inner(const S *__restrict__ p, const int shl, const int shr, const Inst &I,
+                                           R g[9], uint64_t pol = 0) {
+    pull_inner_one<0, S, R, kRaw, kStream>(p, I, g[0], pol);
+    pull_inner_one<2, S, R, kRaw, kStream>(p, I, g[2], pol);
+    pull_inner_one<4, S, R, kRaw, kStream>(p, I, g[4], pol);
+    const S *pl = p + shl;
+    pull_inner_one<1, S, R, kRaw, kStream>(pl, I, g[1], pol);
+    pull_inner_one<5, S, R, kRaw, kStream>(pl, I, g[5], pol);
+    pull_inner_one<8, S, R, kRaw, kStream>(pl, I, g[8], pol);
+    const S *pr = p + shr;
+    pull_inner_one<3, S, R, kRaw, kStream>(pr, I, g[3], pol);
+    pull_inner_one<6, S, R, kRaw, kStream>(pr, I, g[6], pol);
+    pull_inner_one<7, S, R, kRaw, kStream>(pr, I, g[7], pol);
+}
+static_assert(Q<1>::cx > 0 && Q<5>::cx > 0 && Q<8>::cx > 0 && Q<3>::cx < 0 && Q<6>::cx < 0 && Q<7>::cx < 0 &&
+                  Q<0>::cx == 0 && Q<2>::cx == 0 && Q<4>::cx == 0,
+              "pull_inner's choice of base pointer per direction");
+// Shifts of pull_inner's pl and pr for column x (an element offset from p).
+__device__ __forceinline__ int strip_left(const Inst &I, int x) { return (x & 31) == 0 ? kStripW - I.strip : 0; }
+__device__ __forceinline__ int strip_right(const Inst &I, int x) { return (x & 31) == 31 ? I.strip - kStripW : 0; }
 
 // Post-collision populations stored at the cell whose plane-0 element p is.
 template <class S, class R, bool kRaw = false, bool kStream = false>
 __device__ __forceinline__ void put_at(S *__restrict__ p, const Inst &I, const R g[9], uint64_t pol = 0) {
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
-        if constexpr (kRaw && kStream) Store<S>::st_stream(p + k * I.plane32, g[k], pol);
-        else if constexpr (kRaw) Store<S>::st_raw(p + k * I.plane32, g[k]);
-        else Store<S>::st(p + k * I.plane32, g[k], I.scale[k]);
+        if constexpr (kRaw && kStream) Store<S>::st_stream(p + k * kPlaneStride, g[k], pol);
+        else if constexpr (kRaw) Store<S>::st_raw(p + k * kPlaneStride, g[k]);
+        else Store<S>::st(p + k * kPlaneStride, g[k], I.scale[k]);
     }
 }
 

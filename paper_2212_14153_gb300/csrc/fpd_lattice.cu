@@ -247,11 +247,16 @@ __device__ __forceinline__ void lattice_tile(const Inst &I, S *__restrict__ pool
     uint64_t pol = 0;
     if constexpr (kStream) pol = pol_evict_first();
     // populations in stored units (sigma_k g_k)
+    const int cx0 = col_off(I, x);  // the thread's cells k sit k RX columns on, within the strip
     auto pull = [&]() {
         if (inner) {
-            const S *p = Asrc + (y[0] * I.pitch + x);
+            const S *p = Asrc + (y[0] * kRowStride + cx0);
 #pragma unroll
-            for (int k = 0; k < CY; ++k) pull_inner<S, R, true, kStream>(p + (k * RY * I.pitch + k * RX), I, g[k], pol);
+            for (int k = 0; k < CY; ++k) {
+                const S *pk = p + (k * RY * kRowStride + k * RX);
+                pull_inner<S, R, true, kStream>(pk, strip_left(I, tx + k * RX), strip_right(I, tx + k * RX), I, g[k],
+                                                pol);
+            }
         } else {
 #pragma unroll
             for (int k = 0; k < CY; ++k)
@@ -280,7 +285,8 @@ __device__ __forceinline__ void lattice_tile(const Inst &I, S *__restrict__ pool
         R Fx, Fy, s_nu, s_e, s_eps, s_q;
         cell_overlay<R, kStream>(I, tab, sov, m, W, any, x + k * RX, y[k], Fx, Fy, s_nu, s_e, s_eps, s_q);
         collide_cell<S, R, kColl>(I, g[k], Fx, Fy, s_nu, s_e, s_eps, s_q, forced);
-        put_at<S, R, true, kStream>(Adst + (kInner ? y[k] * I.pitch + x + k * RX : C[k].r0 + C[k].x), I, g[k], pol);
+        put_at<S, R, true, kStream>(Adst + (kInner ? y[k] * kRowStride + cx0 + k * RX : C[k].o), I, g[k],
+                                    pol);
     }
 }
 
@@ -392,7 +398,7 @@ template <> struct VecWidth<__half> { static constexpr int value = 4; };
 
 // The NV cells x0 .. x0 + NV - 1 of row y owned by one thread.
 struct VCell {
-    int x0, xm, xp;  // first cell, the cell left of it, the cell right of the last (periodic)
+    int x0, xm, xp;  // first cell, the cell left of it, the cell right of the last (periodic): element offsets
     int r0, rm, rp;  // element offsets of rows y, y - 1, y + 1 (wrapped when y is periodic)
     bool bot, top, valid;
     bool left, right;  // first lane of its segment / last lane holding cells of its row segment
@@ -403,12 +409,13 @@ __device__ __forceinline__ VCell make_vcell(const Inst &I, int x0, int y, int la
     VCell c;
     c.valid = x0 < I.nx && y < I.ny;
     const int yy = c.valid ? y : 0;
-    c.x0 = x0;
-    c.xm = (x0 == 0) ? I.nx - 1 : x0 - 1;
-    c.xp = (x0 + NV >= I.nx) ? 0 : x0 + NV;
-    c.r0 = yy * I.pitch;
-    c.rm = ((yy == 0) ? I.ny - 1 : yy - 1) * I.pitch;
-    c.rp = ((yy == I.ny - 1) ? 0 : yy + 1) * I.pitch;
+    // column element offsets (NV divides the strip width: a vector stays in its strip)
+    c.x0 = col_off(I, x0 < I.nx ? x0 : 0);
+    c.xm = col_off(I, (x0 == 0) ? I.nx - 1 : x0 - 1);
+    c.xp = col_off(I, (x0 + NV >= I.nx) ? 0 : x0 + NV);
+    c.r0 = yy * kRowStride;
+    c.rm = ((yy == 0) ? I.ny - 1 : yy - 1) * kRowStride;
+    c.rp = ((yy == I.ny - 1) ? 0 : yy + 1) * kRowStride;
     c.bot = (yy == 0) && !I.periodic_y;
     c.top = (yy == I.ny - 1) && !I.periodic_y;
     c.left = lane_in_seg == 0;
@@ -427,7 +434,7 @@ __device__ __forceinline__ void vload_one(const S *__restrict__ A, const Inst &I
     const int row = wall ? C.r0 : (cy > 0 ? C.rm : (cy < 0 ? C.rp : C.r0));
     // stored values (scale[k] == scale[opp k]: the wall's reflected plane
     // is in the same units)
-    if (C.valid) VecIO<S, NV>::ld(A + ((wall ? o : k) * I.plane32 + row + C.x0), 1.0f, v);
+    if (C.valid) VecIO<S, NV>::ld(A + ((wall ? o : k) * kPlaneStride + row + C.x0), 1.0f, v);
     else {
 #pragma unroll
         for (int j = 0; j < NV; ++j) v[j] = (R)0;
@@ -445,12 +452,12 @@ __device__ __forceinline__ void vload_one(const S *__restrict__ A, const Inst &I
 #pragma unroll
         for (int j = 0; j < NV; ++j) g[j][k] = v[j];
     } else if constexpr (cx > 0) {
-        if (C.left && C.valid) nb = (R)Store<S>::ld_raw(A + (k * I.plane32 + row + C.xm));
+        if (C.left && C.valid) nb = (R)Store<S>::ld_raw(A + (k * kPlaneStride + row + C.xm));
         g[0][k] = nb;
 #pragma unroll
         for (int j = 1; j < NV; ++j) g[j][k] = v[j - 1];
     } else {
-        if (C.right && C.valid) nb = (R)Store<S>::ld_raw(A + (k * I.plane32 + row + C.xp));
+        if (C.right && C.valid) nb = (R)Store<S>::ld_raw(A + (k * kPlaneStride + row + C.xp));
 #pragma unroll
         for (int j = 0; j < NV - 1; ++j) g[j][k] = v[j + 1];
         g[NV - 1][k] = nb;
@@ -464,7 +471,7 @@ __device__ __forceinline__ void vstore_one(S *__restrict__ D, const Inst &I, con
     R v[NV];
 #pragma unroll
     for (int j = 0; j < NV; ++j) v[j] = g[j][k];
-    VecIO<S, NV>::st(D + (k * I.plane32 + C.r0 + C.x0), v, 1.0f);
+    VecIO<S, NV>::st(D + (k * kPlaneStride + C.r0 + C.x0), v, 1.0f);
 }
 
 template <class S, int NV, class R>
@@ -789,9 +796,9 @@ __global__ void __launch_bounds__(kTileX *kTileY)
     const int x = bx * kTileX + threadIdx.x, y = by * kTileY + threadIdx.y;
     bool bad = false;
     if (x < I.nx && y < I.ny) {
-        const S *A = pop_buffer(pool, I, gparity ^ I.par_xor) + (y * I.pitch + x);
+        const S *A = pop_buffer(pool, I, gparity ^ I.par_xor) + (y * kRowStride + col_off(I, x));
 #pragma unroll
-        for (int k = 0; k < 9; ++k) bad |= !isfinite(Store<S>::ld(A + k * I.plane32, 1.0f));
+        for (int k = 0; k < 9; ++k) bad |= !isfinite(Store<S>::ld(A + k * kPlaneStride, 1.0f));
     }
     if (__syncthreads_or(bad) && threadIdx.x == 0 && threadIdx.y == 0) atomicOr(status + slot, kFlagNonFinite);
 }

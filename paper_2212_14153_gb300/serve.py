@@ -43,9 +43,9 @@ class Request:
 
 def state_bytes(cfg: dict, precision: int) -> int:
     """Device bytes of one instance's populations (two buffers of 9 planes,
-    128-byte rows)."""
+    the width padded to whole 32-column strips)."""
     es = {0: 8, 1: 4, 2: 2}[precision]
-    align = 128 // es
+    align = 32
     pitch = (int(cfg["nx"]) + align - 1) // align * align
     return 2 * 9 * pitch * int(cfg["ny"]) * es
 

@@ -108,11 +108,12 @@ def test_memory_cap_limits_residency(fake):
     assert srv.resident_bytes == 0
 
 
-def test_state_bytes_pads_rows_to_128_bytes():
-    # two buffers of 9 planes
+def test_state_bytes_pads_width_to_whole_strips():
+    # two buffers of 9 planes, the width padded to 32-column strips
     assert serve.state_bytes(dict(nx=80, ny=40), 1) == 2 * 9 * 96 * 40 * 4
-    assert serve.state_bytes(dict(nx=80, ny=40), 2) == 2 * 9 * 128 * 40 * 2
+    assert serve.state_bytes(dict(nx=80, ny=40), 2) == 2 * 9 * 96 * 40 * 2
     assert serve.state_bytes(dict(nx=64, ny=10), 0) == 2 * 9 * 64 * 10 * 8
+    assert serve.state_bytes(dict(nx=65, ny=10), 0) == 2 * 9 * 96 * 10 * 8
 
 
 def test_request_larger_than_the_cap_is_rejected_not_spun_on(fake):
