@@ -295,8 +295,9 @@ int fpd_internal_flow(fpd_sim *s, double *eps);
 /* Kernel tuning (same arithmetic, same results up to rounding: the
  * compiler may contract multiply-adds differently in each variant):
  * variant 0 runs the lattice sweep with one cell per thread (32 x 8 threads
- * per 32 x 8 tile), variant 1 with two cells per thread along x, 16 cells
- * apart (16 x 8 threads), variant 2 with 2 (FP64) or 4 (FP32, FP16 storage) consecutive
+ * per 32 x 8 tile), variant 1 with two cells per thread along x, adjacent
+ * (FP32, FP16 storage; paired accesses) or 16 cells apart (FP64) (16 x 8
+ * threads), variant 2 with 2 (FP64) or 4 (FP32, FP16 storage) consecutive
  * cells per thread along x, each plane moved with one 16-byte (8-byte for
  * FP16) access; variant 2 needs nx to be a multiple of that width, and an
  * instance whose nx is not runs variant 0 instead.  Chosen per workload by

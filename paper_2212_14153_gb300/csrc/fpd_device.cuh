@@ -173,6 +173,21 @@ template <> struct Store<float> {
     static __device__ __forceinline__ void st_stream(float *p, float v, uint64_t pol) {
         asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(v), "l"(pol) : "memory");
     }
+    // two adjacent elements, p 8-byte aligned
+    static __device__ __forceinline__ void ld2_raw(const float *p, float &a, float &b) {
+        const float2 t = *reinterpret_cast<const float2 *>(p);
+        a = t.x, b = t.y;
+    }
+    static __device__ __forceinline__ void st2_raw(float *p, float a, float b) {
+        *reinterpret_cast<float2 *>(p) = make_float2(a, b);
+    }
+    static __device__ __forceinline__ void ld2_stream(const float *p, uint64_t pol, float &a, float &b) {
+        asm volatile("ld.global.nc.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(a), "=f"(b) : "l"(p), "l"(pol));
+    }
+    static __device__ __forceinline__ void st2_stream(float *p, float a, float b, uint64_t pol) {
+        asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(p), "f"(a), "f"(b), "l"(pol)
+                     : "memory");
+    }
 };
 template <> struct Store<__half> {
     static constexpr bool kScaled = true;
@@ -191,6 +206,27 @@ template <> struct Store<__half> {
     }
     static __device__ __forceinline__ void st_stream(__half *p, float v, uint64_t pol) {
         asm volatile("st.global.L2::cache_hint.b16 [%0], %1, %2;" ::"l"(p), "h"(__half_as_ushort(__float2half_rn(v))),
+                     "l"(pol)
+                     : "memory");
+    }
+    // two adjacent elements, p 4-byte aligned: exact widening, and one
+    // packed round-to-nearest narrowing of both (each as __float2half_rn)
+    static __device__ __forceinline__ void ld2_raw(const __half *p, float &a, float &b) {
+        const float2 t = __half22float2(*reinterpret_cast<const __half2 *>(p));
+        a = t.x, b = t.y;
+    }
+    static __device__ __forceinline__ void st2_raw(__half *p, float a, float b) {
+        *reinterpret_cast<__half2 *>(p) = __floats2half2_rn(a, b);
+    }
+    static __device__ __forceinline__ void ld2_stream(const __half *p, uint64_t pol, float &a, float &b) {
+        unsigned u;
+        asm volatile("ld.global.nc.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(u) : "l"(p), "l"(pol));
+        const float2 t = __half22float2(*reinterpret_cast<const __half2 *>(&u));
+        a = t.x, b = t.y;
+    }
+    static __device__ __forceinline__ void st2_stream(__half *p, float a, float b, uint64_t pol) {
+        const __half2 h = __floats2half2_rn(a, b);
+        asm volatile("st.global.L2::cache_hint.b32 [%0], %1, %2;" ::"l"(p), "r"(*reinterpret_cast<const unsigned *>(&h)),
                      "l"(pol)
                      : "memory");
     }
@@ -334,6 +370,55 @@ static_assert(Q<1>::cx > 0 && Q<5>::cx > 0 && Q<8>::cx > 0 && Q<3>::cx < 0 && Q<
 // Shifts of pull_inner's pl and pr for column x (an element offset from p).
 __device__ __forceinline__ int strip_left(const Inst &I, int x) { return (x & 31) == 0 ? kStripW - I.strip : 0; }
 __device__ __forceinline__ int strip_right(const Inst &I, int x) { return (x & 31) == 31 ? I.strip - kStripW : 0; }
+
+// Two x-adjacent cells a (even column, element p in plane 0) and b = a + 1
+// with no wall and no periodic wrap among their neighbours, in stored
+// units: a direction with c_kx = 0 pulls both from adjacent elements (one
+// paired access); c_kx = +1 pulls a from column x - 1 (p + shl across the
+// strip's left edge) and b from a's column; c_kx = -1 pulls a from b's
+// column and b from x + 2 (p + 1 + shr across the right edge).
+template <class S, bool kStream> __device__ __forceinline__ float ld1(const S *q, uint64_t pol) {
+    if constexpr (kStream) return Store<S>::ld_stream(q, pol);
+    else return Store<S>::ld_raw(q);
+}
+template <int k, class S, bool kStream>
+__device__ __forceinline__ void pull_adj_one(const S *__restrict__ p, int shl, int shr, float ga[9], float gb[9],
+                                             uint64_t pol) {
+    constexpr int cx = Q<k>::cx, off = PullOff<k>::value;
+    if constexpr (cx == 0) {
+        if constexpr (kStream) Store<S>::ld2_stream(p + off, pol, ga[k], gb[k]);
+        else Store<S>::ld2_raw(p + off, ga[k], gb[k]);
+    } else if constexpr (cx > 0) {
+        ga[k] = ld1<S, kStream>(p + shl + off, pol);
+        gb[k] = ld1<S, kStream>(p + 1 + off, pol);
+    } else {
+        ga[k] = ld1<S, kStream>(p + off, pol);
+        gb[k] = ld1<S, kStream>(p + 1 + shr + off, pol);
+    }
+}
+template <class S, bool kStream>
+__device__ __forceinline__ void pull_adj(const S *__restrict__ p, int shl, int shr, float ga[9], float gb[9],
+                                         uint64_t pol) {
+    pull_adj_one<0, S, kStream>(p, shl, shr, ga, gb, pol);
+    pull_adj_one<2, S, kStream>(p, shl, shr, ga, gb, pol);
+    pull_adj_one<4, S, kStream>(p, shl, shr, ga, gb, pol);
+    pull_adj_one<1, S, kStream>(p, shl, shr, ga, gb, pol);
+    pull_adj_one<5, S, kStream>(p, shl, shr, ga, gb, pol);
+    pull_adj_one<8, S, kStream>(p, shl, shr, ga, gb, pol);
+    pull_adj_one<3, S, kStream>(p, shl, shr, ga, gb, pol);
+    pull_adj_one<6, S, kStream>(p, shl, shr, ga, gb, pol);
+    pull_adj_one<7, S, kStream>(p, shl, shr, ga, gb, pol);
+}
+// Post-collision populations of two x-adjacent cells, p (even column) in
+// plane 0, one paired store per plane.
+template <class S, bool kStream>
+__device__ __forceinline__ void put_adj(S *__restrict__ p, const float ga[9], const float gb[9], uint64_t pol) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        if constexpr (kStream) Store<S>::st2_stream(p + k * kPlaneStride, ga[k], gb[k], pol);
+        else Store<S>::st2_raw(p + k * kPlaneStride, ga[k], gb[k]);
+    }
+}
 
 // Post-collision populations stored at the cell whose plane-0 element p is.
 template <class S, class R, bool kRaw = false, bool kStream = false>
@@ -557,62 +642,96 @@ __device__ __forceinline__ void collide(R g[9], R Fx, R Fy, R s_nu, R s_e, R s_e
 // stored values, so the FP16 path needs no per-population rescaling, and it
 // keeps only the pair sums and differences live: about 60 operations per
 // cell against ~115 for the moment form.
-template <class R, bool kScaled>
-__device__ __forceinline__ void collide_trt(R x[9], R sp, R sm, const Inst &I) {
+// Correctly rounded arithmetic on one value or on a pair of FP32 values.
+// The pair form issues one packed instruction (f32x2) for both lanes, and
+// each lane rounds exactly as the scalar form does, so a thread that
+// advances two cells with it gets the bits each cell gets alone.  Every
+// operation is spelled out (no contraction left to the compiler).
+template <class V> struct Ar;
+template <> struct Ar<double> {
+    static __device__ __forceinline__ double c(double a) { return a; }
+    static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+    static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+    static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+    static __device__ __forceinline__ double fma(double a, double b, double d) { return __fma_rn(a, b, d); }
+    static __device__ __forceinline__ double rcp(double a) { return recip(a); }
+};
+template <> struct Ar<float> {
+    static __device__ __forceinline__ float c(float a) { return a; }
+    static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+    static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+    static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+    static __device__ __forceinline__ float fma(float a, float b, float d) { return __fmaf_rn(a, b, d); }
+    static __device__ __forceinline__ float rcp(float a) { return recip(a); }
+};
+template <> struct Ar<float2> {
+    static __device__ __forceinline__ float2 c(float a) { return make_float2(a, a); }
+    static __device__ __forceinline__ float2 add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+    // a - b as fma(b, -1, a): one rounding of the exact difference, as __fsub_rn
+    static __device__ __forceinline__ float2 sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+    static __device__ __forceinline__ float2 mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+    static __device__ __forceinline__ float2 fma(float2 a, float2 b, float2 d) { return __ffma2_rn(a, b, d); }
+    static __device__ __forceinline__ float2 rcp(float2 a) { return make_float2(recip(a.x), recip(a.y)); }
+};
+
+template <class R, bool kScaled, class V>
+__device__ __forceinline__ void collide_trt(V x[9], V sp, V sm, const Inst &I) {
+    using A = Ar<V>;
     // per weight class c = 0 (rest), 1 (axis), 2 (diagonal): sigma_c w_c
     // and multiples, and 1 / sigma_c
-    R sw0, sw1, sw2, k45_1, k45_2, k3_1, k3_2, i0, i1, i2;
+    V sw0, sw1, sw2, k45_1, k45_2, k3_1, k3_2, i0, i1, i2;
     if constexpr (kScaled) {
-        sw0 = (R)I.trt_sw[0], sw1 = (R)I.trt_sw[1], sw2 = (R)I.trt_sw[2];
-        k45_1 = (R)I.trt_k45[1], k45_2 = (R)I.trt_k45[2];
-        k3_1 = (R)I.trt_k3[1], k3_2 = (R)I.trt_k3[2];
-        i0 = (R)I.inv_scale[0], i1 = (R)I.inv_scale[1], i2 = (R)I.inv_scale[5];
+        sw0 = A::c(I.trt_sw[0]), sw1 = A::c(I.trt_sw[1]), sw2 = A::c(I.trt_sw[2]);
+        k45_1 = A::c(I.trt_k45[1]), k45_2 = A::c(I.trt_k45[2]);
+        k3_1 = A::c(I.trt_k3[1]), k3_2 = A::c(I.trt_k3[2]);
+        i0 = A::c(I.inv_scale[0]), i1 = A::c(I.inv_scale[1]), i2 = A::c(I.inv_scale[5]);
     } else {
-        sw0 = (R)(4.0 / 9.0), sw1 = (R)(1.0 / 9.0), sw2 = (R)(1.0 / 36.0);
-        k45_1 = (R)0.5, k45_2 = (R)0.125, k3_1 = (R)(1.0 / 3.0), k3_2 = (R)(1.0 / 12.0);
-        i0 = i1 = i2 = (R)1;
+        sw0 = A::c((R)(4.0 / 9.0)), sw1 = A::c((R)(1.0 / 9.0)), sw2 = A::c((R)(1.0 / 36.0));
+        k45_1 = A::c((R)0.5), k45_2 = A::c((R)0.125), k3_1 = A::c((R)(1.0 / 3.0)), k3_2 = A::c((R)(1.0 / 12.0));
+        i0 = i1 = i2 = A::c((R)1);  // unused
     }
+    const V one = A::c((R)1), half = A::c((R)0.5), mhalf = A::c((R)-0.5);
     // link pairs: a = x_k + x_opp = 2 sigma g+_k, b = x_k - x_opp = 2 sigma g-_k
-    const R a13 = x[1] + x[3], b13 = x[1] - x[3];
-    const R a24 = x[2] + x[4], b24 = x[2] - x[4];
-    const R a57 = x[5] + x[7], b57 = x[5] - x[7];
-    const R a68 = x[6] + x[8], b68 = x[6] - x[8];
-    R drho, jx, jy;
+    const V a13 = A::add(x[1], x[3]), b13 = A::sub(x[1], x[3]);
+    const V a24 = A::add(x[2], x[4]), b24 = A::sub(x[2], x[4]);
+    const V a57 = A::add(x[5], x[7]), b57 = A::sub(x[5], x[7]);
+    const V a68 = A::add(x[6], x[8]), b68 = A::sub(x[6], x[8]);
+    V drho, jx, jy;
     if constexpr (kScaled) {
-        drho = i2 * (a57 + a68) + (i1 * (a13 + a24) + i0 * x[0]);
-        jx = i2 * (b57 - b68) + i1 * b13;
-        jy = i2 * (b57 + b68) + i1 * b24;
+        drho = A::fma(i2, A::add(a57, a68), A::fma(i1, A::add(a13, a24), A::mul(i0, x[0])));
+        jx = A::fma(i2, A::sub(b57, b68), A::mul(i1, b13));
+        jy = A::fma(i2, A::add(b57, b68), A::mul(i1, b24));
     } else {
-        drho = x[0] + (a13 + a24) + (a57 + a68);
-        jx = b13 + (b57 - b68);
-        jy = b24 + (b57 + b68);
+        drho = A::add(A::add(x[0], A::add(a13, a24)), A::add(a57, a68));
+        jx = A::add(b13, A::sub(b57, b68));
+        jy = A::add(b24, A::add(b57, b68));
     }
-    const R rho = (R)1 + drho;
-    const R irho = recip(rho);
-    const R ux = jx * irho, uy = jy * irho;
+    const V rho = A::add(one, drho);
+    const V irho = A::rcp(rho);
+    const V ux = A::mul(jx, irho), uy = A::mul(jy, irho);
     // sigma eq+_k = sigma w D + 4.5 sigma w rho (c.u)^2, D = rho - 1 - 1.5 rho u^2;
     // sigma eq-_k = 3 sigma w rho c.u; here already times the rates
-    const R D = drho - (R)1.5 * (rho * (ux * ux + uy * uy));
-    const R spD = sp * D, spr = sp * rho, smr = sm * rho;
-    const R es1 = sw1 * spD, es2 = sw2 * spD;
-    const R qs1 = k45_1 * spr, qs2 = k45_2 * spr;
-    const R ts1 = k3_1 * smr, ts2 = k3_2 * smr;
-    const R c1 = (R)0.5 - (R)0.5 * sp, c2 = (R)0.5 - (R)0.5 * sm;
+    const V D = A::fma(A::c((R)-1.5), A::mul(rho, A::fma(ux, ux, A::mul(uy, uy))), drho);
+    const V spD = A::mul(sp, D), spr = A::mul(sp, rho), smr = A::mul(sm, rho);
+    const V es1 = A::mul(sw1, spD), es2 = A::mul(sw2, spD);
+    const V qs1 = A::mul(k45_1, spr), qs2 = A::mul(k45_2, spr);
+    const V ts1 = A::mul(k3_1, smr), ts2 = A::mul(k3_2, smr);
+    const V c1 = A::fma(mhalf, sp, half), c2 = A::fma(mhalf, sm, half);
     // rest population: x0 - sp (x0 - sigma_0 w_0 D)
-    x[0] = ((R)1 - sp) * x[0] + sw0 * spD;
+    x[0] = A::fma(A::sub(one, sp), x[0], A::mul(sw0, spD));
     // each pair: the even half (a/2) and the odd half (b/2) relax separately,
     //   A = a/2 - sp (a/2 - sigma eq+),  B = b/2 - sm (b/2 - sigma eq-),
     // and x*_k = A + B, x*_opp = A - B
-    auto pair = [&](int k, int ko, R cu, R a, R b, R es, R qs, R ts) {
-        const R A = c1 * a + (qs * (cu * cu) + es);
-        const R B = c2 * b + ts * cu;
-        x[k] = A + B;
-        x[ko] = A - B;
+    auto pair = [&](int k, int ko, V cu, V a, V b, V es, V qs, V ts) {
+        const V ev = A::fma(c1, a, A::fma(qs, A::mul(cu, cu), es));
+        const V od = A::fma(c2, b, A::mul(ts, cu));
+        x[k] = A::add(ev, od);
+        x[ko] = A::sub(ev, od);
     };
     pair(1, 3, ux, a13, b13, es1, qs1, ts1);
     pair(2, 4, uy, a24, b24, es1, qs1, ts1);
-    pair(5, 7, ux + uy, a57, b57, es2, qs2, ts2);
-    pair(6, 8, uy - ux, a68, b68, es2, qs2, ts2);
+    pair(5, 7, A::add(ux, uy), a57, b57, es2, qs2, ts2);
+    pair(6, 8, A::sub(uy, ux), a68, b68, es2, qs2, ts2);
 }
 
 // Relaxation rates of one cell from its kinematic viscosity (Eq. 1 gives nu).

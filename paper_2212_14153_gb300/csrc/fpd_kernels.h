@@ -58,7 +58,8 @@ constexpr int kWatchSteps = 1024;
 // of the same step: the sweep is then launched as a programmatic dependent
 // of it and loads its populations before waiting for it.
 // variant: 0 = one cell per thread (32 x 8 threads), 1 = two cells per
-// thread along x, 16 apart (16 x 8 threads), 2 = lattice_vec_width(precision) cells per
+// thread along x, adjacent (FP32, FP16 storage) or 16 apart (FP64) (16 x 8
+// threads), 2 = lattice_vec_width(precision) cells per
 // thread along x with vector loads and stores ((32 / width) x 8 threads;
 // needs nx % width == 0, otherwise variant 0 runs); same tiles, same results.
 constexpr int kLatticeVariants = 3;

@@ -164,11 +164,14 @@ constexpr int kCollTrt = 0, kCollMrt = 1, kCollAny = 2;
 // rate sets (most of a lattice).  Every kernel makes the same choice per
 // cell, so an instance gives the same bits in every launch shape and in a
 // batch.
+template <int kColl> __device__ __forceinline__ bool moment_form(const Inst &I, bool forced) {
+    return kColl == kCollMrt || (kColl == kCollAny && I.collision == 1) || forced;
+}
 template <class S, class R, int kColl>
 __device__ __forceinline__ void collide_cell(const Inst &I, R g[9], R Fx, R Fy, R s_nu, R s_e, R s_eps, R s_q,
                                              bool forced) {
     constexpr bool kScaled = Store<S>::kScaled;
-    if (kColl == kCollMrt || (kColl == kCollAny && I.collision == 1) || forced) {
+    if (moment_form<kColl>(I, forced)) {
         if constexpr (kScaled) {
 #pragma unroll
             for (int k = 0; k < 9; ++k) g[k] *= (R)I.inv_scale[k];
@@ -208,15 +211,23 @@ __device__ __forceinline__ bool tile_cold_early(const unsigned *__restrict__ pre
     return any == 0u;
 }
 
+// Storage types whose variant-1 threads own two x-adjacent cells, moved
+// with one paired access per plane (FP16: one packed conversion for both);
+// the FP64 path places them kTileX / 2 apart.
+template <class S> struct AdjPairs { static constexpr bool value = !std::is_same<S, double>::value; };
+
 // One tile of the sweep: tile (bx, by) of instance I at the instance's step
 // parity, on kTileX x (kTileY / CY) threads; thread (tx, ty) owns the CY
 // cells (x, y0 + ty + k kTileY / CY), k < CY, of its column.  kAlongX: on
 // (kTileX / CY) x kTileY threads instead, thread (tx, ty) owns the CY cells
 // (x0 + tx + k kTileX / CY, y0 + ty) of its row, whose elements in every
 // plane lie a constant distance apart, so that one address serves all of
-// them (immediate offsets).  kInner: tiles away from walls and periodic
-// edges use the precomputed pull offsets.  kStream: the population loads
-// and stores carry the L2 evict-first priority (the single-lattice sweep).
+// them (immediate offsets); with two cells and FP32 or FP16 storage they
+// are the adjacent cells x0 + 2 tx and x0 + 2 tx + 1 (paired accesses, and
+// the two-relaxation-time collision of both in packed FP32 pairs).  kInner:
+// tiles away from walls and periodic edges use the in-strip pull offsets.
+// kStream: the population loads and stores carry the L2 evict-first
+// priority (the single-lattice sweep).
 template <class S, int CY, bool kInner, bool kAlongX, int kColl, bool kStream = false>
 __device__ __forceinline__ void lattice_tile(const Inst &I, S *__restrict__ pool, const BeadTab &tab,
                                              const unsigned *__restrict__ mask_read,
@@ -224,9 +235,13 @@ __device__ __forceinline__ void lattice_tile(const Inst &I, S *__restrict__ pool
                                              const int bx, const int by, const int parity, const int early_load,
                                              const int early_cold, const bool lead, const int tx, const int ty) {
     using R = typename Real<S>::type;
+    // kAdj: the two cells of a thread are x-adjacent (FP32 and FP16
+    // storage), moved with paired accesses; otherwise kTileX / 2 apart
+    constexpr bool kAdj = kAlongX && CY == 2 && AdjPairs<S>::value;
     constexpr int RY = kAlongX ? 0 : kTileY / CY;
-    constexpr int RX = kAlongX ? kTileX / CY : 0;
-    const int x = bx * kTileX + tx;
+    constexpr int RX = kAlongX ? (kAdj ? 1 : kTileX / CY) : 0;
+    const int xt = kAdj ? 2 * tx : tx;  // column within the tile
+    const int x = bx * kTileX + xt;
     const int tile = I.tile_base + by * I.ntx + bx;
     const int W = I.mask_words;
     const S *Asrc = pop_buffer(pool, I, parity);
@@ -251,11 +266,15 @@ __device__ __forceinline__ void lattice_tile(const Inst &I, S *__restrict__ pool
     auto pull = [&]() {
         if (inner) {
             const S *p = Asrc + (y[0] * kRowStride + cx0);
+            if constexpr (kAdj) {
+                pull_adj<S, kStream>(p, strip_left(I, xt), strip_right(I, xt + 1), g[0], g[1], pol);
+            } else {
 #pragma unroll
-            for (int k = 0; k < CY; ++k) {
-                const S *pk = p + (k * RY * kRowStride + k * RX);
-                pull_inner<S, R, true, kStream>(pk, strip_left(I, tx + k * RX), strip_right(I, tx + k * RX), I, g[k],
-                                                pol);
+                for (int k = 0; k < CY; ++k) {
+                    const S *pk = p + (k * RY * kRowStride + k * RX);
+                    pull_inner<S, R, true, kStream>(pk, strip_left(I, xt + k * RX), strip_right(I, xt + k * RX), I,
+                                                    g[k], pol);
+                }
             }
         } else {
 #pragma unroll
@@ -279,15 +298,48 @@ __device__ __forceinline__ void lattice_tile(const Inst &I, S *__restrict__ pool
     if (!valid[0]) return;  // the thread's other cells (further along its column or row) are invalid too
     if (!early_load) pull();
     const bool forced = any != 0u || body_forced<R>(I);
+    // stores of the thread's cells (k < CY); x-adjacent pairs in one access
+    // per plane when both are in the lattice
+    auto store = [&]() {
+        if constexpr (kAdj) {
+            S *q = Adst + (y[0] * kRowStride + cx0);
+            if (valid[1]) put_adj<S, kStream>(q, g[0], g[1], pol);
+            else put_at<S, R, true, kStream>(q, I, g[0], pol);
+        } else {
+#pragma unroll
+            for (int k = 0; k < CY; ++k)
+                if (valid[k])
+                    put_at<S, R, true, kStream>(Adst + (kInner ? y[k] * kRowStride + cx0 + k * RX : C[k].o), I,
+                                                g[k], pol);
+        }
+    };
+    if constexpr (CY == 2 && std::is_same<R, float>::value) {
+        // two unforced cells: the two-relaxation-time collision on both at
+        // once, in packed FP32 pairs (each lane rounds as a lone cell does)
+        if (valid[1] && !moment_form<kColl>(I, forced)) {
+            R Fx, Fy, s_e, s_eps, s_nu[2], s_q[2];
+#pragma unroll
+            for (int k = 0; k < 2; ++k)
+                cell_overlay<R, kStream>(I, tab, sov, m, W, any, x + k * RX, y[k], Fx, Fy, s_nu[k], s_e, s_eps,
+                                         s_q[k]);
+            float2 v[9];
+#pragma unroll
+            for (int q = 0; q < 9; ++q) v[q] = make_float2(g[0][q], g[1][q]);
+            collide_trt<R, Store<S>::kScaled>(v, make_float2(s_nu[0], s_nu[1]), make_float2(s_q[0], s_q[1]), I);
+#pragma unroll
+            for (int q = 0; q < 9; ++q) g[0][q] = v[q].x, g[1][q] = v[q].y;
+            store();
+            return;
+        }
+    }
 #pragma unroll
     for (int k = 0; k < CY; ++k) {
         if (!valid[k]) continue;
         R Fx, Fy, s_nu, s_e, s_eps, s_q;
         cell_overlay<R, kStream>(I, tab, sov, m, W, any, x + k * RX, y[k], Fx, Fy, s_nu, s_e, s_eps, s_q);
         collide_cell<S, R, kColl>(I, g[k], Fx, Fy, s_nu, s_e, s_eps, s_q, forced);
-        put_at<S, R, true, kStream>(Adst + (kInner ? y[k] * kRowStride + cx0 + k * RX : C[k].o), I, g[k],
-                                    pol);
     }
+    store();
 }
 
 // Tile order of a single-lattice sweep.  Every other step takes the tiles
@@ -315,13 +367,13 @@ __global__ void __launch_bounds__(kTileX *kTileY / CY)
 // by << 16 | bx).  Each instance reads table and layout of its own parity
 // (global parity ^ par_xor); the record is copied to shared memory per CTA.
 // Resident CTAs per SM the batched sweep is compiled for: one cell per
-// thread in the reduced-precision paths fits the precomputed pull offsets in
+// thread in the reduced-precision paths fits the in-strip pull offsets in
 // 32 registers (8 CTAs of 256 threads); the other shapes keep the register
 // counts they had without a bound.
 template <class S, int CY> struct BatchMinBlocks {
     static constexpr int value = std::is_same<S, double>::value ? 4 : (CY == 1 ? 8 : 7);
 };
-// Which batched shapes use the precomputed pull offsets.
+// Which batched shapes use the in-strip pull offsets of inner tiles.
 template <class S, int CY, bool kAlongX> struct BatchInner {
     static constexpr bool value = (CY == 1 || kAlongX) && !std::is_same<S, double>::value;
 };

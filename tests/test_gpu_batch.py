@@ -182,8 +182,9 @@ def test_batch_vector_variant(fpd, precision, tol):
 
 @pytest.mark.parametrize("precision,tol", [(0, 1e-13), (1, 1e-5), (2, 1e-2)])
 def test_batch_two_cells_along_x(fpd, precision, tol):
-    # variant 1 in a batch (two cells 16 apart along x per thread, precomputed
-    # pull offsets in inner tiles in the reduced precisions): each instance
+    # variant 1 in a batch (two cells along x per thread, adjacent with paired
+    # accesses in the reduced precisions, in-strip pull offsets in inner
+    # tiles): each instance
     # agrees with the instance alone to rounding
     cases = _cases(precision) + [wl.couette_only(100, 72, u=0.01, nu=0.2, precision=precision)]
     steps = [41, 60, 17, 33, 25]

@@ -312,8 +312,8 @@ def test_graph_chunks_equal_direct_steps(precision):
 @pytest.mark.parametrize("variant", [1, 2])
 @pytest.mark.parametrize("precision,tol", [(0, 1e-13), (1, 1e-5), (2, 1e-2)])
 def test_sweep_variants_agree(precision, tol, variant):
-    # the autotuner's launch shapes (1 cell per thread, 2 cells 16 apart
-    # along x, or a vector of cells along x) compute the same arithmetic; the compiler may
+    # the autotuner's launch shapes (1 cell per thread, 2 cells along x, or
+    # a vector of cells along x) compute the same arithmetic; the compiler may
     # contract multiply-adds differently in each instantiation, so they
     # agree to rounding, not bit for bit.  nx = 76: a multiple of the vector
     # width whose last tile is 12 cells wide; ny = 45: ragged rows too
@@ -380,7 +380,8 @@ def test_vector_sweep_fp64_parity(seed, nx, ny, N, NF, a, xi, coll):
     (45, 7, 9, 3, 1, 1.0, 0.5, 0),      # narrower than the 16-column split
 ])
 def test_two_cells_along_x_fp64_parity(seed, nx, ny, N, NF, a, xi, coll):
-    # variant 1: each thread owns the cells x and x + 16 of one tile row
+    # variant 1: each thread owns two cells of one tile row (x and x + 16 in
+    # FP64)
     rng = np.random.default_rng(seed)
     cfg = wl.random_fiber(rng, nx, ny, n_beads=N, a=a, xi=xi, n_fibers=NF, collision=coll,
                           gx=float(rng.uniform(-1e-6, 1e-6)))
@@ -390,6 +391,38 @@ def test_two_cells_along_x_fp64_parity(seed, nx, ny, N, NF, a, xi, coll):
     g.step(301)
     o.step(301)
     compare_f64(g, o)
+
+
+@pytest.mark.parametrize("precision,tol", [(1, 1e-4), (2, 1e-2)])
+@pytest.mark.parametrize("nx,ny,fiber", [
+    (97, 70, True),    # inner tiles: pairs at both strip edges pull across them
+    (75, 41, True),    # odd width: the last pair of each row holds one cell
+    (130, 28, True),   # five strips, the last two columns wide
+    (7, 9, False),     # one strip, narrower than a tile, periodic wrap inside the pairs
+])
+def test_adjacent_pairs_reduced_precision_against_oracle(precision, tol, nx, ny, fiber):
+    # variant 1 in FP32 and FP16 storage: each thread owns two x-adjacent
+    # cells, moved with paired accesses, their unforced collision in packed
+    # FP32 pairs; against the oracle on ragged lattices
+    rng = np.random.default_rng(1000 * nx + ny)
+    if fiber:
+        cfg = wl.random_fiber(rng, nx, ny, n_beads=4, a=2.0, xi=1.0, precision=precision,
+                              gx=float(rng.uniform(-1e-6, 1e-6)))
+    else:
+        cfg = wl.couette_only(nx, ny, u=0.01, nu=0.15, init_couette=0, precision=precision)
+    g = gpu_sim(cfg)
+    g.set_tuning(1)
+    o = orc_sim(cfg)
+    g.step(301)
+    o.step(301)
+    ux, uy, _ = g.fields()
+    oux, ouy, _ = o.fields()
+    e = rel_l2(np.stack([ux, uy]), np.stack([oux, ouy]), floor=1e-4 * np.sqrt(2 * ux.size))
+    print(f"variant 1, precision {precision}, {nx} x {ny}: rel L2 u {e:.2e}")
+    assert e < tol
+    if fiber:
+        R, oR = g.beads()[0], o.beads()[0]
+        assert rel_l2(R, oR) < tol
 
 
 def test_vector_sweep_tiny_lattices():

@@ -80,8 +80,8 @@ def two_fiber_oracle_64():
 @pytest.mark.parametrize("precision", [0, 1, 2])
 def test_timed_launch_shapes_against_oracle_at_full_size(fpd, precision, two_fiber_oracle_64, monkeypatch):
     # the configuration the benchmark times: 4096 x 1024, two fibers, sweep
-    # variant 1 (two cells per thread 16 apart along x, precomputed pull
-    # offsets, tile order reversed every other step, early update of
+    # variant 1 (two adjacent cells per thread along x, paired accesses and
+    # packed FP32 collision, tile order reversed every other step, early update of
     # unmarked tiles, approximate 1/rho in FP32) and whatever variant the
     # autotuner picks; 64 steps run as 1 direct step + a 32-step captured
     # chunk + 31 direct steps, or all direct (no graphs)
