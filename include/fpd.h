@@ -169,9 +169,15 @@ int fpd_sync(fpd_sim *s);
  *   FPD_FLAG_NONFINITE: a non-finite bead velocity, or a non-finite
  *     population found by the watchdog, a pass over the populations that
  *     runs whenever the step count crosses a multiple of 1024.  fpd_sync and
- *     the calls that synchronise then return FPD_ENAN. */
+ *     the calls that synchronise then return FPD_ENAN.
+ *   FPD_FLAG_COPY_TIMEOUT: a CTA of the staged sweep (tuning variants 3
+ *     and 4) waited 0.1 s for the bulk copy of its block into shared memory
+ *     without seeing it complete, and left that block's cells unwritten for
+ *     the step; fpd_sync and the calls that synchronise then return
+ *     FPD_ECUDA. */
 #define FPD_FLAG_FAST_BEAD 1u
 #define FPD_FLAG_NONFINITE 2u
+#define FPD_FLAG_COPY_TIMEOUT 4u
 
 /* Synchronise and copy the status bits of s into *flags (no error for a
  * set bit).  FPD_EINVAL for a NULL argument. */
@@ -300,7 +306,11 @@ int fpd_internal_flow(fpd_sim *s, double *eps);
  * threads), variant 2 with 2 (FP64) or 4 (FP32, FP16 storage) consecutive
  * cells per thread along x, each plane moved with one 16-byte (8-byte for
  * FP16) access; variant 2 needs nx to be a multiple of that width, and an
- * instance whose nx is not runs variant 0 instead.  Chosen per workload by
+ * instance whose nx is not runs variant 0 instead.  Variants 3 and 4 run
+ * variant 1's threads on blocks of 2 or 4 (FP32 storage) or 4 or 8 (FP16
+ * storage) tiles stacked in y, whose populations one bulk copy per block
+ * stages in shared memory; FP64 storage and batches run variant 1 for
+ * them.  Chosen per workload by
  * an autotuner that times them.  fpd_set_tuning synchronises and drops
  * captured step graphs; FPD_EINVAL for an unknown variant.  fpd_get_tuning:
  * current variant and count. */

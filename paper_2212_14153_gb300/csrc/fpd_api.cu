@@ -341,7 +341,7 @@ int enqueue_step(fpd_sim *s, cudaStream_t st, int64_t t, bool profiled) {
     // from step 1 on, the previous bead phase (or the initial marks) is in
     // the previous buffer
     const fpd::SweepMasks mk{s->masks[t % M], s->masks[(t + M - 1) % M], s->masks[(t + 1) % M],
-                             (t >= 1 && s->early_cold) ? 1 : 0};
+                             (t >= 1 && s->early_cold) ? 1 : 0, s->status};
     e = fpd::launch_lattice(s->precision, s->inst_d, I, s->pool, s->tab[parity], mk, parity, after_beads,
                             s->variant, st);
     if (e != cudaSuccess) return cuda_fail(s, e, "lattice kernel launch");
@@ -548,6 +548,7 @@ int create_impl(const fpd_params *p, void *stream, void *workspace, uint64_t wor
             return code;                                    \
         }                                                   \
     } while (0)
+    FPD_TRY(fpd::prepare_lattice_kernels(), "sweep kernel attributes");
     const StateLayout L = state_layout(I, s->elem);
     if (workspace) {
         if (workspace_bytes < L.total || ((uintptr_t)workspace % kStateAlign) != 0) {
@@ -682,6 +683,8 @@ int fpd_sync(fpd_sim *s) {
     if (e != cudaSuccess) return cuda_fail(s, e, "read status");
     if (flags & fpd::kFlagNonFinite)
         return fail(s, FPD_ENAN, "non-finite state found by step %lld (FPD_FLAG_NONFINITE)", (long long)s->nstep);
+    if (flags & fpd::kFlagCopyTimeout)
+        return fail(s, FPD_ECUDA, "a staged sweep's bulk copy did not complete (FPD_FLAG_COPY_TIMEOUT)");
     return FPD_OK;
 }
 

@@ -34,6 +34,7 @@ struct SweepMasks {
     const unsigned *prev;  // the previous bead phase's marks
     unsigned *clear;       // zeroed for the next bead phase
     int early_cold;
+    unsigned *status = nullptr;  // the instance's status word (staged sweep)
 };
 
 // Sticky per-instance status bits, set on the device (values of the
@@ -43,9 +44,11 @@ struct SweepMasks {
 // instance, so that no sweep updates a tile early any more (that path
 // assumes a bead moves less than a cell per step).  kFlagNonFinite: a
 // non-finite bead velocity, or a non-finite population found by the
-// watchdog.
+// watchdog.  kFlagCopyTimeout: a CTA of the staged sweep gave up waiting
+// for the bulk copy of its block (bounded wait) and left the block unwritten.
 constexpr unsigned kFlagFastBead = 1u;
 constexpr unsigned kFlagNonFinite = 2u;
+constexpr unsigned kFlagCopyTimeout = 4u;
 constexpr double kFastBead = 0.5;
 // Steps between two watchdog passes over the populations (a multiple of
 // kGraphSteps, so that the passes fall between captured chunks).
@@ -61,8 +64,15 @@ constexpr int kWatchSteps = 1024;
 // thread along x, adjacent (FP32, FP16 storage) or 16 apart (FP64) (16 x 8
 // threads), 2 = lattice_vec_width(precision) cells per
 // thread along x with vector loads and stores ((32 / width) x 8 threads;
-// needs nx % width == 0, otherwise variant 0 runs); same tiles, same results.
-constexpr int kLatticeVariants = 3;
+// needs nx % width == 0, otherwise variant 0 runs), 3 and 4 = variant 1's
+// threads on blocks of 2 or 4 (FP32) / 4 or 8 (FP16) tiles stacked in y,
+// whose populations a bulk copy stages in shared memory (FP32 and FP16
+// storage with masks.status set; otherwise, and in batches, variant 1
+// runs); same tiles, same results.
+constexpr int kLatticeVariants = 5;
+// Kernel attributes of the staged sweep on the current device (once per
+// instance creation, outside any stream capture).
+cudaError_t prepare_lattice_kernels();
 inline int lattice_vec_width(int precision) { return precision == 0 ? 2 : 4; }
 cudaError_t launch_lattice(int precision, const Inst *inst_d, const Inst &inst_h, void *pool, BeadTab tab,
                            const SweepMasks &masks, int parity, int after_beads, int variant, cudaStream_t st);

@@ -216,6 +216,65 @@ __device__ __forceinline__ bool tile_cold_early(const unsigned *__restrict__ pre
 // the FP64 path places them kTileX / 2 apart.
 template <class S> struct AdjPairs { static constexpr bool value = !std::is_same<S, double>::value; };
 
+// Second half of a tile's update for a thread's CY cells: the fields of
+// Eqs. 1, 2, 4 at each cell, the collision (the two-relaxation-time form of
+// two unforced cells in packed FP32 pairs, else cell by cell) and the stores
+// into buffer Adst.  g holds the pulled populations in stored units; the
+// cells' layout is lattice_tile's (kAlongX, CY, kAdj).
+template <class S, int CY, bool kInner, bool kAlongX, int kColl, bool kStream>
+__device__ __forceinline__ void finish_cells(const Inst &I, const BeadTab &tab, const float *__restrict__ sov,
+                                             const unsigned *__restrict__ m, const int W, const unsigned any,
+                                             const int x, const int (&y)[CY], const bool (&valid)[CY],
+                                             const Cell (&C)[CY], typename Real<S>::type (&g)[CY][9],
+                                             S *__restrict__ Adst, const int cx0, const uint64_t pol) {
+    using R = typename Real<S>::type;
+    constexpr bool kAdj = kAlongX && CY == 2 && AdjPairs<S>::value;
+    constexpr int RX = kAlongX ? (kAdj ? 1 : kTileX / CY) : 0;
+    const bool forced = any != 0u || body_forced<R>(I);
+    // stores of the thread's cells (k < CY); x-adjacent pairs in one access
+    // per plane when both are in the lattice
+    auto store = [&]() {
+        if constexpr (kAdj) {
+            S *q = Adst + (y[0] * kRowStride + cx0);
+            if (valid[1]) put_adj<S, kStream>(q, g[0], g[1], pol);
+            else put_at<S, R, true, kStream>(q, I, g[0], pol);
+        } else {
+#pragma unroll
+            for (int k = 0; k < CY; ++k)
+                if (valid[k])
+                    put_at<S, R, true, kStream>(Adst + (kInner ? y[k] * kRowStride + cx0 + k * RX : C[k].o), I,
+                                                g[k], pol);
+        }
+    };
+    if constexpr (CY == 2 && std::is_same<R, float>::value) {
+        // two unforced cells: the two-relaxation-time collision on both at
+        // once, in packed FP32 pairs (each lane rounds as a lone cell does)
+        if (valid[1] && !moment_form<kColl>(I, forced)) {
+            R Fx, Fy, s_e, s_eps, s_nu[2], s_q[2];
+#pragma unroll
+            for (int k = 0; k < 2; ++k)
+                cell_overlay<R, kStream>(I, tab, sov, m, W, any, x + k * RX, y[k], Fx, Fy, s_nu[k], s_e, s_eps,
+                                         s_q[k]);
+            float2 v[9];
+#pragma unroll
+            for (int q = 0; q < 9; ++q) v[q] = make_float2(g[0][q], g[1][q]);
+            collide_trt<R, Store<S>::kScaled>(v, make_float2(s_nu[0], s_nu[1]), make_float2(s_q[0], s_q[1]), I);
+#pragma unroll
+            for (int q = 0; q < 9; ++q) g[0][q] = v[q].x, g[1][q] = v[q].y;
+            store();
+            return;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < CY; ++k) {
+        if (!valid[k]) continue;
+        R Fx, Fy, s_nu, s_e, s_eps, s_q;
+        cell_overlay<R, kStream>(I, tab, sov, m, W, any, x + k * RX, y[k], Fx, Fy, s_nu, s_e, s_eps, s_q);
+        collide_cell<S, R, kColl>(I, g[k], Fx, Fy, s_nu, s_e, s_eps, s_q, forced);
+    }
+    store();
+}
+
 // One tile of the sweep: tile (bx, by) of instance I at the instance's step
 // parity, on kTileX x (kTileY / CY) threads; thread (tx, ty) owns the CY
 // cells (x, y0 + ty + k kTileY / CY), k < CY, of its column.  kAlongX: on
@@ -297,49 +356,7 @@ __device__ __forceinline__ void lattice_tile(const Inst &I, S *__restrict__ pool
     const float *sov = stage_overlay<R, kStream>(I, tab, m, any);  // every thread of the CTA
     if (!valid[0]) return;  // the thread's other cells (further along its column or row) are invalid too
     if (!early_load) pull();
-    const bool forced = any != 0u || body_forced<R>(I);
-    // stores of the thread's cells (k < CY); x-adjacent pairs in one access
-    // per plane when both are in the lattice
-    auto store = [&]() {
-        if constexpr (kAdj) {
-            S *q = Adst + (y[0] * kRowStride + cx0);
-            if (valid[1]) put_adj<S, kStream>(q, g[0], g[1], pol);
-            else put_at<S, R, true, kStream>(q, I, g[0], pol);
-        } else {
-#pragma unroll
-            for (int k = 0; k < CY; ++k)
-                if (valid[k])
-                    put_at<S, R, true, kStream>(Adst + (kInner ? y[k] * kRowStride + cx0 + k * RX : C[k].o), I,
-                                                g[k], pol);
-        }
-    };
-    if constexpr (CY == 2 && std::is_same<R, float>::value) {
-        // two unforced cells: the two-relaxation-time collision on both at
-        // once, in packed FP32 pairs (each lane rounds as a lone cell does)
-        if (valid[1] && !moment_form<kColl>(I, forced)) {
-            R Fx, Fy, s_e, s_eps, s_nu[2], s_q[2];
-#pragma unroll
-            for (int k = 0; k < 2; ++k)
-                cell_overlay<R, kStream>(I, tab, sov, m, W, any, x + k * RX, y[k], Fx, Fy, s_nu[k], s_e, s_eps,
-                                         s_q[k]);
-            float2 v[9];
-#pragma unroll
-            for (int q = 0; q < 9; ++q) v[q] = make_float2(g[0][q], g[1][q]);
-            collide_trt<R, Store<S>::kScaled>(v, make_float2(s_nu[0], s_nu[1]), make_float2(s_q[0], s_q[1]), I);
-#pragma unroll
-            for (int q = 0; q < 9; ++q) g[0][q] = v[q].x, g[1][q] = v[q].y;
-            store();
-            return;
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < CY; ++k) {
-        if (!valid[k]) continue;
-        R Fx, Fy, s_nu, s_e, s_eps, s_q;
-        cell_overlay<R, kStream>(I, tab, sov, m, W, any, x + k * RX, y[k], Fx, Fy, s_nu, s_e, s_eps, s_q);
-        collide_cell<S, R, kColl>(I, g[k], Fx, Fy, s_nu, s_e, s_eps, s_q, forced);
-    }
-    store();
+    finish_cells<S, CY, kInner, kAlongX, kColl, kStream>(I, tab, sov, m, W, any, x, y, valid, C, g, Adst, cx0, pol);
 }
 
 // Tile order of a single-lattice sweep.  Every other step takes the tiles
@@ -361,6 +378,215 @@ __global__ void __launch_bounds__(kTileX *kTileY / CY)
                                        tile_order(blockIdx.x, gridDim.x, parity),
                                        tile_order(blockIdx.y, gridDim.y, parity), parity, early_load, early_cold,
                                        (blockIdx.x | blockIdx.y) == 0, threadIdx.x, threadIdx.y);
+}
+
+// --------------------------------------------- staged sweep (variants 3, 4)
+// A CTA of kTileX / 2 x kTileY threads updates NS tiles stacked in y (a
+// block of 32 x 8 NS cells, one strip wide).  Its populations and their y
+// halo, rows y0 - 1 .. y0 + 8 NS of the strip, are contiguous in the
+// current buffer (the strip layout), so one elected thread moves all of them
+// into shared memory with a single bulk copy (cp.async.bulk, completion on
+// an mbarrier) the moment the CTA starts; the x halo (column 31 of the
+// strip to the left for the three directions with c_kx = +1, column 0 of
+// the one to the right for c_kx = -1) comes with plain loads.  The copy
+// engine keeps a whole block in flight per CTA without holding registers,
+// where the register-fed pull of variant 1 keeps 36 B (FP16) or 72 B (FP32)
+// a thread in flight.  Each thread then pulls its two x-adjacent cells of
+// every tile from shared memory and runs the same collision and stores as
+// variant 1 (finish_cells), so the results are bit-identical to it.  Tiles
+// the previous bead phase left unmarked are updated first, without waiting
+// for this step's bead phase; the others after it.  Blocks at a wall, at the
+// periodic edges or at the lattice's ragged end run variant 1's tile code.
+// Every wait on the copy is bounded: a copy that has not completed within
+// kCopyWaitNs sets kFlagCopyTimeout in the instance's status word and the
+// CTA leaves its block unwritten (reported by fpd_sync).
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+// makes the initialised barrier visible to the copy engine (async proxy)
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// bytes (a multiple of 16) from global src to shared dst, both 16-byte
+// aligned, completing as transaction bytes on bar; L2 policy pol
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar,
+                                         uint64_t pol) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_test(unsigned long long *bar, unsigned phase) {
+    unsigned done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    return done != 0u;
+}
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Wait for phase `phase` of bar to complete, for at most kCopyWaitNs (and a
+// bounded number of polls); false when it did not.
+constexpr unsigned long long kCopyWaitNs = 100000000ull;  // 0.1 s
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned phase) {
+    if (mbar_test(bar, phase)) return true;
+    const unsigned long long t0 = globaltimer_ns();
+    for (unsigned i = 0; i < (1u << 24); ++i) {
+        if (mbar_test(bar, phase)) return true;
+        if (globaltimer_ns() - t0 > kCopyWaitNs) break;
+    }
+    return false;
+}
+
+// x-halo slot of the directions with c_kx != 0: 0..2 for k = 1, 5, 8
+// (column 31 of the strip to the left), 3..5 for k = 3, 6, 7 (column 0 of
+// the strip to the right)
+template <int k> struct HaloSlot {
+    static constexpr int value = k == 1 ? 0 : k == 5 ? 1 : k == 8 ? 2 : k == 3 ? 3 : k == 6 ? 4 : 5;
+};
+__device__ __forceinline__ int halo_plane(int j) { return j == 0 ? 1 : j == 1 ? 5 : j == 2 ? 8 : j == 3 ? 3 : j == 4 ? 6 : 7; }
+
+// Pull of direction k for the two x-adjacent cells a (column xt, even) and
+// b = a + 1 of staged row r, p = rows + r kRowStride + xt: the same sources
+// as pull_adj, read from shared memory, with the strip-edge sources from
+// the x halo.
+template <int k, class S>
+__device__ __forceinline__ void pull_staged_one(const S *__restrict__ p, const float (*__restrict__ halo)[6],
+                                                const int r, const int xt, float ga[9], float gb[9]) {
+    constexpr int cx = Q<k>::cx, cy = Q<k>::cy, off = PullOff<k>::value;
+    if constexpr (cx == 0) {
+        Store<S>::ld2_raw(p + off, ga[k], gb[k]);
+    } else if constexpr (cx > 0) {
+        ga[k] = (xt == 0) ? halo[r - cy][HaloSlot<k>::value] : Store<S>::ld_raw(p + off);
+        gb[k] = Store<S>::ld_raw(p + 1 + off);
+    } else {
+        ga[k] = Store<S>::ld_raw(p + off);
+        gb[k] = (xt == kTileX - 2) ? halo[r - cy][HaloSlot<k>::value] : Store<S>::ld_raw(p + 1 + off);
+    }
+}
+template <class S>
+__device__ __forceinline__ void pull_staged(const S *__restrict__ p, const float (*__restrict__ halo)[6], const int r,
+                                            const int xt, float ga[9], float gb[9]) {
+    pull_staged_one<0, S>(p, halo, r, xt, ga, gb);
+    pull_staged_one<2, S>(p, halo, r, xt, ga, gb);
+    pull_staged_one<4, S>(p, halo, r, xt, ga, gb);
+    pull_staged_one<1, S>(p, halo, r, xt, ga, gb);
+    pull_staged_one<5, S>(p, halo, r, xt, ga, gb);
+    pull_staged_one<8, S>(p, halo, r, xt, ga, gb);
+    pull_staged_one<3, S>(p, halo, r, xt, ga, gb);
+    pull_staged_one<6, S>(p, halo, r, xt, ga, gb);
+    pull_staged_one<7, S>(p, halo, r, xt, ga, gb);
+}
+
+// Tiles per CTA of the staged sweep (variant 3: kStagedNS, variant 4: twice
+// that), chosen so that a block's staged rows stay near 20 KB and 40 KB.
+template <class S> struct StagedNS { static constexpr int value = std::is_same<S, __half>::value ? 4 : 2; };
+
+template <class S, int NS>
+__global__ void __launch_bounds__(kTileX *kTileY / 2)
+    k_lattice_staged(const Inst I, S *__restrict__ pool, const BeadTab tab, const unsigned *__restrict__ mask_read,
+                     const unsigned *__restrict__ mask_prev, unsigned *__restrict__ mask_clear, const int parity,
+                     const int early_load, const int early_cold, unsigned *__restrict__ status) {
+    using R = float;
+    constexpr int kThreads = kTileX * kTileY / 2;
+    constexpr int kRows = NS * kTileY + 2;
+    constexpr unsigned kBytes = kRows * kRowStride * sizeof(S);
+    static_assert(kBytes % 16 == 0, "bulk copies move multiples of 16 bytes");
+    __shared__ __align__(128) unsigned char s_raw[kBytes];
+    __shared__ float s_halo[kRows][6];
+    __shared__ __align__(8) unsigned long long s_bar;
+    const int bx = tile_order(blockIdx.x, gridDim.x, parity), bb = tile_order(blockIdx.y, gridDim.y, parity);
+    const bool lead = (blockIdx.x | blockIdx.y) == 0;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * (kTileX / 2) + tx;
+    const int by0 = bb * NS;
+    // the block's cells, their neighbours and the staged rows lie inside the
+    // lattice, away from walls and periodic edges
+    const bool inner = bx > 0 && by0 > 0 && (bx + 1) * kTileX < I.nx && (by0 + NS) * kTileY < I.ny;
+    if (!inner) {
+        for (int s = 0; s < NS && by0 + s < I.nty; ++s) {
+            if (s) __syncthreads();  // the previous tile's cells no longer read the staged overlay
+            lattice_tile<S, 2, true, true, kCollTrt, true>(I, pool, tab, mask_read, mask_prev, mask_clear, bx, by0 + s,
+                                                           parity, early_load, early_cold, lead, tx, ty);
+        }
+        return;
+    }
+    const S *Asrc = pop_buffer(pool, I, parity);
+    S *Adst = pop_buffer(pool, I, parity ^ 1);
+    const int y0 = by0 * kTileY;
+    // row y0 - 1 of the block's strip; its populations come from the previous
+    // sweep, complete before this launch began (the bead phase in between
+    // waited for it), so they are read at once
+    const S *g0 = Asrc + ((y0 - 1) * kRowStride + col_off(I, bx * kTileX));
+    const uint64_t pol = pol_evict_first();
+    if (tid == 0) {
+        mbar_init(&s_bar, 1);
+        fence_mbar_init();
+        mbar_arrive_expect_tx(&s_bar, kBytes);
+        bulk_g2s(s_raw, g0, kBytes, &s_bar, pol);
+    }
+    for (int h = tid; h < kRows * 6; h += kThreads) {
+        const int r = h / 6, j = h - 6 * r;
+        const int col = j < 3 ? kStripW - 1 - I.strip : I.strip;  // from column 0 of the block's strip
+        s_halo[r][j] = Store<S>::ld_stream(g0 + (r * kRowStride + halo_plane(j) * kPlaneStride + col), pol);
+    }
+    const int W = I.mask_words;
+    unsigned cold = 0u;
+#pragma unroll
+    for (int s = 0; s < NS; ++s)
+        if (tile_cold_early(mask_prev + (I.tile_base + (by0 + s) * I.ntx + bx) * W, W, early_cold, lead))
+            cold |= 1u << s;
+    if (tid == 0)  // masks of two steps back, for the next bead phase
+        for (int s = 0; s < NS; ++s)
+            for (int w = 0; w < W; ++w) mask_clear[(I.tile_base + (by0 + s) * I.ntx + bx) * W + w] = 0u;
+    __syncthreads();  // the barrier is initialised, the x halo staged
+    const bool copied = mbar_wait_bounded(&s_bar, 0);
+    if (__syncthreads_or(!copied)) {
+        if (tid == 0 && status) atomicOr(status, kFlagCopyTimeout);
+        if (!copied) mbar_wait_bounded(&s_bar, 0);  // let a late copy land before the CTA ends
+        if (lead) pdl_wait();
+        return;
+    }
+    if (cold == (1u << NS) - 1u) pdl_trigger();
+    const int xt = 2 * tx, x = bx * kTileX + xt, cx0 = col_off(I, x);
+    const S *rows = reinterpret_cast<const S *>(s_raw);
+    bool waited = false;
+    // the unmarked tiles first, then, after this step's bead phase, the rest
+#pragma unroll 1
+    for (int pass = 0; pass < 2; ++pass) {
+#pragma unroll 1
+        for (int s = 0; s < NS; ++s) {
+            const bool c = (cold >> s) & 1u;
+            if (c != (pass == 0)) continue;
+            if (!c && !waited) {
+                pdl_wait();
+                pdl_trigger();
+                waited = true;
+            }
+            const unsigned *m = mask_read + (I.tile_base + (by0 + s) * I.ntx + bx) * W;
+            unsigned any = 0u;
+            if (!c)
+                for (int w = 0; w < W; ++w) any |= m[w];
+            if (any != 0u) __syncthreads();  // the previous tile's cells no longer read the staged overlay
+            const float *sov = stage_overlay<R, true>(I, tab, m, any);
+            const int r = s * kTileY + ty + 1;  // staged row of the thread's cells
+            const int y[2] = {y0 + r - 1, y0 + r - 1};
+            const bool valid[2] = {true, true};
+            Cell C[2];  // unused: inner cells
+            R g[2][9];
+            pull_staged<S>(rows + (r * kRowStride + xt), s_halo, r, xt, g[0], g[1]);
+            finish_cells<S, 2, true, true, kCollTrt, true>(I, tab, sov, m, W, any, x, y, valid, C, g, Adst, cx0, pol);
+        }
+    }
 }
 
 // Batched sweep over a packed tile list: tiles[t] = (instance slot,
@@ -871,6 +1097,18 @@ static cudaLaunchConfig_t sweep_config(dim3 grid, dim3 block, int after_beads, c
     return cfg;
 }
 
+// The staged sweep on blocks of NS tiles (FP32 / FP16 storage).
+template <class S, int NS>
+static cudaError_t launch_staged(const Inst &I, void *pool, BeadTab tab, const SweepMasks &mk, int parity,
+                                 int after_beads, cudaStream_t st) {
+    cudaLaunchAttribute attr[1];
+    const dim3 grid(I.ntx, (I.nty + NS - 1) / NS);
+    const int ec = after_beads ? mk.early_cold : 0;
+    const cudaLaunchConfig_t cfg = sweep_config(grid, dim3(kTileX / 2, kTileY), after_beads, st, attr);
+    return cudaLaunchKernelEx(&cfg, k_lattice_staged<S, NS>, I, (S *)pool, tab, mk.read, mk.prev, mk.clear, parity,
+                              after_beads, ec, mk.status);
+}
+
 template <class S>
 static cudaError_t lattice_v(int variant, const Inst &I, void *pool, BeadTab tab, const SweepMasks &mk, int parity,
                              int after_beads, cudaStream_t st) {
@@ -889,7 +1127,16 @@ static cudaError_t lattice_v(int variant, const Inst &I, void *pool, BeadTab tab
         return cudaLaunchKernelEx(&cfg, k_lattice_vec<S>, I, (S *)pool, tab, mk.read, mk.prev, mk.clear,
                                   parity, after_beads, ec);
     }
-    if (variant == 1) {
+    if constexpr (AdjPairs<S>::value) {
+        // the bulk copies need the buffers 16-byte aligned (strips and rows
+        // are multiples of 16 bytes long)
+        const bool aligned = (reinterpret_cast<uintptr_t>((S *)pool + I.pop_off) & 15u) == 0;
+        if ((variant == 3 || variant == 4) && mk.status != nullptr && aligned) {
+            if (variant == 3) return launch_staged<S, StagedNS<S>::value>(I, pool, tab, mk, parity, after_beads, st);
+            return launch_staged<S, 2 * StagedNS<S>::value>(I, pool, tab, mk, parity, after_beads, st);
+        }
+    }
+    if (variant == 1 || variant == 3 || variant == 4) {
         const cudaLaunchConfig_t cfg = sweep_config(grid, dim3(kTileX / 2, kTileY), after_beads, st, attr);
         return cudaLaunchKernelEx(&cfg, k_lattice<S, 2, true, kCollTrt>, I, (S *)pool, tab, mk.read, mk.prev,
                                   mk.clear, parity, after_beads, ec);
@@ -897,6 +1144,22 @@ static cudaError_t lattice_v(int variant, const Inst &I, void *pool, BeadTab tab
     const cudaLaunchConfig_t cfg = sweep_config(grid, dim3(kTileX, kTileY), after_beads, st, attr);
     return cudaLaunchKernelEx(&cfg, k_lattice<S, 1, false, kCollTrt>, I, (S *)pool, tab, mk.read, mk.prev,
                               mk.clear, parity, after_beads, ec);
+}
+
+// The staged sweep's CTAs keep 20-46 KB of static shared memory: its
+// kernels prefer the largest shared-memory carveout, so that shared memory
+// does not limit the CTAs per SM before registers do.  Host-side attribute
+// calls on the current device, made before any launch or stream capture.
+cudaError_t prepare_lattice_kernels() {
+    const void *k[] = {(const void *)k_lattice_staged<float, StagedNS<float>::value>,
+                       (const void *)k_lattice_staged<float, 2 * StagedNS<float>::value>,
+                       (const void *)k_lattice_staged<__half, StagedNS<__half>::value>,
+                       (const void *)k_lattice_staged<__half, 2 * StagedNS<__half>::value>};
+    for (const void *f : k) {
+        const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_lattice(int precision, const Inst *, const Inst &inst_h, void *pool, BeadTab tab,
@@ -929,7 +1192,7 @@ static cudaError_t lattice_batch_v(int variant, const Inst *insts, const int2 *t
         return cudaLaunchKernelEx(&cfg, k_lattice_batch_vec<S>, insts, tiles, (S *)pool, tab0, tab1, mk.read,
                                   mk.prev, mk.clear, gparity, after_beads, ec);
     }
-    if (variant == 1) {
+    if (variant == 1 || variant == 3 || variant == 4) {  // the staged blocks are single-lattice only
         const cudaLaunchConfig_t cfg = sweep_config(grid, dim3(kTileX / 2, kTileY), after_beads, st, attr);
         return cudaLaunchKernelEx(&cfg, k_lattice_batch<S, 2, true, kCollTrt>, insts, tiles, (S *)pool, tab0, tab1,
                                   mk.read, mk.prev, mk.clear, gparity, after_beads, ec);

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "libfpd.so")
 FPD_OK, FPD_EINVAL, FPD_ENOMEM, FPD_ECUDA, FPD_ETIMEOUT, FPD_ENAN, FPD_EBUSY = 0, -1, -2, -3, -4, -5, -6
 FPD_F64, FPD_F32, FPD_F32_F16STORE = 0, 1, 2
 FPD_MRT_MAGIC, FPD_MRT_LL, FPD_BGK = 0, 1, 2
-FPD_FLAG_FAST_BEAD, FPD_FLAG_NONFINITE = 1, 2
+FPD_FLAG_FAST_BEAD, FPD_FLAG_NONFINITE, FPD_FLAG_COPY_TIMEOUT = 1, 2, 4
 SLOT_FREE, SLOT_RUNNING, SLOT_FINISHED, SLOT_FAILED = 0, 1, 2, 3
 
 _DP = ctypes.POINTER(ctypes.c_double)

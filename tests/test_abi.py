@@ -40,7 +40,7 @@ def test_library_exports_every_declared_symbol(lib):
 def test_version_and_defaults(lib):
     from paper_2212_14153_gb300 import fpd
     assert fpd.fpd_version() == 4
-    assert fpd.fpd_sweep_variants() == 3
+    assert fpd.fpd_sweep_variants() == 5
     p = fpd.fpd_default_params()
     assert (p.nx, p.ny, p.u_bottom, p.u_top, p.visc_ratio, p.phi_cut) == (80, 40, -0.01, 0.01, 50.0, 8.0)
     assert p.precision == fpd.FPD_F64 and p.collision == fpd.FPD_MRT_MAGIC

@@ -309,7 +309,7 @@ def test_graph_chunks_equal_direct_steps(precision):
         assert np.array_equal(x, y)
 
 
-@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4])
 @pytest.mark.parametrize("precision,tol", [(0, 1e-13), (1, 1e-5), (2, 1e-2)])
 def test_sweep_variants_agree(precision, tol, variant):
     # the autotuner's launch shapes (1 cell per thread, 2 cells along x, or
@@ -322,7 +322,7 @@ def test_sweep_variants_agree(precision, tol, variant):
     a = gpu_sim(cfg)
     b = gpu_sim(cfg)
     b.set_tuning(variant)
-    assert b.tuning() == (variant, 3)
+    assert b.tuning() == (variant, 5)
     a.step(77)
     b.step(77)
     w = oracle.feq(1.0, 0.0, 0.0)[:, None, None]
@@ -330,6 +330,47 @@ def test_sweep_variants_agree(precision, tol, variant):
     print(f"variant {variant} vs 0, precision {precision}: rel L2 of f - w {e:.2e}")
     assert e < tol
     assert rel_l2(b.beads()[0], a.beads()[0]) < tol * 1e-3
+
+
+@pytest.mark.parametrize("variant", [3, 4])
+@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-4), (2, 1e-2)])
+@pytest.mark.parametrize("nx,ny", [
+    (160, 150),  # inner blocks of 2, 4 and 8 tiles, ragged top rows
+    (203, 282),  # ragged last strip (11 columns), several block rows
+])
+def test_staged_blocks_against_variant1_and_oracle(precision, tol, variant, nx, ny):
+    # variants 3 and 4: blocks of tiles stacked in y whose populations one
+    # bulk copy stages in shared memory, the x halo by plain loads; the same
+    # cells, collision and stores as variant 1 (FP64 storage runs variant 1).
+    # Two fibers that cross inner blocks and block edges; the unmarked tiles
+    # of a block go first, the marked ones after the bead phase
+    rng = np.random.default_rng(7000 * nx + ny + variant)
+    cfg = wl.random_fiber(rng, nx, ny, n_beads=8, a=2.5, xi=1.0, n_fibers=2, precision=precision,
+                          gx=float(rng.uniform(-1e-6, 1e-6)))
+    a = gpu_sim(cfg)
+    a.set_tuning(1)
+    b = gpu_sim(cfg)
+    b.set_tuning(variant)
+    assert b.tuning() == (variant, 5)
+    o = orc_sim(cfg)
+    for n in (1, 32, 67):  # a direct step, a captured chunk, direct steps
+        a.step(n)
+        b.step(n)
+        o.step(n)
+    b.sync()
+    assert b.flags() == 0
+    w = oracle.feq(1.0, 0.0, 0.0)[:, None, None]
+    pa, pb = a.populations(), b.populations()
+    e = rel_l2(pb - w, pa - w)
+    print(f"variant {variant} vs 1, precision {precision}, {nx} x {ny}: rel L2 of f - w {e:.2e}, "
+          f"bit-identical {np.array_equal(pa, pb)}")
+    assert e < {0: 1e-13, 1: 1e-5, 2: 1e-2}[precision]
+    ux, uy, _ = b.fields()
+    oux, ouy, _ = o.fields()
+    eu = rel_l2(np.stack([ux, uy]), np.stack([oux, ouy]), floor=1e-4 * np.sqrt(2 * ux.size))
+    eR = rel_l2(b.beads()[0], o.beads()[0])
+    print(f"  vs oracle: rel L2 u {eu:.2e}, R {eR:.2e}")
+    assert eu < tol and eR < {0: 1e-12, 1: 1e-6, 2: 1e-4}[precision]
 
 
 def test_auto_tuning_picks_a_measured_variant_and_caches_it(tmp_path, monkeypatch):
