@@ -341,7 +341,7 @@ int enqueue_step(fpd_sim *s, cudaStream_t st, int64_t t, bool profiled) {
     // from step 1 on, the previous bead phase (or the initial marks) is in
     // the previous buffer
     const fpd::SweepMasks mk{s->masks[t % M], s->masks[(t + M - 1) % M], s->masks[(t + 1) % M],
-                             (t >= 1 && s->early_cold) ? 1 : 0, s->status};
+                             (t >= 1 && s->early_cold) ? 1 : 0, s->status, s->copy_shortfall};
     e = fpd::launch_lattice(s->precision, s->inst_d, I, s->pool, s->tab[parity], mk, parity, after_beads,
                             s->variant, st);
     if (e != cudaSuccess) return cuda_fail(s, e, "lattice kernel launch");
@@ -533,6 +533,8 @@ int create_impl(const fpd_params *p, void *stream, void *workspace, uint64_t wor
         s->use_graphs = !(ng && ng[0] == '1');
         const char *ne = std::getenv("FPD_NO_EARLY_COLD");
         s->early_cold = !(ne && ne[0] == '1');
+        const char *cs = std::getenv("FPD_TEST_COPY_SHORTFALL");
+        s->copy_shortfall = (cs && cs[0] == '1') ? 16u : 0u;
     }
     const fpd::Inst &I = s->inst;
     const int nb = I.nb;

@@ -35,6 +35,7 @@ struct SweepMasks {
     unsigned *clear;       // zeroed for the next bead phase
     int early_cold;
     unsigned *status = nullptr;  // the instance's status word (staged sweep)
+    unsigned copy_shortfall = 0;  // test only: extra bytes the staged copies expect (their waits run out)
 };
 
 // Sticky per-instance status bits, set on the device (values of the

@@ -496,7 +496,8 @@ template <class S, int NS>
 __global__ void __launch_bounds__(kTileX *kTileY / 2)
     k_lattice_staged(const Inst I, S *__restrict__ pool, const BeadTab tab, const unsigned *__restrict__ mask_read,
                      const unsigned *__restrict__ mask_prev, unsigned *__restrict__ mask_clear, const int parity,
-                     const int early_load, const int early_cold, unsigned *__restrict__ status) {
+                     const int early_load, const int early_cold, unsigned *__restrict__ status,
+                     const unsigned shortfall) {
     using R = float;
     constexpr int kThreads = kTileX * kTileY / 2;
     constexpr int kRows = NS * kTileY + 2;
@@ -531,7 +532,7 @@ __global__ void __launch_bounds__(kTileX *kTileY / 2)
     if (tid == 0) {
         mbar_init(&s_bar, 1);
         fence_mbar_init();
-        mbar_arrive_expect_tx(&s_bar, kBytes);
+        mbar_arrive_expect_tx(&s_bar, kBytes + shortfall);  // shortfall: 0 but in a failure test
         bulk_g2s(s_raw, g0, kBytes, &s_bar, pol);
     }
     for (int h = tid; h < kRows * 6; h += kThreads) {
@@ -1106,7 +1107,7 @@ static cudaError_t launch_staged(const Inst &I, void *pool, BeadTab tab, const S
     const int ec = after_beads ? mk.early_cold : 0;
     const cudaLaunchConfig_t cfg = sweep_config(grid, dim3(kTileX / 2, kTileY), after_beads, st, attr);
     return cudaLaunchKernelEx(&cfg, k_lattice_staged<S, NS>, I, (S *)pool, tab, mk.read, mk.prev, mk.clear, parity,
-                              after_beads, ec, mk.status);
+                              after_beads, ec, mk.status, mk.copy_shortfall);
 }
 
 template <class S>

@@ -54,6 +54,10 @@ struct fpd_sim {
     unsigned long long *ex_count = nullptr;
     int64_t ex_first = 0;
     bool early_cold = true;  // unmarked tiles update before the bead phase ends (same results)
+    // bytes the staged sweep's copies are told to expect beyond what they
+    // move (FPD_TEST_COPY_SHORTFALL=1: 16), so that its bounded wait runs
+    // out in a failure-handling test; 0 otherwise
+    unsigned copy_shortfall = 0;
     int64_t watch_next = fpd::kWatchSteps;  // step count at which the next watchdog pass runs
     int variant = 0;  // lattice sweep variant (see launch_lattice)
     cudaStream_t cap_stream = nullptr;

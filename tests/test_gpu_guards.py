@@ -8,6 +8,9 @@
   bead driven past 0.5 cells per step sets FPD_FLAG_FAST_BEAD and from then
   on every tile waits, so the run equals one with the early path off.
 - The watchdog: a diverged single instance is reported by fpd_sync.
+- The staged sweep's bounded wait on its bulk copy: a barrier made to
+  expect more bytes than arrive is given up on, flagged and reported, and
+  the context stays usable.
 """
 import math
 import os
@@ -158,3 +161,35 @@ def test_watchdog_reports_a_diverged_instance_at_sync(fpd, precision):
     good.step(1100)
     good.sync()
     assert good.flags() == 0
+
+
+# ------------------------------------------------- staged sweep: bounded wait
+@pytest.mark.parametrize("precision", [1, 2])
+def test_staged_copy_wait_runs_out_and_is_reported(fpd, precision, monkeypatch):
+    # the staged sweep (variant 3) waits a bounded time for the bulk copy of
+    # its block.  FPD_TEST_COPY_SHORTFALL=1 has each block's barrier expect
+    # 16 bytes more than its copy moves, so no wait can complete (the copy
+    # itself lands, nothing faults): every CTA of an inner block gives up
+    # after 0.1 s, sets FPD_FLAG_COPY_TIMEOUT and ends, and fpd_sync reports
+    # FPD_ECUDA.  The context stays usable: fresh instances then run the
+    # staged sweep bit for bit like variant 1
+    rng = np.random.default_rng(4242 + precision)
+    cfg = wl.random_fiber(rng, 160, 150, n_beads=8, a=2.5, xi=1.0, precision=precision)
+    monkeypatch.setenv("FPD_TEST_COPY_SHORTFALL", "1")
+    bad = fpd.Simulation(cfg)
+    monkeypatch.delenv("FPD_TEST_COPY_SHORTFALL")
+    bad.set_tuning(3)
+    bad.step(1)
+    assert bad.flags() & fpd.FPD_FLAG_COPY_TIMEOUT
+    with pytest.raises(fpd.FpdError) as e:
+        bad.sync()
+    assert e.value.code == fpd.FPD_ECUDA
+    bad.close()
+    a, b = fpd.Simulation(cfg), fpd.Simulation(cfg)
+    a.set_tuning(3)
+    b.set_tuning(1)
+    a.step(40)
+    b.step(40)
+    a.sync()
+    assert a.flags() == 0
+    assert np.array_equal(a.populations(), b.populations())
