@@ -118,7 +118,15 @@ void fpd_default_params(fpd_params *p);
  * (R_i = c + (i - (N+1)/2) l_0 (cos theta, sin theta), i = 1..N, Sec. 4.1:
  * fiber centred) and compute the first bead table.  stream: a cudaStream_t
  * or NULL.  On success *out owns the state.  Errors: FPD_EINVAL (bad
- * parameter, message names it), FPD_ENOMEM, FPD_ECUDA. */
+ * parameter, message names it), FPD_ENOMEM, FPD_ECUDA.
+ * Environment read here (for the life of the instance; none changes a
+ * result unless stated): FPD_NO_GRAPHS=1 launches every kernel directly
+ * instead of replaying captured step chunks; FPD_NO_EARLY_COLD=1 makes
+ * every tile of every sweep wait for its step's bead phase; for tests only,
+ * FPD_TEST_COPY_SHORTFALL=1 has each staged-sweep block (tuning variants 3
+ * and 4) expect 16 bytes more than its bulk copy moves, so that its
+ * bounded wait runs out: those blocks are left unwritten and
+ * FPD_FLAG_COPY_TIMEOUT is set. */
 int fpd_create(const fpd_params *p, void *stream, fpd_sim **out);
 
 /* Device bytes of the state of one instance with parameters p (populations,
