@@ -669,11 +669,21 @@ __global__ void __launch_bounds__(NT, BeadMinBlocks<S, NT>::value)
     // the instance's status bits as earlier phases left them
     if (tid == 0) s_stold = (status && advance) ? __ldcg(status + ii) : 0u;
     // stage the instance's new positions and support sums (written by every
-    // CTA; the L2-coherent loads see them), then every segment once
+    // CTA; the L2-coherent loads see them), then every segment once.  The
+    // fast-bead guard below tests this phase's velocities: they are loaded in
+    // the same round of loads, so that the guard adds no memory round trip
+    // to the phase's last CTA
+    const bool guard = status && advance;
+    bool fast = false, bad = false;
     for (int q = tid; q < I.nb; q += blockDim.x) {
         s_rx[q] = __ldcg(tnew.Rx + I.bead_off + q);
         s_ry[q] = __ldcg(tnew.Ry + I.bead_off + q);
         s_gx[q] = __ldcg(tnew.S + I.bead_off + q);
+        if (guard) {
+            const double vx = __ldcg(tnew.Vx + I.bead_off + q), vy = __ldcg(tnew.Vy + I.bead_off + q);
+            fast |= !(fabs(vx) < kFastBead && fabs(vy) < kFastBead);
+            bad |= !(isfinite(vx) && isfinite(vy));
+        }
     }
     __syncthreads();
     // fast-bead guard: the early update of unmarked tiles assumes a bead
@@ -681,13 +691,7 @@ __global__ void __launch_bounds__(NT, BeadMinBlocks<S, NT>::value)
     // reaches kFastBead per component (or is not finite), flag the instance;
     // while the flag is set, mark every tile of the instance (bead 0's bit)
     // in this phase's masks, so that the next sweeps wait on all of them
-    if (status && advance) {
-        bool fast = false, bad = false;
-        for (int q = tid; q < I.nb; q += blockDim.x) {
-            const double vx = __ldcg(tnew.Vx + I.bead_off + q), vy = __ldcg(tnew.Vy + I.bead_off + q);
-            fast |= !(fabs(vx) < kFastBead && fabs(vy) < kFastBead);
-            bad |= !(isfinite(vx) && isfinite(vy));
-        }
+    if (guard) {
         const int any_fast = __syncthreads_or(fast);
         const int any_bad = __syncthreads_or(bad);
         if (any_fast && tid == 0) atomicOr(status + ii, kFlagFastBead | (any_bad ? kFlagNonFinite : 0u));
