@@ -349,6 +349,26 @@ __device__ __forceinline__ void lattice_tile(const Inst &I, S *__restrict__ pool
     pdl_trigger();
     if (tx == 0 && ty == 0)  // a mask of two steps back, for the next bead phase
         for (int w = 0; w < W; ++w) mask_clear[tile * W + w] = 0u;
+    if constexpr (kAdj && kInner && kStream && kColl == kCollTrt && std::is_same<S, __half>::value) {
+        // an unmarked tile away from walls and edges, with no body force or
+        // sandwich layer: both cells are unforced at the fluid rates, so
+        // finish_cells would take its packed two-relaxation-time branch with
+        // s_nu and s_q of Phi = 0; the same operations in a straight line
+        // (FP16 storage: step 34.6 -> 33.9 us; FP32 storage measured slower
+        // with it, 44.6 -> 45.4 us, and keeps the general path)
+        if (cold && inner && !I.sandwich && !body_forced<R>(I)) {
+            if (!early_load) pull();
+            float2 v[9];
+#pragma unroll
+            for (int q = 0; q < 9; ++q) v[q] = make_float2(g[0][q], g[1][q]);
+            const float sp = I.fluid_rates_f[0], sm = I.fluid_rates_f[3];
+            collide_trt<R, Store<S>::kScaled>(v, make_float2(sp, sp), make_float2(sm, sm), I);
+#pragma unroll
+            for (int q = 0; q < 9; ++q) g[0][q] = v[q].x, g[1][q] = v[q].y;
+            put_adj<S, kStream>(Adst + (y[0] * kRowStride + cx0), g[0], g[1], pol);
+            return;
+        }
+    }
     const unsigned *m = mask_read + tile * W;
     unsigned any = 0u;
     if (!cold)
