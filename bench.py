@@ -670,7 +670,9 @@ def main():
     ap.add_argument("--cap-bytes", type=int, default=150 << 30)
     ap.add_argument("--max-slots", type=int, default=512)
     ap.add_argument("--chunk", type=int, default=500)
-    ap.add_argument("--variant", default="auto", choices=["auto", "0", "1", "2", "3", "4"])
+    ap.add_argument("--variant", default="auto",
+                    help="sweep launch shape: auto (timed by the autotuner) or a variant number "
+                         "below fpd_sweep_variants()")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and FP16 sub-measurements")
     ap.add_argument("--batched-instances", type=int, default=128)
     ap.add_argument("--batched-steps", type=int, default=64)
