@@ -369,6 +369,17 @@ __device__ __forceinline__ void lattice_tile(const Inst &I, S *__restrict__ pool
             return;
         }
     }
+    if constexpr (CY == 1 && kInner && kColl == kCollTrt && !std::is_same<S, double>::value) {
+        // the same for one cell per thread (variant 0, the batched sweep):
+        // the one-cell two-relaxation-time update at the fluid rates that
+        // finish_cells takes for an unforced cell, in a straight line
+        if (cold && inner && !I.sandwich && !body_forced<R>(I)) {
+            if (!early_load) pull();
+            collide_trt<R, Store<S>::kScaled>(g[0], I.fluid_rates_f[0], I.fluid_rates_f[3], I);
+            put_at<S, R, true, kStream>(Adst + (y[0] * kRowStride + cx0), I, g[0], pol);
+            return;
+        }
+    }
     const unsigned *m = mask_read + tile * W;
     unsigned any = 0u;
     if (!cold)
