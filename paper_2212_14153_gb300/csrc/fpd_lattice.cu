@@ -372,8 +372,10 @@ __device__ __forceinline__ void lattice_tile(const Inst &I, S *__restrict__ pool
     if constexpr (CY == 1 && kInner && kColl == kCollTrt && !std::is_same<S, double>::value) {
         // the same for one cell per thread (variant 0, the batched sweep):
         // the one-cell two-relaxation-time update at the fluid rates that
-        // finish_cells takes for an unforced cell, in a straight line
-        if (cold && inner && !I.sandwich && !body_forced<R>(I)) {
+        // finish_cells takes for an unforced cell, in a straight line; at
+        // walls and edges too (the pull handles them)
+        if (cold && !I.sandwich && !body_forced<R>(I)) {
+            if (!valid[0]) return;
             if (!early_load) pull();
             collide_trt<R, Store<S>::kScaled>(g[0], I.fluid_rates_f[0], I.fluid_rates_f[3], I);
             put_at<S, R, true, kStream>(Adst + (y[0] * kRowStride + cx0), I, g[0], pol);
